@@ -1,0 +1,353 @@
+/*
+ * oracle.c -- plain FP64 CPU oracle for the blocked Cholesky and pivot-free
+ * LU of Camarero, "Simple, Fast and Practicable Algorithms for Cholesky, LU
+ * and QR Decomposition Using Fast Rectangular Matrix Multiplication"
+ * (arXiv:1812.02056).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously correct
+ * reference that the tests, the smoke check and the CPU-baseline leg of the
+ * benchmark compare the CUDA library against.  The library never includes,
+ * links or calls it, and it shares no code with the library.
+ *
+ * Everything is IEEE double, round-to-nearest, compiled without FMA
+ * contraction (-ffp-contract=off), so each element is the exact sequence of
+ * roundings written below.  Loops over independent output elements may run
+ * on several OpenMP threads; no element's arithmetic depends on the thread
+ * count.
+ *
+ * Indices are 0-based; the paper's are 1-based and inclusive (Sec. 2, the
+ * paragraph after Algorithm 3).  Matrices are row-major with a leading
+ * dimension: element (i, j) of X is X[i * ldx + j].
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* mode bits for orc_chol / orc_lu */
+#define ORC_FULL_SQUARE 1 /* Cholesky: update the whole trailing square, as
+                             Algorithm 1 writes it (default: lower triangle,
+                             the only part the column step reads). LU always
+                             updates the full square. */
+#define ORC_SEQUENTIAL 2  /* subtract each product L_ik*L_jk from A_ij in
+                             turn instead of forming S = R R^T first */
+
+int orc_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+void orc_set_num_threads(int t) {
+#ifdef _OPENMP
+  if (t > 0) omp_set_num_threads(t);
+#else
+  (void)t;
+#endif
+}
+
+/*
+ * Algorithm 1 (fast Cholesky with step s).
+ *
+ * A (n x n, lda) is read, lower triangle and diagonal only unless
+ * ORC_FULL_SQUARE is set (then the whole square is copied and updated).
+ * L (n x n, ldl) receives the factor; its strict upper triangle is zero.
+ * s >= 1.  Returns 0, or c+1 when the value under the square root at column
+ * c is not positive (or is NaN): the paper assumes this never happens for a
+ * positive-definite input; the oracle stops there and leaves later columns
+ * of L zero.
+ */
+int64_t orc_chol(int64_t n, int64_t s, const double *A, int64_t lda, double *L,
+                 int64_t ldl, int mode) {
+  if (n < 0 || s < 1) return -1;
+  const int full = (mode & ORC_FULL_SQUARE) != 0;
+  const int seq = (mode & ORC_SEQUENTIAL) != 0;
+  /* working copy of A: the algorithm overwrites A's trailing part */
+  double *W = (double *)malloc((size_t)(n > 0 ? n : 1) * (size_t)(n > 0 ? n : 1) * sizeof(double));
+  if (!W) return -2;
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t j = 0; j < n; ++j)
+      W[i * n + j] = (full || j <= i) ? A[i * lda + j] : 0.0;
+  /* L := zero matrix of size n */
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t j = 0; j < n; ++j) L[i * ldl + j] = 0.0;
+
+  int64_t z = 0;
+  for (int64_t c = 0; c < n; ++c) {
+    if (c == z + s) {
+      /* R := L[c..n-1, z..c-1];  S := R R^T;  A[c.., c..] -= S;  z := c */
+#pragma omp parallel for schedule(dynamic, 8)
+      for (int64_t i = c; i < n; ++i) {
+        const int64_t jend = full ? n : i + 1;
+        for (int64_t j = c; j < jend; ++j) {
+          if (seq) {
+            double w = W[i * n + j];
+            for (int64_t k = z; k < c; ++k) w = w - L[i * ldl + k] * L[j * ldl + k];
+            W[i * n + j] = w;
+          } else {
+            double sij = 0.0;
+            for (int64_t k = z; k < c; ++k) sij = sij + L[i * ldl + k] * L[j * ldl + k];
+            W[i * n + j] = W[i * n + j] - sij;
+          }
+        }
+      }
+      z = c;
+    }
+    /* L_cc := sqrt(A_cc - sum_{k=z}^{c-1} L_ck^2) */
+    double d = W[c * n + c];
+    for (int64_t k = z; k < c; ++k) d = d - L[c * ldl + k] * L[c * ldl + k];
+    if (!(d > 0.0)) {
+      free(W);
+      return c + 1;
+    }
+    const double lcc = sqrt(d);
+    L[c * ldl + c] = lcc;
+    /* L_ic := (A_ic - sum_{k=z}^{c-1} L_ik L_ck) / L_cc   for i > c */
+#pragma omp parallel for schedule(static)
+    for (int64_t i = c + 1; i < n; ++i) {
+      double v = W[i * n + c];
+      for (int64_t k = z; k < c; ++k) v = v - L[i * ldl + k] * L[c * ldl + k];
+      L[i * ldl + c] = v / lcc;
+    }
+  }
+  free(W);
+  return 0;
+}
+
+/*
+ * Algorithm 2 (fast LU with step s, no pivoting): A = L U with L lower
+ * triangular and U upper unitriangular.
+ *
+ * A (n x n, lda) is read in full.  L and U (n x n each) receive the factors;
+ * the parts outside their triangles are zero.  The diagonal of U is the
+ * computed quotient L_cc / L_cc, which is exactly 1 in IEEE arithmetic.
+ * Returns 0, or c+1 when L_cc is zero or NaN (the paper requires nonzero
+ * leading principal minors, which rules this out).
+ */
+int64_t orc_lu(int64_t n, int64_t s, const double *A, int64_t lda, double *L,
+               int64_t ldl, double *U, int64_t ldu, int mode) {
+  if (n < 0 || s < 1) return -1;
+  const int seq = (mode & ORC_SEQUENTIAL) != 0;
+  double *W = (double *)malloc((size_t)(n > 0 ? n : 1) * (size_t)(n > 0 ? n : 1) * sizeof(double));
+  if (!W) return -2;
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t j = 0; j < n; ++j) W[i * n + j] = A[i * lda + j];
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t j = 0; j < n; ++j) {
+      L[i * ldl + j] = 0.0;
+      U[i * ldu + j] = 0.0;
+    }
+
+  int64_t z = 0;
+  for (int64_t c = 0; c < n; ++c) {
+    if (c == z + s) {
+      /* R_L := L[c.., z..c-1]; R_U := U[z..c-1, c..]; S := R_L R_U;
+         A[c.., c..] -= S;  z := c */
+#pragma omp parallel for schedule(static)
+      for (int64_t i = c; i < n; ++i) {
+        for (int64_t j = c; j < n; ++j) {
+          if (seq) {
+            double w = W[i * n + j];
+            for (int64_t k = z; k < c; ++k) w = w - L[i * ldl + k] * U[k * ldu + j];
+            W[i * n + j] = w;
+          } else {
+            double sij = 0.0;
+            for (int64_t k = z; k < c; ++k) sij = sij + L[i * ldl + k] * U[k * ldu + j];
+            W[i * n + j] = W[i * n + j] - sij;
+          }
+        }
+      }
+      z = c;
+    }
+    /* L_ic := A_ic - sum_{k=z}^{c-1} L_ik U_kc   for i >= c */
+#pragma omp parallel for schedule(static)
+    for (int64_t i = c; i < n; ++i) {
+      double v = W[i * n + c];
+      for (int64_t k = z; k < c; ++k) v = v - L[i * ldl + k] * U[k * ldu + c];
+      L[i * ldl + c] = v;
+    }
+    const double lcc = L[c * ldl + c];
+    if (lcc == 0.0 || lcc != lcc) {
+      free(W);
+      return c + 1;
+    }
+    /* U_ci := (A_ci - sum_{k=z}^{c-1} L_ck U_ki) / L_cc   for i >= c */
+#pragma omp parallel for schedule(static)
+    for (int64_t i = c; i < n; ++i) {
+      double v = W[c * n + i];
+      for (int64_t k = z; k < c; ++k) v = v - L[c * ldl + k] * U[k * ldu + i];
+      U[c * ldu + i] = v / lcc;
+    }
+  }
+  free(W);
+  return 0;
+}
+
+/*
+ * Triangular solves, textbook forward and back substitution, B row-major
+ * n x nrhs (ldb), overwritten with the solution.
+ */
+
+/* L Y = B, L lower (non-unit diagonal) */
+void orc_solve_lower(int64_t n, int64_t nrhs, const double *L, int64_t ldl, double *B,
+                     int64_t ldb) {
+#pragma omp parallel for schedule(static)
+  for (int64_t r = 0; r < nrhs; ++r) {
+    for (int64_t i = 0; i < n; ++i) {
+      double v = B[i * ldb + r];
+      for (int64_t k = 0; k < i; ++k) v = v - L[i * ldl + k] * B[k * ldb + r];
+      B[i * ldb + r] = v / L[i * ldl + i];
+    }
+  }
+}
+
+/* L^T X = Y, L lower (non-unit diagonal) */
+void orc_solve_lower_trans(int64_t n, int64_t nrhs, const double *L, int64_t ldl, double *B,
+                           int64_t ldb) {
+#pragma omp parallel for schedule(static)
+  for (int64_t r = 0; r < nrhs; ++r) {
+    for (int64_t i = n - 1; i >= 0; --i) {
+      double v = B[i * ldb + r];
+      for (int64_t k = i + 1; k < n; ++k) v = v - L[k * ldl + i] * B[k * ldb + r];
+      B[i * ldb + r] = v / L[i * ldl + i];
+    }
+  }
+}
+
+/* U X = Y, U upper with unit diagonal (the stored diagonal is not read) */
+void orc_solve_unit_upper(int64_t n, int64_t nrhs, const double *U, int64_t ldu, double *B,
+                          int64_t ldb) {
+#pragma omp parallel for schedule(static)
+  for (int64_t r = 0; r < nrhs; ++r) {
+    for (int64_t i = n - 1; i >= 0; --i) {
+      double v = B[i * ldb + r];
+      for (int64_t k = i + 1; k < n; ++k) v = v - U[i * ldu + k] * B[k * ldb + r];
+      B[i * ldb + r] = v;
+    }
+  }
+}
+
+/* X = A^{-1} B from a Cholesky factor: L Y = B, then L^T X = Y */
+void orc_chol_solve(int64_t n, int64_t nrhs, const double *L, int64_t ldl, double *B,
+                    int64_t ldb) {
+  orc_solve_lower(n, nrhs, L, ldl, B, ldb);
+  orc_solve_lower_trans(n, nrhs, L, ldl, B, ldb);
+}
+
+/* X = A^{-1} B from a Crout LU: L Y = B, then U X = Y */
+void orc_lu_solve(int64_t n, int64_t nrhs, const double *L, int64_t ldl, const double *U,
+                  int64_t ldu, double *B, int64_t ldb) {
+  orc_solve_lower(n, nrhs, L, ldl, B, ldb);
+  orc_solve_unit_upper(n, nrhs, U, ldu, B, ldb);
+}
+
+/* R = B - A X  (all row-major, n x n A, n x nrhs B, X, R) */
+void orc_residual(int64_t n, int64_t nrhs, const double *A, int64_t lda, const double *X,
+                  int64_t ldx, const double *B, int64_t ldb, double *R, int64_t ldr) {
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    for (int64_t r = 0; r < nrhs; ++r) {
+      double v = 0.0;
+      for (int64_t k = 0; k < n; ++k) v = v + A[i * lda + k] * X[k * ldx + r];
+      R[i * ldr + r] = B[i * ldb + r] - v;
+    }
+  }
+}
+
+/*
+ * Iterative refinement from a (possibly low-precision) Cholesky factor held
+ * in FP64:  x := solve(L, b); repeat { r := b - A x; stop when
+ * max_r eta_r <= tol; d := solve(L, r); x := x + d }.  eta_r is the normwise
+ * backward error ||b - A x||_inf / (||A||_inf ||x||_inf + ||b||_inf) of
+ * column r.  Returns the number of corrections applied; *eta_out receives
+ * the final max eta (or the last one if max_iter was reached).
+ */
+int64_t orc_chol_refine(int64_t n, int64_t nrhs, const double *A, int64_t lda, const double *L,
+                        int64_t ldl, const double *B, int64_t ldb, double *X, int64_t ldx,
+                        double tol, int64_t max_iter, double *eta_out) {
+  double *R = (double *)malloc((size_t)(n > 0 ? n : 1) * (size_t)(nrhs > 0 ? nrhs : 1) * sizeof(double));
+  if (!R) return -2;
+  double anorm = 0.0; /* ||A||_inf, max row sum of |A| */
+  for (int64_t i = 0; i < n; ++i) {
+    double rs = 0.0;
+    for (int64_t k = 0; k < n; ++k) rs = rs + fabs(A[i * lda + k]);
+    if (rs > anorm) anorm = rs;
+  }
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t r = 0; r < nrhs; ++r) X[i * ldx + r] = B[i * ldb + r];
+  orc_chol_solve(n, nrhs, L, ldl, X, ldx);
+  int64_t it = 0;
+  double eta = 0.0;
+  for (;;) {
+    orc_residual(n, nrhs, A, lda, X, ldx, B, ldb, R, nrhs);
+    eta = 0.0;
+    for (int64_t r = 0; r < nrhs; ++r) {
+      double rn = 0.0, xn = 0.0, bn = 0.0;
+      for (int64_t i = 0; i < n; ++i) {
+        if (fabs(R[i * nrhs + r]) > rn) rn = fabs(R[i * nrhs + r]);
+        if (fabs(X[i * ldx + r]) > xn) xn = fabs(X[i * ldx + r]);
+        if (fabs(B[i * ldb + r]) > bn) bn = fabs(B[i * ldb + r]);
+      }
+      const double den = anorm * xn + bn;
+      const double e = den > 0.0 ? rn / den : 0.0;
+      if (e > eta) eta = e;
+    }
+    if (eta <= tol || it >= max_iter) break;
+    orc_chol_solve(n, nrhs, L, ldl, R, nrhs);
+    for (int64_t i = 0; i < n; ++i)
+      for (int64_t r = 0; r < nrhs; ++r) X[i * ldx + r] = X[i * ldx + r] + R[i * nrhs + r];
+    ++it;
+  }
+  if (eta_out) *eta_out = eta;
+  free(R);
+  return it;
+}
+
+/*
+ * Backward errors, accumulated in long double:
+ *   Cholesky: ||A - L L^T||_F / ||A||_F over the full square (A symmetric);
+ *   LU:       ||A - L U||_F / ||A||_F.
+ */
+double orc_chol_backward_error(int64_t n, const double *A, int64_t lda, const double *L,
+                               int64_t ldl) {
+  long double num = 0.0L, den = 0.0L;
+#pragma omp parallel for schedule(dynamic, 8) reduction(+ : num, den)
+  for (int64_t i = 0; i < n; ++i) {
+    for (int64_t j = 0; j < n; ++j) {
+      long double p = 0.0L;
+      const int64_t kmax = i < j ? i : j;
+      for (int64_t k = 0; k <= kmax; ++k)
+        p += (long double)L[i * ldl + k] * (long double)L[j * ldl + k];
+      const long double a = (long double)A[i * lda + j];
+      num += (a - p) * (a - p);
+      den += a * a;
+    }
+  }
+  return den > 0.0L ? (double)sqrtl(num / den) : 0.0;
+}
+
+double orc_lu_backward_error(int64_t n, const double *A, int64_t lda, const double *L,
+                             int64_t ldl, const double *U, int64_t ldu) {
+  long double num = 0.0L, den = 0.0L;
+#pragma omp parallel for schedule(dynamic, 8) reduction(+ : num, den)
+  for (int64_t i = 0; i < n; ++i) {
+    for (int64_t j = 0; j < n; ++j) {
+      long double p = 0.0L;
+      const int64_t kmax = i < j ? i : j;
+      for (int64_t k = 0; k <= kmax; ++k) {
+        const long double u = (k == j) ? 1.0L : (long double)U[k * ldu + j];
+        p += (long double)L[i * ldl + k] * u;
+      }
+      const long double a = (long double)A[i * lda + j];
+      num += (a - p) * (a - p);
+      den += a * a;
+    }
+  }
+  return den > 0.0L ? (double)sqrtl(num / den) : 0.0;
+}

@@ -1,0 +1,119 @@
+"""The oracle's pins must catch plausible mistakes.
+
+Each case plants one mistake (a dropped term, a wrong sign, a transposed
+operand, a wrong index or range, a missing step) in a copy of oracle.c,
+compiles the copy with the same flags, and checks that at least one pin --
+Pascal closed form, rational brute force, LAPACK, step agreement -- fails
+with it.  The planted copies live in a temporary directory; the committed
+oracle is untouched.
+"""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1812_02056_gb300 import inputs as I
+from tests import exact
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "oracle.c")
+
+MUTATIONS = {
+    "chol_diag_dropped_term": ("d = d - L[c * ldl + k] * L[c * ldl + k];", "d = d;"),
+    "chol_diag_sign": ("d = d - L[c * ldl + k] * L[c * ldl + k];",
+                       "d = d + L[c * ldl + k] * L[c * ldl + k];"),
+    "chol_col_sign": ("v = v - L[i * ldl + k] * L[c * ldl + k];",
+                      "v = v + L[i * ldl + k] * L[c * ldl + k];"),
+    "chol_col_transposed": ("v = v - L[i * ldl + k] * L[c * ldl + k];",
+                            "v = v - L[k * ldl + i] * L[c * ldl + k];"),
+    "chol_no_divide": ("L[i * ldl + c] = v / lcc;", "L[i * ldl + c] = v;"),
+    "chol_no_sqrt": ("const double lcc = sqrt(d);", "const double lcc = d;"),
+    "chol_update_transposed": ("sij = sij + L[i * ldl + k] * L[j * ldl + k];",
+                               "sij = sij + L[i * ldl + k] * L[k * ldl + j];"),
+    "chol_update_sign": ("W[i * n + j] = W[i * n + j] - sij;", "W[i * n + j] = W[i * n + j] + sij;"),
+    "chol_update_skips_diag": ("for (int64_t j = c; j < jend; ++j) {", "for (int64_t j = c + 1; j < jend; ++j) {"),
+    "chol_checkpoint_not_moved": ("      z = c;\n    }\n    /* L_cc", "    }\n    /* L_cc"),
+    "chol_col_first_term_dropped": ("for (int64_t k = z; k < c; ++k) v = v - L[i * ldl + k] * L[c * ldl + k];",
+                                    "for (int64_t k = z + 1; k < c; ++k) v = v - L[i * ldl + k] * L[c * ldl + k];"),
+    "lu_no_divide": ("U[c * ldu + i] = v / lcc;", "U[c * ldu + i] = v;"),
+    "lu_update_transposed": ("sij = sij + L[i * ldl + k] * U[k * ldu + j];",
+                             "sij = sij + L[i * ldl + k] * U[j * ldu + k];"),
+    "lu_col_wrong_factor": ("v = v - L[i * ldl + k] * U[k * ldu + c];",
+                            "v = v - L[i * ldl + k] * U[c * ldu + k];"),
+    "lu_row_sign": ("v = v - L[c * ldl + k] * U[k * ldu + i];", "v = v + L[c * ldl + k] * U[k * ldu + i];"),
+}
+
+
+def _build_mutant(tmp_path, name, old, new):
+    src = open(SRC).read()
+    assert src.count(old) >= 1, f"mutation {name} does not apply"
+    mutated = src.replace(old, new)
+    c_path = tmp_path / f"{name}.c"
+    so_path = tmp_path / f"{name}.so"
+    c_path.write_text(mutated)
+    subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
+                    str(c_path), "-o", str(so_path), "-lm"], check=True)
+    return str(so_path)
+
+
+def _pins_pass() -> bool:
+    """Run a compact set of the pins against whatever library oracle._lib is."""
+    try:
+        P, Lp = I.pascal_sym(12), I.pascal_lower(12)
+        for s in (1, 3, 12):
+            L, info = oracle.chol(P, s)
+            if info != 0 or not np.array_equal(L, Lp):
+                return False
+            Lu, Uu, info = oracle.lu(P, s)
+            if info != 0 or not np.array_equal(Lu, Lp) or not np.array_equal(Uu, Lp.T):
+                return False
+        A = I.small_int_spd(5, 501)
+        ref = exact.cholesky_exact_decimal(A.astype(int).tolist())
+        for s in (1, 2, 5):
+            L, info = oracle.chol(A, s)
+            if info != 0:
+                return False
+            for i in range(5):
+                for j in range(i + 1):
+                    if abs(L[i, j] - float(ref[i][j])) > 1e-13 * max(abs(float(ref[i][j])), 1.0):
+                        return False
+        B = I.spd_gram(64, 3)
+        ref = np.linalg.cholesky(B)
+        for s in (1, 5, 64):
+            L, info = oracle.chol(B, s)
+            if info != 0 or np.abs(L - ref).max() > 1e-12 * np.abs(ref).max():
+                return False
+        C = I.lu_diag_dominant(30, 2)
+        for s in (1, 4, 30):
+            L, U, info = oracle.lu(C, s)
+            if info != 0 or oracle.lu_backward_error(C, L, U) > 1e-13:
+                return False
+        return True
+    except Exception:
+        return False
+
+
+def test_unmutated_oracle_passes_compact_pins():
+    assert _pins_pass()
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(tmp_path, name):
+    old, new = MUTATIONS[name]
+    path = _build_mutant(tmp_path, name, old, new)
+    saved = oracle._lib
+    try:
+        lib = ctypes.CDLL(path)
+        oracle._lib = None
+        real = oracle.build
+        oracle.build = lambda force=False: path  # load the planted copy
+        try:
+            oracle._load()
+        finally:
+            oracle.build = real
+        assert not _pins_pass(), f"planted mistake {name} went unnoticed"
+    finally:
+        oracle._lib = saved
+        del lib
