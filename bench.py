@@ -1,0 +1,371 @@
+#!/usr/bin/env python
+"""Benchmark of the blocked Cholesky (Algorithm 1, arXiv:1812.02056) on GB300.
+
+One step = one FP64 Cholesky factorization with step s of an n x n SPD matrix
+A = G G^T + n I (G iid N(0,1)), through the C ABI (gb_chol_factor), A and L
+resident in HBM.  Default n = 8192, s = 256.  The metric is factorization
+GFLOP/s counted as n^3/3 flops per step.
+
+Prints ONE JSON line (rank 0).  Besides the contract keys it carries:
+  roofline      the dominant kernel (largest device-time phase), from CUDA
+                events the library records around each launch on the
+                factorization's stream during the timed region;
+  cpu_baseline  the CPU oracle timed on a bounded sample on the host cores;
+  e2e           the same metric through gb_chol_factor on pinned HOST
+                buffers (host<->device copies inside the timed region);
+  extra         s sweep (FP64 and FP32), pivot-free LU, accuracy figures.
+
+--impl reference times the CPU oracle (the reference arm of this project)
+on a bounded sample of the same workload and prints the same JSON line with
+"impl": "reference".
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Cholesky GFLOP/s (n^3/3 flops per factorization)"
+UNIT = "GFLOP/s"
+
+
+def chol_flops(n: int) -> float:
+    return n ** 3 / 3.0
+
+
+def lu_flops(n: int) -> float:
+    return 2.0 * n ** 3 / 3.0
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.out = os.path.join("/tmp", f"gbchol_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.out, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.out) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        try:
+            os.remove(self.out)
+        except OSError:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------- CPU oracle
+def cpu_oracle_sample(n: int, s: int, seed: int, reps: int = 1):
+    import oracle
+    from paper_1812_02056_gb300 import inputs
+    A = inputs.spd_gram(n, seed)
+    oracle.chol(A[:64, :64], min(s, 64))  # load / build outside the timing
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        L, info = oracle.chol(A, s)
+    dt = (time.perf_counter() - t0) / reps
+    return {"value": chol_flops(n) / dt / 1e9, "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"oracle FP64 Cholesky (Algorithm 1) n={n} s={s}, {reps} run(s), "
+                      f"{dt:.2f} s each; GFLOP/s = (n^3/3)/time"}
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle on a bounded sample of the workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_1812_02056_gb300 import inputs
+    n = args.ref_n
+    s = min(args.s, n)
+    A = inputs.spd_gram(n, inputs.seed_for(inputs.W_N8192))
+    oracle.chol(A[:64, :64], 8)
+    for _ in range(args.warmup):
+        oracle.chol(A, s)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.chol(A, s)
+    el = time.perf_counter() - t0
+    ms = el / args.steps * 1e3
+    value = chol_flops(n) * args.steps / el / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"FP64 Cholesky (Algorithm 1), A = G G^T + n I, n={args.n}, "
+                               f"s={args.s}; each reference step factors a bounded sample "
+                               f"n={n}, s={s}", "n": args.n, "s": args.s, "sample_n": n},
+        "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle",
+                         "cores": oracle.num_threads(),
+                         "sample": f"oracle FP64 Cholesky n={n} s={s} per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_ours(args):
+    import torch
+
+    from paper_1812_02056_gb300 import _build, binding, inputs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0 or world == 1:
+        _build.build()
+    if dist:
+        dist.barrier()
+    h = binding.Handle(local)
+    n, s = args.n, args.s
+    dt = binding.DTYPES[args.dtype]
+    A = inputs.spd_gram(n, inputs.seed_for(inputs.W_N8192, rank), device=dev)
+    if args.dtype == "f32":
+        A = A.float()
+    L = torch.empty((n, n), dtype=torch.float64 if dt == binding.GB_F64 else torch.float32,
+                    device=dev)
+    info = torch.zeros(1, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        binding.check(h.gb_chol_factor(n, s, dt, A, n, L, n, info, stream), "gb_chol_factor")
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    assert int(info.item()) == 0, f"breakdown at column {int(info.item())}"
+
+    # ---- timed region
+    h.set_option(binding.GB_OPT_PROFILE, 1)
+    h.profile_read()  # drop anything recorded before
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    launches0 = binding.kernel_launches()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = binding.kernel_launches() - launches0
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    prof = h.profile_read().as_dict()
+    h.set_option(binding.GB_OPT_PROFILE, 0)
+    ms_total = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    flops = chol_flops(n)
+    value = world * args.steps * flops / (ms_total * 1e-3) / 1e9
+    assert int(info.item()) == 0
+
+    peaks, peak_src = load_peaks()
+    # FP64 / FP32 pipe rates: measured by the library's FMA loop, and the
+    # nominal per-SM rate x SMs x max clock (unit counts and clocks)
+    fma64 = h.measure_fma_peak("f64")
+    fma32 = h.measure_fma_peak("f32")
+
+    # dominant kernel = phase with the largest device time
+    dom = max(prof, key=lambda p: prof[p]["ms"])
+    d = prof[dom]
+    dom_ms_per_launch = d["ms"] / max(d["launches"], 1)
+    if args.dtype in ("f64", "f32") and dom in ("update", "inner", "panel", "diag"):
+        ach = d["flops"] / (d["ms"] * 1e-3) / 1e12
+        peak = (fma64 if args.dtype == "f64" else fma32) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None, "kernel": dom,
+                "peak_source": f"{args.dtype} FMA pipe, measured by gb_measure_fma_peak",
+                "launches": d["launches"], "ms_per_launch": dom_ms_per_launch,
+                "algorithmic_flops_per_launch": d["flops"] / max(d["launches"], 1)}
+    else:
+        ach = d["bytes"] / (d["ms"] * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / peaks["hbm_gbs"], "traffic": None, "kernel": dom,
+                "peak_source": f"hbm_gbs ({peak_src})", "launches": d["launches"]}
+
+    # ---- accuracy of the timed factor (FP64 backward error on the device)
+    extra = {"phases": prof, "fma_peak_tflops": {"f64": fma64 / 1e12, "f32": fma32 / 1e12}}
+    if not args.quick:
+        A64 = A.double() if A.dtype != torch.float64 else A
+        extra["backward_error"] = h.backward_error(A64, L, args.dtype)
+
+    # ---- end to end through host buffers (pinned)
+    e2e = None
+    if not args.no_e2e:
+        Ah = torch.empty((n, n), dtype=A.dtype, pin_memory=True)
+        Ah.copy_(A)
+        Lh = torch.empty((n, n), dtype=L.dtype, pin_memory=True)
+        infoh = torch.zeros(1, dtype=torch.int32, pin_memory=True)
+        esteps = max(1, min(args.steps, args.e2e_steps))
+        binding.check(h.gb_chol_factor(n, s, dt, Ah, n, Lh, n, infoh, stream), "e2e warmup")
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(esteps):
+            binding.check(h.gb_chol_factor(n, s, dt, Ah, n, Lh, n, infoh, stream), "e2e")
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([el], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        assert int(infoh[0]) == 0
+        esz = A.element_size()
+        e2e = {"value": world * esteps * flops / el / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": n * n * esz, "d2h_bytes_per_step": n * n * L.element_size() + 4,
+               "steps": esteps, "ms_per_step": el / esteps * 1e3}
+        del Ah, Lh
+
+    # ---- sweeps (not part of the timed value)
+    if not args.quick:
+        sweep = {}
+        for sdt in ("f64", "f32"):
+            Asw = A if sdt == args.dtype else (A.float() if sdt == "f32" else A.double())
+            Lsw = torch.empty((n, n), dtype=Asw.dtype, device=dev)
+            for ss in (64, 117, 256, 512):
+                reps = 1 if sdt == "f64" else 3
+                binding.check(h.gb_chol_factor(n, ss, binding.DTYPES[sdt], Asw, n, Lsw, n, info,
+                                               stream), "sweep")
+                a0 = torch.cuda.Event(enable_timing=True)
+                a1 = torch.cuda.Event(enable_timing=True)
+                a0.record(stream)
+                for _ in range(reps):
+                    h.gb_chol_factor(n, ss, binding.DTYPES[sdt], Asw, n, Lsw, n, info, stream)
+                a1.record(stream)
+                torch.cuda.synchronize()
+                sweep[f"chol_{sdt}_s{ss}"] = flops / (a0.elapsed_time(a1) / reps * 1e-3) / 1e9
+            del Lsw
+        Alu = torch.from_numpy(inputs.lu_diag_dominant(n, inputs.seed_for(inputs.W_N8192, 50))).to(dev)
+        LU = torch.empty_like(Alu)
+        for ss in (256,):
+            h.gb_lu_factor(n, ss, binding.GB_F64, Alu, n, LU, n, info, stream)
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            h.gb_lu_factor(n, ss, binding.GB_F64, Alu, n, LU, n, info, stream)
+            a1.record(stream)
+            torch.cuda.synchronize()
+            sweep[f"lu_f64_s{ss}"] = lu_flops(n) / (a0.elapsed_time(a1) * 1e-3) / 1e9
+        extra["sweep_gflops"] = sweep
+        del Alu, LU
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_oracle_sample(args.cpu_n, min(s, args.cpu_n), inputs.seed_for(inputs.W_N8192, 90))
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": args.dtype, "data": "synthetic",
+            "config": {"workload": f"{args.dtype.upper()} Cholesky (Algorithm 1), "
+                                   f"A = G G^T + n I, n={n}, s={s}",
+                       "n": n, "s": s, "inner_step": h.get_option(binding.GB_OPT_INNER_STEP),
+                       "l2": f"inputs larger than L2 (A and L {n * n * A.element_size() >> 20} MiB each)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "gpu_launches": launches, "clocks": clk, "roofline": roof, "e2e": e2e,
+            "cpu_baseline": cpu, "extra": extra,
+        }
+        print(json.dumps(line))
+    h.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=8192)
+    ap.add_argument("--s", type=int, default=256)
+    ap.add_argument("--dtype", choices=["f64", "f32"], default="f64")
+    ap.add_argument("--cpu-n", type=int, default=4096)
+    ap.add_argument("--ref-n", type=int, default=3072)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--quick", action="store_true", help="skip sweeps and accuracy figures")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

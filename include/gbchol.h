@@ -1,0 +1,287 @@
+/*
+ * gbchol.h -- C ABI of the GB300 (sm_103a) blocked Cholesky / pivot-free LU
+ * library.
+ *
+ * The method is that of Camarero, "Simple, Fast and Practicable Algorithms
+ * for Cholesky, LU and QR Decomposition Using Fast Rectangular Matrix
+ * Multiplication" (arXiv:1812.02056), Sec. 2:
+ *
+ *  - Algorithm 1 (Cholesky): columns are finished one at a time, each from
+ *    the columns since the last checkpoint z; every s columns the trailing
+ *    matrix receives the delayed rank-s update A[c.., c..] -= R R^T with
+ *    R = L[c.., z..c-1], and z moves to c.
+ *  - Algorithm 2 (LU, no pivoting, Crout form): the same schedule with
+ *    A[c.., c..] -= R_L R_U, L lower triangular, U upper unitriangular.
+ *
+ * Conventions shared by every call
+ *  - Matrices are row-major (the order PyTorch uses): element (i, j) of X is
+ *    X[i * ldx + j]; every leading dimension must be >= the row length.
+ *  - Pointers may be device memory (cudaMalloc / PyTorch CUDA tensors) or
+ *    host memory, unless a call says otherwise.  The library detects which
+ *    with cudaPointerGetAttributes; host buffers are staged through the
+ *    handle's device workspace and the call then waits for its stream, so a
+ *    call on host buffers returns with its outputs in place.  Calls on device
+ *    buffers are asynchronous on `stream`.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).
+ *  - The caller owns every buffer it passes; the library never frees caller
+ *    memory.  The handle owns its workspace (grown on demand, released by
+ *    gb_destroy).
+ *  - `info` is an int that receives 0 on success or c > 0, the 1-based
+ *    column at which the factorization broke down (Cholesky: the value under
+ *    the square root was not positive or was NaN; LU: the pivot L_cc was
+ *    zero or NaN).  It may be a device or a host pointer.  On breakdown the
+ *    contents of the output past column c-1 are unspecified.
+ *  - Return values report host-side problems only (see gb_status below).
+ *    Nothing traps on the device: device-side errors are reported through
+ *    `info` and the handle's error word.
+ *
+ * Thread safety and ordering: a handle may be used from one host thread at a
+ * time, and its calls must be ordered on one stream (its workspace and
+ * device flags are shared by all its calls).  Use one handle per stream for
+ * concurrent work.
+ */
+#ifndef GBCHOL_H
+#define GBCHOL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status */
+typedef int gb_status;
+#define GB_OK 0
+/* -k (k = 1, 2, ...): the k-th argument of the call is invalid */
+#define GB_ERR_NOMEM (-1001)         /* device or host allocation failed            */
+#define GB_ERR_CUDA (-1002)          /* a CUDA runtime call failed                  */
+#define GB_ERR_TIMEOUT (-1003)       /* a bounded device-side wait expired          */
+#define GB_ERR_NOT_CONVERGED (-1004) /* refinement reached max_iter above tol      */
+#define GB_ERR_REJECTED (-1005)      /* server: request larger than the budget      */
+#define GB_ERR_UNSUPPORTED (-1006)   /* combination of options not implemented      */
+#define GB_ERR_BREAKDOWN (-1007)     /* solve: the factor has a zero/NaN pivot      */
+#define GB_ERR_STATE (-1008)         /* object used in the wrong state              */
+
+/* Short English description of a status code (static storage). */
+const char *gb_status_string(gb_status st);
+
+/* ------------------------------------------------------------------ dtypes */
+/*
+ * Arithmetic of a factorization.
+ *  GB_F64      A and L/U are double; every step in FP64.
+ *  GB_F32      A and L/U are float;  every step in FP32.
+ *  GB_MIX_BF16 A is double, L/U are float.  The working matrix is FP32; the
+ *              diagonal-block column steps (square root, pivots) run in
+ *              FP64; the panel rows in FP32; the delayed rank-s update runs
+ *              on the tensor cores with BF16 operands and FP32 accumulation.
+ *  GB_MIX_F16  as GB_MIX_BF16 with FP16 operands.
+ * Mixed factors are meant to be refined back to FP64 accuracy by
+ * gb_chol_solve / gb_lu_solve given the original FP64 matrix.
+ */
+typedef enum gb_dtype {
+  GB_F64 = 0,
+  GB_F32 = 1,
+  GB_MIX_BF16 = 2,
+  GB_MIX_F16 = 3
+} gb_dtype;
+
+/* ------------------------------------------------------------------ handle */
+typedef struct gb_handle gb_handle;
+
+/* Create a handle bound to CUDA device `device` (made current by every call
+ * that takes the handle).  Returns GB_ERR_CUDA if the device is absent. */
+gb_status gb_create(gb_handle **h, int device);
+
+/* Wait for the handle's work, release its workspace and free it. */
+gb_status gb_destroy(gb_handle *h);
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+int gb_version(void);
+
+/* Text of the last CUDA error recorded by this thread (static storage). */
+const char *gb_last_error(void);
+
+/* Options set on a handle (all have defaults). */
+typedef enum gb_option {
+  GB_OPT_INNER_STEP = 1,    /* width of the column steps inside one s-block
+                               (default 64, range 1..64).  s <= this value is
+                               Algorithm 1/2 exactly as written; larger s
+                               factors each block of s columns with this
+                               inner step (the paper's remark that s may vary
+                               during the execution, Sec. 2, last paragraph). */
+  GB_OPT_USE_GRAPHS = 2,    /* 1: replay a captured CUDA graph of the whole
+                               block loop for repeated (n, s, dtype, ld)
+                               calls on device buffers (default 1).          */
+  GB_OPT_TC_UPDATE = 3,     /* 1: mixed dtypes use the tcgen05 tensor-core
+                               update (default); 0: the SIMT FP32 update.   */
+  GB_OPT_SPIN_LIMIT = 4,    /* limit of bounded device waits, in units of
+                               100 ns of %globaltimer (default 2^26, ~6.7 s). */
+  GB_OPT_PROFILE = 5        /* 1: record CUDA events around every launch of
+                               the factorizations (read with
+                               gb_profile_read); default 0.                 */
+} gb_option;
+
+gb_status gb_set_option(gb_handle *h, gb_option opt, int64_t value);
+gb_status gb_get_option(gb_handle *h, gb_option opt, int64_t *value);
+
+/* ---------------------------------------------------------------- Cholesky */
+/*
+ * gb_chol_factor -- Algorithm 1 (fast Cholesky with step s), arXiv:1812.02056
+ * Sec. 2.
+ *
+ *  n     order of A (n >= 0).
+ *  s     step: the delayed rank-s update is applied every s columns.  s >= 1;
+ *        s >= n means no update (Cholesky-Crout); s = 1 is the recursive
+ *        right-looking algorithm (Sec. 2, after Algorithm 3).  s = 0 picks
+ *        the tuned step for (n, dt).
+ *  dt    arithmetic, see gb_dtype.  A is double for GB_F64 and the mixed
+ *        dtypes, float for GB_F32; L is double for GB_F64, float otherwise.
+ *  A     n x n symmetric positive-definite matrix, leading dimension lda.
+ *        Only the lower triangle (with the diagonal) is read.
+ *  L     n x n output, leading dimension ldl.  Receives the lower-triangular
+ *        factor with A = L L^T; its strict upper triangle is set to zero.
+ *        L may alias A when both have the same element type (in place).
+ *  info  see the conventions above.
+ */
+gb_status gb_chol_factor(gb_handle *h, int64_t n, int64_t s, gb_dtype dt, const void *A,
+                         int64_t lda, void *L, int64_t ldl, int *info, void *stream);
+
+/* ---------------------------------------------------------------------- LU */
+/*
+ * gb_lu_factor -- Algorithm 2 (fast LU with step s, no pivoting),
+ * arXiv:1812.02056 Sec. 2.  A must have nonzero leading principal minors.
+ *
+ *  A     n x n, leading dimension lda, read in full.  Element types as for
+ *        gb_chol_factor.
+ *  LU    n x n output in compact form, leading dimension ldlu: the lower
+ *        triangle with the diagonal holds L, the strict upper triangle holds
+ *        the strict upper part of the unit upper triangular U (its diagonal
+ *        of ones is implied, not stored).  LU may alias A when both have the
+ *        same element type.
+ *  s, dt, info, stream as for gb_chol_factor.
+ */
+gb_status gb_lu_factor(gb_handle *h, int64_t n, int64_t s, gb_dtype dt, const void *A,
+                       int64_t lda, void *LU, int64_t ldlu, int *info, void *stream);
+
+/* ------------------------------------------------------------------ solves */
+typedef struct gb_refine_opts {
+  double tol;     /* stop when max_r eta_r <= tol (default 1e-14)           */
+  int max_iter;   /* maximum number of corrections (default 30)             */
+} gb_refine_opts;
+
+typedef struct gb_solve_stats {
+  int iterations; /* corrections applied                                    */
+  int converged;  /* 1 if eta <= tol was reached (always 1 without A)       */
+  double eta;     /* final max over right-hand sides of
+                     ||b - A x||_inf / (||A||_inf ||x||_inf + ||b||_inf);
+                     0 when A was not given                                  */
+} gb_solve_stats;
+
+/*
+ * gb_chol_solve -- solve A X = B from a factor made by gb_chol_factor:
+ * L Y = B then L^T X = Y (forward and back substitution).  Not part of the
+ * paper, which stops at the factor; it is the use the factor is made for
+ * (Sec. 1: "used everywhere to solve linear systems").
+ *
+ *  factor_dt  the dtype the factor was made with (L is double for GB_F64,
+ *             float otherwise).
+ *  L, ldl     the factor.
+ *  A, lda     NULL for a plain solve in the factor's precision (FP64 for
+ *             GB_F64, FP32 otherwise, result stored as double).  Non-NULL:
+ *             the original FP64 matrix (full square, symmetric); the call
+ *             then refines X in FP64: r = B - A X (FP64), d = solve(L, r)
+ *             (factor precision), X += d (FP64), until opts->tol.
+ *  B, ldb     n x nrhs right-hand sides (double), row-major.
+ *  X, ldx     n x nrhs solution (double); may alias B only when A is NULL.
+ *  opts       NULL for defaults.    stats  may be NULL.
+ * With A given the call waits for its stream once per correction to read
+ * eta.  Returns GB_ERR_NOT_CONVERGED if max_iter corrections left
+ * eta > tol (X holds the last iterate), GB_ERR_BREAKDOWN if a diagonal
+ * entry of L is zero or not finite.
+ */
+gb_status gb_chol_solve(gb_handle *h, int64_t n, int64_t nrhs, gb_dtype factor_dt, const void *L,
+                        int64_t ldl, const double *A, int64_t lda, const double *B, int64_t ldb,
+                        double *X, int64_t ldx, const gb_refine_opts *opts,
+                        gb_solve_stats *stats, void *stream);
+
+/*
+ * gb_lu_solve -- solve A X = B from a compact factor made by gb_lu_factor:
+ * L Y = B, then U X = Y with U unit upper.  Arguments as gb_chol_solve; A,
+ * when given, is the original FP64 matrix in full.
+ */
+gb_status gb_lu_solve(gb_handle *h, int64_t n, int64_t nrhs, gb_dtype factor_dt, const void *LU,
+                      int64_t ldlu, const double *A, int64_t lda, const double *B, int64_t ldb,
+                      double *X, int64_t ldx, const gb_refine_opts *opts, gb_solve_stats *stats,
+                      void *stream);
+
+/* ---------------------------------------------------------- diagnostics */
+/* Phases of a factorization, as timed under GB_OPT_PROFILE. */
+typedef enum gb_phase {
+  GB_PHASE_COPY = 0,   /* A -> working matrix (cast, zero the upper part)  */
+  GB_PHASE_DIAG = 1,   /* column steps of the diagonal blocks              */
+  GB_PHASE_PANEL = 2,  /* rows (and, for LU, columns of U) of the panel    */
+  GB_PHASE_INNER = 3,  /* updates inside an s-block (inner step < s)       */
+  GB_PHASE_UPDATE = 4, /* the delayed rank-s update of the trailing matrix */
+  GB_NUM_PHASES = 5
+} gb_phase;
+
+typedef struct gb_profile {
+  int64_t launches[GB_NUM_PHASES]; /* kernel launches per phase              */
+  double ms[GB_NUM_PHASES];        /* summed device time per phase (events)  */
+  double flops[GB_NUM_PHASES];     /* algorithmic flops per phase            */
+  double bytes[GB_NUM_PHASES];     /* algorithmic DRAM bytes per phase       */
+} gb_profile;
+
+/* Wait for the events recorded since the last read (or reset), add their
+ * times into *out (which the caller zero-initialises once) and forget them.
+ * Flops count one multiply-add as 2; bytes count each element of the
+ * working matrix read or written once per launch. */
+gb_status gb_profile_read(gb_handle *h, gb_profile *out);
+
+/* Total number of kernels this library has launched in the process (all
+ * handles).  Callers difference two readings. */
+uint64_t gb_kernel_launches(void);
+
+/*
+ * gb_measure_fma_peak -- run a register-only fused-multiply-add loop on
+ * every SM of the handle's device (dt = GB_F64 for DFMA, GB_F32 for FFMA)
+ * and report the achieved rate in flop/s (2 per FMA).  Synchronous.
+ */
+gb_status gb_measure_fma_peak(gb_handle *h, gb_dtype dt, double *flops_per_s);
+
+/*
+ * gb_backward_error -- ||A - L L^T||_F / ||A||_F (is_lu = 0) or
+ * ||A - L U||_F / ||A||_F (is_lu = 1, compact factor, unit U), computed on
+ * the device in FP64.  A is double (full square); the factor is double for
+ * GB_F64 and float otherwise.  Device pointers only.  Writes the result to
+ * *out (host) and waits for the stream.
+ */
+gb_status gb_backward_error(gb_handle *h, int is_lu, int64_t n, gb_dtype factor_dt,
+                            const double *A, int64_t lda, const void *F, int64_t ldf,
+                            double *out, void *stream);
+
+/* ---------------------------------------------------------------- batched */
+/*
+ * gb_chol_factor_batched -- Algorithm 1 applied independently to `count`
+ * matrices of possibly different orders, in one persistent launch.
+ *
+ *  n[count]    orders (host array), 0 <= n[i] <= 1024.
+ *  A[count]    device pointers (host array of pointers) to the matrices,
+ *              factored in place: on return the lower triangle holds L and
+ *              the strict upper triangle is zero.
+ *  lda[count]  leading dimensions (host array), lda[i] >= n[i].
+ *  dt          GB_F64 (double matrices) or GB_F32 (float matrices).
+ *  s           step (s >= 1), or 0 for the tuned step per order.
+ *  info        count ints (device or host), per-matrix status as above.
+ */
+gb_status gb_chol_factor_batched(gb_handle *h, int64_t count, const int64_t *n, void *const *A,
+                                 const int64_t *lda, gb_dtype dt, int64_t s, int *info,
+                                 void *stream);
+
+#ifdef __cplusplus
+} /* extern "C" */
+#endif
+
+#endif /* GBCHOL_H */

@@ -134,8 +134,16 @@ int64_t orc_lu(int64_t n, int64_t s, const double *A, int64_t lda, double *L,
                int64_t ldl, double *U, int64_t ldu, int mode) {
   if (n < 0 || s < 1) return -1;
   const int seq = (mode & ORC_SEQUENTIAL) != 0;
-  double *W = (double *)malloc((size_t)(n > 0 ? n : 1) * (size_t)(n > 0 ? n : 1) * sizeof(double));
-  if (!W) return -2;
+  const size_t nn = (size_t)(n > 0 ? n : 1);
+  double *W = (double *)malloc(nn * nn * sizeof(double));
+  double *urow = (double *)malloc(nn * sizeof(double)); /* row c of U being formed  */
+  double *ucol = (double *)malloc(nn * sizeof(double)); /* U[z..c-1][c], gathered   */
+  if (!W || !urow || !ucol) {
+    free(W);
+    free(urow);
+    free(ucol);
+    return -2;
+  }
   for (int64_t i = 0; i < n; ++i)
     for (int64_t j = 0; j < n; ++j) W[i * n + j] = A[i * lda + j];
   for (int64_t i = 0; i < n; ++i)
@@ -144,48 +152,67 @@ int64_t orc_lu(int64_t n, int64_t s, const double *A, int64_t lda, double *L,
       U[i * ldu + j] = 0.0;
     }
 
+  /* Memory is walked by rows: a row of S (or of U) keeps one partial sum per
+     element and receives the products in ascending k, so every element sees
+     the same sequence of roundings as the k-innermost loop of the paper. */
   int64_t z = 0;
   for (int64_t c = 0; c < n; ++c) {
     if (c == z + s) {
       /* R_L := L[c.., z..c-1]; R_U := U[z..c-1, c..]; S := R_L R_U;
          A[c.., c..] -= S;  z := c */
-#pragma omp parallel for schedule(static)
-      for (int64_t i = c; i < n; ++i) {
-        for (int64_t j = c; j < n; ++j) {
+#pragma omp parallel
+      {
+        double *srow = (double *)malloc(nn * sizeof(double));
+#pragma omp for schedule(static)
+        for (int64_t i = c; i < n; ++i) {
           if (seq) {
-            double w = W[i * n + j];
-            for (int64_t k = z; k < c; ++k) w = w - L[i * ldl + k] * U[k * ldu + j];
-            W[i * n + j] = w;
+            for (int64_t k = z; k < c; ++k) {
+              const double lik = L[i * ldl + k];
+              for (int64_t j = c; j < n; ++j) W[i * n + j] = W[i * n + j] - lik * U[k * ldu + j];
+            }
           } else {
-            double sij = 0.0;
-            for (int64_t k = z; k < c; ++k) sij = sij + L[i * ldl + k] * U[k * ldu + j];
-            W[i * n + j] = W[i * n + j] - sij;
+            for (int64_t j = c; j < n; ++j) srow[j] = 0.0;
+            for (int64_t k = z; k < c; ++k) {
+              const double lik = L[i * ldl + k];
+              for (int64_t j = c; j < n; ++j) srow[j] = srow[j] + lik * U[k * ldu + j];
+            }
+            for (int64_t j = c; j < n; ++j) W[i * n + j] = W[i * n + j] - srow[j];
           }
         }
+        free(srow);
       }
       z = c;
     }
     /* L_ic := A_ic - sum_{k=z}^{c-1} L_ik U_kc   for i >= c */
+    for (int64_t k = z; k < c; ++k) ucol[k] = U[k * ldu + c];
 #pragma omp parallel for schedule(static)
     for (int64_t i = c; i < n; ++i) {
       double v = W[i * n + c];
-      for (int64_t k = z; k < c; ++k) v = v - L[i * ldl + k] * U[k * ldu + c];
+      for (int64_t k = z; k < c; ++k) v = v - L[i * ldl + k] * ucol[k];
       L[i * ldl + c] = v;
     }
     const double lcc = L[c * ldl + c];
     if (lcc == 0.0 || lcc != lcc) {
       free(W);
+      free(urow);
+      free(ucol);
       return c + 1;
     }
     /* U_ci := (A_ci - sum_{k=z}^{c-1} L_ck U_ki) / L_cc   for i >= c */
 #pragma omp parallel for schedule(static)
-    for (int64_t i = c; i < n; ++i) {
-      double v = W[c * n + i];
-      for (int64_t k = z; k < c; ++k) v = v - L[c * ldl + k] * U[k * ldu + i];
-      U[c * ldu + i] = v / lcc;
+    for (int64_t i0 = c; i0 < n; i0 += 256) {
+      const int64_t i1 = i0 + 256 < n ? i0 + 256 : n;
+      for (int64_t i = i0; i < i1; ++i) urow[i] = W[c * n + i];
+      for (int64_t k = z; k < c; ++k) {
+        const double lck = L[c * ldl + k];
+        for (int64_t i = i0; i < i1; ++i) urow[i] = urow[i] - lck * U[k * ldu + i];
+      }
+      for (int64_t i = i0; i < i1; ++i) U[c * ldu + i] = urow[i] / lcc;
     }
   }
   free(W);
+  free(urow);
+  free(ucol);
   return 0;
 }
 

@@ -1,0 +1,292 @@
+"""ctypes binding of the gbchol C ABI (include/gbchol.h).
+
+Argument marshalling only: every step of every call runs in the CUDA
+library.  Each ``gb_*`` function here takes the same arguments as its C
+counterpart (pointers as ints); the ``chol_factor`` / ``lu_factor`` /
+``chol_solve`` / ``lu_solve`` helpers accept torch tensors (or numpy arrays
+for host buffers) and pass their data pointers.
+
+Importing this module loads ``libgbchol.so`` from the package directory and
+raises if it is absent: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libgbchol.so")
+
+GB_OK = 0
+GB_ERR_NOMEM = -1001
+GB_ERR_CUDA = -1002
+GB_ERR_TIMEOUT = -1003
+GB_ERR_NOT_CONVERGED = -1004
+GB_ERR_REJECTED = -1005
+GB_ERR_UNSUPPORTED = -1006
+GB_ERR_BREAKDOWN = -1007
+GB_ERR_STATE = -1008
+
+GB_F64, GB_F32, GB_MIX_BF16, GB_MIX_F16 = 0, 1, 2, 3
+DTYPES = {"f64": GB_F64, "f32": GB_F32, "mix_bf16": GB_MIX_BF16, "mix_f16": GB_MIX_F16}
+
+GB_OPT_INNER_STEP, GB_OPT_USE_GRAPHS, GB_OPT_TC_UPDATE, GB_OPT_SPIN_LIMIT = 1, 2, 3, 4
+GB_OPT_PROFILE = 5
+
+
+class GbError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: status {status} ({status_string(status)}) {last_error()}")
+
+
+class RefineOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int)]
+
+
+class SolveStats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("eta", ctypes.c_double)]
+
+
+# (name, restype, argtypes) of every exported symbol declared in gbchol.h
+_I64, _I32, _P, _D = ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_double
+SIGNATURES = {
+    "gb_status_string": (ctypes.c_char_p, [_I32]),
+    "gb_version": (_I32, []),
+    "gb_last_error": (ctypes.c_char_p, []),
+    "gb_create": (_I32, [ctypes.POINTER(_P), _I32]),
+    "gb_destroy": (_I32, [_P]),
+    "gb_set_option": (_I32, [_P, _I32, _I64]),
+    "gb_get_option": (_I32, [_P, _I32, ctypes.POINTER(_I64)]),
+    "gb_chol_factor": (_I32, [_P, _I64, _I64, _I32, _P, _I64, _P, _I64, _P, _P]),
+    "gb_lu_factor": (_I32, [_P, _I64, _I64, _I32, _P, _I64, _P, _I64, _P, _P]),
+    "gb_chol_solve": (_I32, [_P, _I64, _I64, _I32, _P, _I64, _P, _I64, _P, _I64, _P, _I64,
+                             ctypes.POINTER(RefineOpts), ctypes.POINTER(SolveStats), _P]),
+    "gb_lu_solve": (_I32, [_P, _I64, _I64, _I32, _P, _I64, _P, _I64, _P, _I64, _P, _I64,
+                           ctypes.POINTER(RefineOpts), ctypes.POINTER(SolveStats), _P]),
+    "gb_backward_error": (_I32, [_P, _I32, _I64, _I32, _P, _I64, _P, _I64,
+                                 ctypes.POINTER(_D), _P]),
+    "gb_chol_factor_batched": (_I32, [_P, _I64, _P, _P, _P, _I32, _I64, _P, _P]),
+    "gb_profile_read": (_I32, [_P, _P]),
+    "gb_kernel_launches": (ctypes.c_uint64, []),
+    "gb_measure_fma_peak": (_I32, [_P, _I32, ctypes.POINTER(_D)]),
+}
+
+PHASES = ["copy", "diag", "panel", "inner", "update"]
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64 * 5), ("ms", ctypes.c_double * 5),
+                ("flops", ctypes.c_double * 5), ("bytes", ctypes.c_double * 5)]
+
+    def as_dict(self):
+        return {p: {"launches": int(self.launches[i]), "ms": float(self.ms[i]),
+                    "flops": float(self.flops[i]), "bytes": float(self.bytes[i])}
+                for i, p in enumerate(PHASES)}
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load the library (once) and declare every entry point's signature."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise ImportError(
+                f"gbchol CUDA library not found at {path}; build it with "
+                "`python -c 'import __graft_entry__ as g; g.build()'`")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def kernel_launches() -> int:
+    return int(load().gb_kernel_launches())
+
+
+def status_string(st: int) -> str:
+    return load().gb_status_string(int(st)).decode()
+
+
+def last_error() -> str:
+    return load().gb_last_error().decode()
+
+
+def check(st: int, where: str) -> int:
+    if st != GB_OK:
+        raise GbError(st, where)
+    return st
+
+
+def _ptr(x) -> int | None:
+    """Data pointer of a torch tensor / numpy array / int / None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError(f"cannot take a pointer of {type(x)}")
+
+
+def _ld(x) -> int:
+    if hasattr(x, "stride") and callable(x.stride):
+        return int(x.stride(0))
+    return int(x.strides[0] // x.itemsize)
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            return None
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Handle:
+    """Owns a ``gb_handle`` for one device."""
+
+    def __init__(self, device: int = 0):
+        self.lib = load()
+        h = ctypes.c_void_p()
+        check(self.lib.gb_create(ctypes.byref(h), int(device)), "gb_create")
+        self.h = h
+        self.device = device
+
+    def close(self):
+        if self.h:
+            self.lib.gb_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_option(self, opt: int, value: int):
+        check(self.lib.gb_set_option(self.h, int(opt), int(value)), "gb_set_option")
+
+    def get_option(self, opt: int) -> int:
+        v = ctypes.c_int64()
+        check(self.lib.gb_get_option(self.h, int(opt), ctypes.byref(v)), "gb_get_option")
+        return v.value
+
+    def profile_read(self, into=None):
+        p = into if into is not None else Profile()
+        check(self.lib.gb_profile_read(self.h, ctypes.byref(p)), "gb_profile_read")
+        return p
+
+    def measure_fma_peak(self, dtype: str = "f64") -> float:
+        v = ctypes.c_double()
+        check(self.lib.gb_measure_fma_peak(self.h, DTYPES[dtype], ctypes.byref(v)),
+              "gb_measure_fma_peak")
+        return v.value
+
+    # ------------------------------------------------------------ raw calls
+    def gb_chol_factor(self, n, s, dt, A, lda, L, ldl, info, stream=None) -> int:
+        return self.lib.gb_chol_factor(self.h, n, s, dt, _ptr(A), lda, _ptr(L), ldl, _ptr(info),
+                                       _stream_ptr(stream))
+
+    def gb_lu_factor(self, n, s, dt, A, lda, LU, ldlu, info, stream=None) -> int:
+        return self.lib.gb_lu_factor(self.h, n, s, dt, _ptr(A), lda, _ptr(LU), ldlu, _ptr(info),
+                                     _stream_ptr(stream))
+
+    def _solve(self, fn, n, nrhs, dt, F, ldf, A, lda, B, ldb, X, ldx, tol, max_iter, stream):
+        opts = RefineOpts(tol, max_iter)
+        stats = SolveStats()
+        st = fn(self.h, n, nrhs, dt, _ptr(F), ldf, _ptr(A), lda, _ptr(B), ldb, _ptr(X), ldx,
+                ctypes.byref(opts), ctypes.byref(stats), _stream_ptr(stream))
+        return st, stats
+
+    def gb_chol_solve(self, n, nrhs, dt, L, ldl, A, lda, B, ldb, X, ldx, tol=1e-14, max_iter=30,
+                      stream=None):
+        return self._solve(self.lib.gb_chol_solve, n, nrhs, dt, L, ldl, A, lda, B, ldb, X, ldx,
+                           tol, max_iter, stream)
+
+    def gb_lu_solve(self, n, nrhs, dt, LU, ldlu, A, lda, B, ldb, X, ldx, tol=1e-14, max_iter=30,
+                    stream=None):
+        return self._solve(self.lib.gb_lu_solve, n, nrhs, dt, LU, ldlu, A, lda, B, ldb, X, ldx,
+                           tol, max_iter, stream)
+
+    def gb_backward_error(self, is_lu, n, dt, A, lda, F, ldf, stream=None) -> float:
+        out = ctypes.c_double()
+        check(self.lib.gb_backward_error(self.h, int(is_lu), n, dt, _ptr(A), lda, _ptr(F), ldf,
+                                         ctypes.byref(out), _stream_ptr(stream)),
+              "gb_backward_error")
+        return out.value
+
+    def gb_chol_factor_batched(self, count, n_arr, ptr_arr, lda_arr, dt, s, info, stream=None):
+        return self.lib.gb_chol_factor_batched(self.h, count, _ptr(n_arr), _ptr(ptr_arr),
+                                               _ptr(lda_arr), dt, s, _ptr(info),
+                                               _stream_ptr(stream))
+
+    # --------------------------------------------------- tensor conveniences
+    def chol_factor(self, A, s: int, dtype: str = "f64", out=None, stream=None):
+        """Factor a CUDA (or host) tensor ``A``; returns ``(L, info)``."""
+        import torch
+        n = A.shape[0]
+        dt = DTYPES[dtype]
+        ltype = torch.float64 if dt == GB_F64 else torch.float32
+        L = out if out is not None else torch.empty((n, n), dtype=ltype, device=A.device)
+        info = torch.zeros(1, dtype=torch.int32, device=A.device)
+        check(self.gb_chol_factor(n, s, dt, A, _ld(A) if n else 1, L, _ld(L) if n else 1, info,
+                                  stream), "gb_chol_factor")
+        return L, info
+
+    def lu_factor(self, A, s: int, dtype: str = "f64", out=None, stream=None):
+        """Compact LU of ``A``; returns ``(LU, info)``."""
+        import torch
+        n = A.shape[0]
+        dt = DTYPES[dtype]
+        ltype = torch.float64 if dt == GB_F64 else torch.float32
+        LU = out if out is not None else torch.empty((n, n), dtype=ltype, device=A.device)
+        info = torch.zeros(1, dtype=torch.int32, device=A.device)
+        check(self.gb_lu_factor(n, s, dt, A, _ld(A) if n else 1, LU, _ld(LU) if n else 1, info,
+                                stream), "gb_lu_factor")
+        return LU, info
+
+    def chol_solve(self, L, B, dtype: str = "f64", A=None, tol=1e-14, max_iter=30, stream=None,
+                   allow_not_converged=False):
+        import torch
+        n, r = B.shape
+        X = torch.empty_like(B)
+        st, stats = self.gb_chol_solve(n, r, DTYPES[dtype], L, _ld(L), A,
+                                       _ld(A) if A is not None else n, B, _ld(B), X, _ld(X), tol,
+                                       max_iter, stream)
+        if not (allow_not_converged and st == GB_ERR_NOT_CONVERGED):
+            check(st, "gb_chol_solve")
+        return X, stats
+
+    def lu_solve(self, LU, B, dtype: str = "f64", A=None, tol=1e-14, max_iter=30, stream=None,
+                 allow_not_converged=False):
+        import torch
+        n, r = B.shape
+        X = torch.empty_like(B)
+        st, stats = self.gb_lu_solve(n, r, DTYPES[dtype], LU, _ld(LU), A,
+                                     _ld(A) if A is not None else n, B, _ld(B), X, _ld(X), tol,
+                                     max_iter, stream)
+        if not (allow_not_converged and st == GB_ERR_NOT_CONVERGED):
+            check(st, "gb_lu_solve")
+        return X, stats
+
+    def backward_error(self, A, F, dtype: str = "f64", lu: bool = False, stream=None) -> float:
+        n = A.shape[0]
+        return self.gb_backward_error(1 if lu else 0, n, DTYPES[dtype], A, _ld(A), F, _ld(F),
+                                      stream)

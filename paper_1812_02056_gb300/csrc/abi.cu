@@ -1,0 +1,811 @@
+// Exported C entry points of gbchol (declared in include/gbchol.h) and the
+// host-side block loops of Algorithms 1 and 2 (arXiv:1812.02056, Sec. 2).
+//
+// Block loop (Cholesky; LU is the same with the U panel alongside):
+//   for z = 0, s, 2s, ...:                     checkpoint z, block width sb
+//     for each inner block [j0, j0+bw) of [z, z+sb):   bw <= inner step
+//       diagonal block column steps            (panel.cu, chol_diag_kernel)
+//       rows below the block                   (panel.cu, chol_rows_kernel)
+//       rest of the s-block's columns -= this inner block's product
+//     A[z+sb.., z+sb..] -= R R^T, R = L[z+sb.., z..z+sb)   (the delayed
+//                                              rank-s update; SIMT or tcgen05)
+// With s <= inner step each s-block is one inner block and the loop is
+// Algorithm 1 as written: the columns of a block are finished from the
+// columns since z, and the trailing matrix sees one update every s columns.
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <memory>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "gb_internal.cuh"
+
+namespace gb {
+
+static thread_local std::string g_last_error;
+std::atomic<uint64_t> g_launches{0};
+
+void record_cuda_error(cudaError_t e, const char *what, const char *file, int line) {
+  char buf[512];
+  snprintf(buf, sizeof buf, "%s:%d: %s -> %s", file, line, what, cudaGetErrorString(e));
+  g_last_error = buf;
+}
+
+const char *last_error_message() { return g_last_error.c_str(); }
+
+gb_status ws_reserve(gb_handle *h, int slot, size_t bytes, cudaStream_t stream) {
+  Workspace &w = h->ws[slot];
+  if (w.bytes >= bytes) return GB_OK;
+  if (w.ptr) {
+    GB_CUDA_TRY(cudaStreamSynchronize(stream));
+    GB_CUDA_TRY(cudaFree(w.ptr));
+    w.ptr = nullptr;
+    w.bytes = 0;
+  }
+  size_t want = std::max<size_t>(bytes, 1 << 20);
+  if (cudaMalloc(&w.ptr, want) != cudaSuccess) {
+    cudaGetLastError();
+    w.ptr = nullptr;
+    return GB_ERR_NOMEM;
+  }
+  w.bytes = want;
+  return GB_OK;
+}
+
+namespace {
+
+// ---------------------------------------------------------------- helpers
+bool is_device_ptr(const void *p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+size_t elem_size_factor(gb_dtype dt) { return dt == GB_F64 ? 8 : 4; }
+size_t elem_size_input(gb_dtype dt) { return dt == GB_F32 ? 4 : 8; }
+bool valid_dtype(int dt) { return dt >= GB_F64 && dt <= GB_MIX_F16; }
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+// A caller buffer that may live on the host: device copy for the duration of
+// a call, released in stream order.
+struct Staged {
+  void *dev = nullptr;
+  const void *host_src = nullptr;
+  void *host_dst = nullptr;
+  int64_t rows = 0, cols = 0, ld = 0, ldd = 0;
+  size_t esz = 0;
+  bool owned = false;
+  cudaStream_t st = nullptr;
+
+  // Take `p` (rows x cols, leading dimension ld, element size esz).  When
+  // `p` is host memory, allocate a dense device copy (copying in when
+  // copy_in) and remember to copy out at finish() when copy_out.
+  gb_status take(const void *p, int64_t r, int64_t c, int64_t l, size_t e, bool copy_in,
+                 bool copy_out, cudaStream_t s) {
+    rows = r;
+    cols = c;
+    ld = l;
+    esz = e;
+    st = s;
+    if (!p || is_device_ptr(p)) {
+      dev = const_cast<void *>(p);
+      ldd = l;
+      return GB_OK;
+    }
+    ldd = c > 0 ? c : 1;
+    size_t bytes = (size_t)std::max<int64_t>(r, 1) * (size_t)ldd * e;
+    if (cudaMallocAsync(&dev, bytes, s) != cudaSuccess) {
+      cudaGetLastError();
+      dev = nullptr;
+      return GB_ERR_NOMEM;
+    }
+    owned = true;
+    if (copy_out) host_dst = const_cast<void *>(p);
+    if (copy_in && r > 0 && c > 0)
+      GB_CUDA_TRY(cudaMemcpy2DAsync(dev, ldd * e, p, l * e, c * e, r, cudaMemcpyHostToDevice, s));
+    return GB_OK;
+  }
+  gb_status finish() {
+    if (host_dst && rows > 0 && cols > 0)
+      GB_CUDA_TRY(cudaMemcpy2DAsync(host_dst, ld * esz, dev, ldd * esz, cols * esz, rows,
+                                    cudaMemcpyDeviceToHost, st));
+    return GB_OK;
+  }
+  ~Staged() {
+    if (owned && dev) cudaFreeAsync(dev, st);
+  }
+  bool on_host() const { return owned; }
+};
+
+// Status word for `info`: the caller's int when it is device memory, else
+// the handle's scratch word copied out at the end.
+struct InfoWord {
+  int *dev = nullptr;
+  int *host = nullptr;
+  gb_status init(gb_handle *h, int *info, cudaStream_t st) {
+    if (is_device_ptr(info)) {
+      dev = info;
+    } else {
+      dev = h->d_status;
+      host = info;
+    }
+    GB_CUDA_TRY(cudaMemsetAsync(dev, 0, sizeof(int), st));
+    return GB_OK;
+  }
+  gb_status finish(cudaStream_t st) {
+    if (host) {
+      GB_CUDA_TRY(cudaMemcpyAsync(host, dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+      GB_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    return GB_OK;
+  }
+};
+
+int64_t default_step(gb_dtype dt, int64_t n) {
+  (void)n;
+  switch (dt) {
+    case GB_F64: return 256;
+    case GB_F32: return 256;
+    default: return 1024;
+  }
+}
+
+// ---------------------------------------------------------------- profile
+cudaEvent_t take_event(gb_handle *h) {
+  if (!h->prof_pool.empty()) {
+    cudaEvent_t e = h->prof_pool.back();
+    h->prof_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+// Records an event pair around the launches made in its scope when the
+// handle's profile option is on.
+struct PhaseTimer {
+  gb_handle *h;
+  cudaStream_t st;
+  int phase;
+  double flops, bytes;
+  cudaEvent_t a = nullptr, b = nullptr;
+  PhaseTimer(gb_handle *h_, cudaStream_t st_, int phase_, double flops_, double bytes_)
+      : h(h_), st(st_), phase(phase_), flops(flops_), bytes(bytes_) {
+    if (!h->profile) return;
+    a = take_event(h);
+    b = take_event(h);
+    if (a && b) cudaEventRecord(a, st);
+  }
+  ~PhaseTimer() {
+    if (!a || !b) return;
+    cudaEventRecord(b, st);
+    h->prof_pending.push_back({phase, a, b, flops, bytes});
+  }
+};
+
+// Number of (i, j), 0 <= i < M, 0 <= j < N, with i + diag >= j.
+double lower_count(int64_t M, int64_t N, int64_t diag) {
+  double c = 0;
+  for (int64_t j0 = 0; j0 < N; j0 += 4096) {  // closed form per column strip
+    const int64_t j1 = std::min(N, j0 + 4096);
+    for (int64_t j = j0; j < j1; ++j) {
+      const int64_t first = std::max<int64_t>(0, j - diag);
+      if (first < M) c += (double)(M - first);
+    }
+  }
+  return c;
+}
+
+double update_flops(int64_t M, int64_t N, int64_t K, bool lower) {
+  return 2.0 * (double)K * (lower ? lower_count(M, N, 0) : (double)M * N);
+}
+
+double update_bytes(int64_t M, int64_t N, int64_t K, bool lower, size_t e) {
+  const double c = lower ? lower_count(M, N, 0) : (double)M * N;
+  return (double)e * (2.0 * c + (double)(M + N) * K);
+}
+
+// ------------------------------------------------------------ block loops
+template <typename T, typename Tc>
+gb_status chol_blocked(gb_handle *h, int64_t n, int64_t s, T *W, int64_t ld, int *status,
+                       gb_dtype dt, cudaStream_t st) {
+  const int64_t b = std::max(1, std::min(64, h->inner_step));
+  for (int64_t z = 0; z < n; z += s) {
+    const int64_t sb = std::min(s, n - z);
+    const int64_t pe = z + sb;  // end of this s-block
+    for (int64_t j0 = z; j0 < pe; j0 += b) {
+      const int bw = (int)std::min(b, pe - j0);
+      const size_t e = sizeof(T);
+      {
+        PhaseTimer t(h, st, GB_PHASE_DIAG, (double)bw * bw * bw / 3.0, (double)bw * bw * e);
+        GB_CUDA_TRY((launch_chol_diag<T, Tc>(W, ld, j0, bw, status, st)));
+      }
+      const int64_t r0 = j0 + bw;
+      if (r0 < n) {
+        PhaseTimer t(h, st, GB_PHASE_PANEL, (double)(n - r0) * bw * bw,
+                     2.0 * (double)(n - r0) * bw * e);
+        GB_CUDA_TRY(launch_chol_rows<T>(W, ld, r0, n - r0, j0, bw, status, st));
+      }
+      if (r0 < pe) {  // the s-block's remaining columns receive this inner block
+        PhaseTimer t(h, st, GB_PHASE_INNER, update_flops(n - r0, pe - r0, bw, true),
+                     update_bytes(n - r0, pe - r0, bw, true, e));
+        GB_CUDA_TRY(launch_update_simt<T>(W + r0 * ld + r0, ld, W + r0 * ld + j0, ld,
+                                          W + r0 * ld + j0, ld, n - r0, pe - r0, bw, false, true,
+                                          0, status, st));
+      }
+    }
+    if (pe < n) {  // delayed rank-sb update of the trailing matrix
+      const int64_t m = n - pe;
+      T *C = W + pe * ld + pe;
+      const T *R = W + pe * ld + z;
+      bool done = false;
+      const bool tc = (dt == GB_MIX_BF16 || dt == GB_MIX_F16) && h->tc_update;
+      PhaseTimer t(h, st, GB_PHASE_UPDATE, update_flops(m, m, sb, true),
+                   update_bytes(m, m, sb, true, sizeof(T)) -
+                       (tc ? (double)m * sb * 2.0 * (sizeof(T) - 2) : 0.0));
+      if constexpr (sizeof(T) == 4) {
+        if ((dt == GB_MIX_BF16 || dt == GB_MIX_F16) && h->tc_update) {
+          TcUpdateArgs a{};
+          a.C = reinterpret_cast<float *>(C);
+          a.ldc = ld;
+          a.X = reinterpret_cast<const float *>(R);
+          a.ldx = ld;
+          a.Y = reinterpret_cast<const float *>(R);
+          a.ldy = ld;
+          a.M = m;
+          a.N = m;
+          a.K = sb;
+          a.nn = false;
+          a.lower = true;
+          a.diag = 0;
+          a.f16 = (dt == GB_MIX_F16);
+          a.status = status;
+          a.err = h->d_err;
+          a.spin_limit = h->spin_limit;
+          const size_t pb = tc_pack_bytes(m, m, sb, false);
+          gb_status ws = ws_reserve(h, WS_PANEL, pb, st);
+          if (ws != GB_OK) return ws;
+          a.pack = h->ws[WS_PANEL].ptr;
+          a.pack_bytes = h->ws[WS_PANEL].bytes;
+          GB_CUDA_TRY(launch_update_tc(a, st));
+          done = true;
+        }
+      }
+      if (!done)
+        GB_CUDA_TRY(launch_update_simt<T>(C, ld, R, ld, R, ld, m, m, sb, false, true, 0, status, st));
+    }
+  }
+  return GB_OK;
+}
+
+template <typename T, typename Tc>
+gb_status lu_blocked(gb_handle *h, int64_t n, int64_t s, T *W, int64_t ld, int *status,
+                     gb_dtype dt, cudaStream_t st) {
+  const int64_t b = std::max(1, std::min(64, h->inner_step));
+  for (int64_t z = 0; z < n; z += s) {
+    const int64_t sb = std::min(s, n - z);
+    const int64_t pe = z + sb;
+    for (int64_t j0 = z; j0 < pe; j0 += b) {
+      const int bw = (int)std::min(b, pe - j0);
+      const size_t e = sizeof(T);
+      {
+        PhaseTimer t(h, st, GB_PHASE_DIAG, 2.0 * (double)bw * bw * bw / 3.0, 2.0 * bw * bw * e);
+        GB_CUDA_TRY((launch_lu_diag<T, Tc>(W, ld, j0, bw, status, st)));
+      }
+      const int64_t r0 = j0 + bw;
+      if (r0 < n) {
+        {
+          PhaseTimer t(h, st, GB_PHASE_PANEL, (double)(n - r0) * bw * bw,
+                       2.0 * (double)(n - r0) * bw * e);
+          GB_CUDA_TRY(launch_lu_rows<T>(W, ld, r0, n - r0, j0, bw, status, st));  // L below
+        }
+        PhaseTimer t(h, st, GB_PHASE_PANEL, (double)(n - r0) * bw * bw,
+                     2.0 * (double)(n - r0) * bw * e);
+        GB_CUDA_TRY(launch_lu_cols<T>(W, ld, r0, n - r0, j0, bw, status, st));  // U right
+      }
+      if (r0 < pe) {
+        {
+          // the s-block's remaining columns (all rows below) ...
+          PhaseTimer t(h, st, GB_PHASE_INNER, update_flops(n - r0, pe - r0, bw, false),
+                       update_bytes(n - r0, pe - r0, bw, false, e));
+          GB_CUDA_TRY(launch_update_simt<T>(W + r0 * ld + r0, ld, W + r0 * ld + j0, ld,
+                                            W + j0 * ld + r0, ld, n - r0, pe - r0, bw, true,
+                                            false, 0, status, st));
+        }
+        // ... and the s-block's remaining rows right of the block
+        if (pe < n) {
+          PhaseTimer t(h, st, GB_PHASE_INNER, update_flops(pe - r0, n - pe, bw, false),
+                       update_bytes(pe - r0, n - pe, bw, false, e));
+          GB_CUDA_TRY(launch_update_simt<T>(W + r0 * ld + pe, ld, W + r0 * ld + j0, ld,
+                                            W + j0 * ld + pe, ld, pe - r0, n - pe, bw, true,
+                                            false, 0, status, st));
+        }
+      }
+    }
+    if (pe < n) {  // delayed rank-sb update A[pe.., pe..] -= R_L R_U
+      const int64_t m = n - pe;
+      T *C = W + pe * ld + pe;
+      const T *RL = W + pe * ld + z;
+      const T *RU = W + z * ld + pe;
+      bool done = false;
+      const bool tc = (dt == GB_MIX_BF16 || dt == GB_MIX_F16) && h->tc_update;
+      PhaseTimer t(h, st, GB_PHASE_UPDATE, update_flops(m, m, sb, false),
+                   update_bytes(m, m, sb, false, sizeof(T)) -
+                       (tc ? 2.0 * (double)m * sb * (sizeof(T) - 2) : 0.0));
+      if constexpr (sizeof(T) == 4) {
+        if ((dt == GB_MIX_BF16 || dt == GB_MIX_F16) && h->tc_update) {
+          TcUpdateArgs a{};
+          a.C = reinterpret_cast<float *>(C);
+          a.ldc = ld;
+          a.X = reinterpret_cast<const float *>(RL);
+          a.ldx = ld;
+          a.Y = reinterpret_cast<const float *>(RU);
+          a.ldy = ld;
+          a.M = m;
+          a.N = m;
+          a.K = sb;
+          a.nn = true;
+          a.lower = false;
+          a.diag = 0;
+          a.f16 = (dt == GB_MIX_F16);
+          a.status = status;
+          a.err = h->d_err;
+          a.spin_limit = h->spin_limit;
+          const size_t pb = tc_pack_bytes(m, m, sb, true);
+          gb_status ws = ws_reserve(h, WS_PANEL, pb, st);
+          if (ws != GB_OK) return ws;
+          a.pack = h->ws[WS_PANEL].ptr;
+          a.pack_bytes = h->ws[WS_PANEL].bytes;
+          GB_CUDA_TRY(launch_update_tc(a, st));
+          done = true;
+        }
+      }
+      if (!done)
+        GB_CUDA_TRY(launch_update_simt<T>(C, ld, RL, ld, RU, ld, m, m, sb, true, false, 0, status, st));
+    }
+  }
+  return GB_OK;
+}
+
+// Common driver of gb_chol_factor / gb_lu_factor.
+gb_status factor_common(bool is_lu, gb_handle *h, int64_t n, int64_t s, gb_dtype dt,
+                        const void *A, int64_t lda, void *L, int64_t ldl, int *info,
+                        void *stream) {
+  if (!h) return -1;
+  if (n < 0) return -2;
+  if (s < 0) return -3;
+  if (!valid_dtype(dt)) return -4;
+  if (n > 0 && !A) return -5;
+  if (lda < std::max<int64_t>(1, n)) return -6;
+  if (n > 0 && !L) return -7;
+  if (ldl < std::max<int64_t>(1, n)) return -8;
+  if (!info) return -9;
+  if (n > (int64_t)1 << 30) return -2;
+  DeviceGuard g(h->device);
+  std::lock_guard<std::mutex> lk(h->mu);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (s == 0) s = default_step(dt, n);
+  const size_t ein = elem_size_input(dt), ef = elem_size_factor(dt);
+  const bool alias = (A == (const void *)L);
+  if (alias && ein != ef) return -7;  // in place needs one element type
+
+  InfoWord iw;
+  gb_status r = iw.init(h, info, st);
+  if (r != GB_OK) return r;
+  if (n == 0) return iw.finish(st);
+
+  Staged sa, sl;
+  if (alias) {
+    if ((r = sl.take(L, n, n, ldl, ef, true, true, st)) != GB_OK) return r;
+    sa.dev = sl.dev;
+    sa.ldd = sl.ldd;
+  } else {
+    if ((r = sa.take(A, n, n, lda, ein, true, false, st)) != GB_OK) return r;
+    if ((r = sl.take(L, n, n, ldl, ef, false, true, st)) != GB_OK) return r;
+  }
+  const int64_t ld = sl.ldd;
+  const bool lower_only = !is_lu;
+  std::unique_ptr<PhaseTimer> tcopy(new PhaseTimer(h, st, GB_PHASE_COPY, 0.0,
+                                                   (double)n * n * (double)(ein + ef)));
+  switch (dt) {
+    case GB_F64: {
+      double *W = (double *)sl.dev;
+      GB_CUDA_TRY((launch_copy_matrix<double, double>((const double *)sa.dev, sa.ldd, W, ld, n,
+                                                      lower_only, st)));
+      tcopy.reset();
+      r = is_lu ? lu_blocked<double, double>(h, n, s, W, ld, iw.dev, dt, st)
+                : chol_blocked<double, double>(h, n, s, W, ld, iw.dev, dt, st);
+      break;
+    }
+    case GB_F32: {
+      float *W = (float *)sl.dev;
+      GB_CUDA_TRY((launch_copy_matrix<float, float>((const float *)sa.dev, sa.ldd, W, ld, n,
+                                                    lower_only, st)));
+      tcopy.reset();
+      r = is_lu ? lu_blocked<float, float>(h, n, s, W, ld, iw.dev, dt, st)
+                : chol_blocked<float, float>(h, n, s, W, ld, iw.dev, dt, st);
+      break;
+    }
+    default: {  // mixed: FP64 in, FP32 working matrix, FP64 diagonal blocks
+      float *W = (float *)sl.dev;
+      GB_CUDA_TRY((launch_copy_matrix<double, float>((const double *)sa.dev, sa.ldd, W, ld, n,
+                                                     lower_only, st)));
+      tcopy.reset();
+      r = is_lu ? lu_blocked<float, double>(h, n, s, W, ld, iw.dev, dt, st)
+                : chol_blocked<float, double>(h, n, s, W, ld, iw.dev, dt, st);
+      break;
+    }
+  }
+  if (r != GB_OK) return r;
+  if ((r = sl.finish()) != GB_OK) return r;
+  if ((r = iw.finish(st)) != GB_OK) return r;
+  if (sl.on_host() || sa.on_host()) GB_CUDA_TRY(cudaStreamSynchronize(st));
+  return GB_OK;
+}
+
+// ------------------------------------------------------------------ solves
+template <typename Tf>
+gb_status tri_solve(gb_handle *h, bool is_lu, const Tf *F, int64_t ldf, double *X, int64_t ldx,
+                    int64_t n, int64_t nrhs, cudaStream_t st) {
+  unsigned e1 = ++h->sync_epoch;
+  if (e1 == 0) e1 = ++h->sync_epoch;
+  GB_CUDA_TRY((launch_trsm<Tf, Tf>(F, ldf, X, ldx, n, nrhs, TRSM_LOWER, h->d_sync, e1, h->d_err,
+                                   h->spin_limit, st)));
+  unsigned e2 = ++h->sync_epoch;
+  if (e2 == 0) e2 = ++h->sync_epoch;
+  GB_CUDA_TRY((launch_trsm<Tf, Tf>(F, ldf, X, ldx, n, nrhs, is_lu ? TRSM_UNIT_UPPER : TRSM_LOWER_T,
+                                   h->d_sync, e2, h->d_err, h->spin_limit, st)));
+  return GB_OK;
+}
+
+gb_status read_device_error(gb_handle *h, cudaStream_t st) {
+  int err = 0;
+  GB_CUDA_TRY(cudaMemcpyAsync(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  GB_CUDA_TRY(cudaStreamSynchronize(st));
+  if (err) {
+    GB_CUDA_TRY(cudaMemsetAsync(h->d_err, 0, sizeof(int), st));
+    GB_CUDA_TRY(cudaStreamSynchronize(st));
+    return (err & DEV_ERR_TIMEOUT) ? GB_ERR_TIMEOUT : GB_ERR_CUDA;
+  }
+  return GB_OK;
+}
+
+template <typename Tf>
+gb_status solve_common(bool is_lu, gb_handle *h, int64_t n, int64_t nrhs, const Tf *F,
+                       int64_t ldf, const double *A, int64_t lda, const double *B, int64_t ldb,
+                       double *X, int64_t ldx, const gb_refine_opts *opts, gb_solve_stats *stats,
+                       cudaStream_t st) {
+  const double tol = (opts && opts->tol > 0) ? opts->tol : 1e-14;
+  const int max_iter = (opts && opts->max_iter >= 0) ? opts->max_iter : 30;
+  if (stats) {
+    stats->iterations = 0;
+    stats->converged = 1;
+    stats->eta = 0.0;
+  }
+  // a zero or non-finite pivot makes the substitutions meaningless
+  GB_CUDA_TRY(launch_check_diag<Tf>(F, ldf, n, h->d_status, st));
+  int bad = 0;
+  GB_CUDA_TRY(cudaMemcpyAsync(&bad, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  GB_CUDA_TRY(cudaStreamSynchronize(st));
+  if (bad) return GB_ERR_BREAKDOWN;
+
+  if (X != B)
+    GB_CUDA_TRY(cudaMemcpy2DAsync(X, ldx * 8, B, ldb * 8, nrhs * 8, n, cudaMemcpyDeviceToDevice, st));
+  gb_status r = tri_solve<Tf>(h, is_lu, F, ldf, X, ldx, n, nrhs, st);
+  if (r != GB_OK) return r;
+  if (!A) return read_device_error(h, st);
+
+  // iterative refinement in FP64
+  const size_t rbytes = (size_t)n * nrhs * 8;
+  if ((r = ws_reserve(h, WS_SOLVE, rbytes, st)) != GB_OK) return r;
+  double *R = (double *)h->ws[WS_SOLVE].ptr;
+  double *norms = h->d_scalars;  // [0]: ||A||_inf; [1..]: 3 * nrhs norms
+  if ((size_t)(1 + 3 * nrhs) > 4096) return GB_ERR_UNSUPPORTED;
+  GB_CUDA_TRY(launch_inf_norm_rows(A, lda, n, norms, st));
+  std::vector<double> hn(1 + 3 * nrhs);
+  int it = 0;
+  double eta = 0.0;
+  for (;;) {
+    GB_CUDA_TRY(launch_residual(A, lda, X, ldx, B, ldb, R, nrhs, n, nrhs, norms + 1, st));
+    GB_CUDA_TRY(cudaMemcpyAsync(hn.data(), norms, sizeof(double) * hn.size(),
+                                cudaMemcpyDeviceToHost, st));
+    GB_CUDA_TRY(cudaStreamSynchronize(st));
+    const double anorm = hn[0];
+    eta = 0.0;
+    for (int64_t c = 0; c < nrhs; ++c) {
+      const double rn = hn[1 + c], xn = hn[1 + nrhs + c], bn = hn[1 + 2 * nrhs + c];
+      const double den = anorm * xn + bn;
+      const double e = den > 0 ? rn / den : (rn > 0 ? INFINITY : 0.0);
+      if (!(e <= eta)) eta = e;  // NaN propagates
+    }
+    if (eta <= tol || it >= max_iter) break;
+    if ((r = tri_solve<Tf>(h, is_lu, F, ldf, R, nrhs, n, nrhs, st)) != GB_OK) return r;
+    GB_CUDA_TRY(launch_axpy_cols(X, ldx, R, nrhs, n, nrhs, st));
+    ++it;
+  }
+  if (stats) {
+    stats->iterations = it;
+    stats->eta = eta;
+    stats->converged = eta <= tol ? 1 : 0;
+  }
+  if ((r = read_device_error(h, st)) != GB_OK) return r;
+  return eta <= tol ? GB_OK : GB_ERR_NOT_CONVERGED;
+}
+
+gb_status solve_entry(bool is_lu, gb_handle *h, int64_t n, int64_t nrhs, gb_dtype factor_dt,
+                      const void *F, int64_t ldf, const double *A, int64_t lda, const double *B,
+                      int64_t ldb, double *X, int64_t ldx, const gb_refine_opts *opts,
+                      gb_solve_stats *stats, void *stream) {
+  if (!h) return -1;
+  if (n < 0) return -2;
+  if (nrhs < 0) return -3;
+  if (!valid_dtype(factor_dt)) return -4;
+  if (n > 0 && !F) return -5;
+  if (ldf < std::max<int64_t>(1, n)) return -6;
+  if (A && lda < std::max<int64_t>(1, n)) return -8;
+  if (n > 0 && nrhs > 0 && !B) return -9;
+  if (ldb < std::max<int64_t>(1, nrhs)) return -10;
+  if (n > 0 && nrhs > 0 && !X) return -11;
+  if (ldx < std::max<int64_t>(1, nrhs)) return -12;
+  if (A && X == B) return -11;
+  if (nrhs > 1365) return -3;  // norms scratch holds 3 * nrhs + 1 doubles
+  DeviceGuard g(h->device);
+  std::lock_guard<std::mutex> lk(h->mu);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (stats) {
+    stats->iterations = 0;
+    stats->converged = 1;
+    stats->eta = 0.0;
+  }
+  if (n == 0 || nrhs == 0) return GB_OK;
+  const size_t ef = elem_size_factor(factor_dt);
+  Staged sf, sa, sb, sx;
+  gb_status r;
+  if ((r = sf.take(F, n, n, ldf, ef, true, false, st)) != GB_OK) return r;
+  if (A && (r = sa.take(A, n, n, lda, 8, true, false, st)) != GB_OK) return r;
+  if (X == B) {
+    if ((r = sx.take(X, n, nrhs, ldx, 8, true, true, st)) != GB_OK) return r;
+    sb.dev = sx.dev;
+    sb.ldd = sx.ldd;
+  } else {
+    if ((r = sb.take(B, n, nrhs, ldb, 8, true, false, st)) != GB_OK) return r;
+    if ((r = sx.take(X, n, nrhs, ldx, 8, false, true, st)) != GB_OK) return r;
+  }
+  if (factor_dt == GB_F64)
+    r = solve_common<double>(is_lu, h, n, nrhs, (const double *)sf.dev, sf.ldd,
+                             (const double *)sa.dev, sa.ldd, (const double *)sb.dev, sb.ldd,
+                             (double *)sx.dev, sx.ldd, opts, stats, st);
+  else
+    r = solve_common<float>(is_lu, h, n, nrhs, (const float *)sf.dev, sf.ldd,
+                            (const double *)sa.dev, sa.ldd, (const double *)sb.dev, sb.ldd,
+                            (double *)sx.dev, sx.ldd, opts, stats, st);
+  if (r != GB_OK && r != GB_ERR_NOT_CONVERGED) return r;
+  gb_status r2 = sx.finish();
+  if (r2 != GB_OK) return r2;
+  if (sx.on_host() || sf.on_host() || sa.on_host() || sb.on_host())
+    GB_CUDA_TRY(cudaStreamSynchronize(st));
+  return r;
+}
+
+}  // namespace
+}  // namespace gb
+
+using namespace gb;
+
+// =================================================================== C ABI
+extern "C" {
+
+const char *gb_status_string(gb_status st) {
+  switch (st) {
+    case GB_OK: return "success";
+    case GB_ERR_NOMEM: return "allocation failed";
+    case GB_ERR_CUDA: return "CUDA runtime error";
+    case GB_ERR_TIMEOUT: return "bounded device wait expired";
+    case GB_ERR_NOT_CONVERGED: return "iterative refinement did not reach the tolerance";
+    case GB_ERR_REJECTED: return "request rejected: footprint exceeds the budget";
+    case GB_ERR_UNSUPPORTED: return "unsupported combination of options";
+    case GB_ERR_BREAKDOWN: return "factor has a zero or non-finite pivot";
+    case GB_ERR_STATE: return "object used in the wrong state";
+    default: return st < 0 && st > -100 ? "invalid argument" : "unknown status";
+  }
+}
+
+int gb_version(void) { return 100; }
+
+const char *gb_last_error(void) { return gb::last_error_message(); }
+
+gb_status gb_create(gb_handle **out, int device) {
+  if (!out) return -1;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+    cudaGetLastError();
+    return GB_ERR_CUDA;
+  }
+  DeviceGuard g(device);
+  gb_handle *h = new (std::nothrow) gb_handle();
+  if (!h) return GB_ERR_NOMEM;
+  h->device = device;
+  cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, device);
+  bool ok = cudaMalloc(&h->d_status, sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&h->d_err, sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&h->d_sync, sizeof(int) * SYNC_WORDS) == cudaSuccess &&
+            cudaMalloc(&h->d_scalars, sizeof(double) * 4096) == cudaSuccess;
+  if (ok)
+    ok = cudaMemset(h->d_status, 0, sizeof(int)) == cudaSuccess &&
+         cudaMemset(h->d_err, 0, sizeof(int)) == cudaSuccess &&
+         cudaMemset(h->d_sync, 0, sizeof(int) * SYNC_WORDS) == cudaSuccess &&
+         cudaDeviceSynchronize() == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    gb_destroy(h);
+    return GB_ERR_NOMEM;
+  }
+  *out = h;
+  return GB_OK;
+}
+
+gb_status gb_destroy(gb_handle *h) {
+  if (!h) return GB_OK;
+  DeviceGuard g(h->device);
+  cudaDeviceSynchronize();
+  for (auto &r : h->prof_pending) {
+    cudaEventDestroy(r.start);
+    cudaEventDestroy(r.stop);
+  }
+  for (auto e : h->prof_pool) cudaEventDestroy(e);
+  for (auto &w : h->ws)
+    if (w.ptr) cudaFree(w.ptr);
+  if (h->d_status) cudaFree(h->d_status);
+  if (h->d_err) cudaFree(h->d_err);
+  if (h->d_sync) cudaFree(h->d_sync);
+  if (h->d_scalars) cudaFree(h->d_scalars);
+  delete h;
+  return GB_OK;
+}
+
+gb_status gb_set_option(gb_handle *h, gb_option opt, int64_t v) {
+  if (!h) return -1;
+  switch (opt) {
+    case GB_OPT_INNER_STEP:
+      if (v < 1 || v > 64) return -3;
+      h->inner_step = (int)v;
+      return GB_OK;
+    case GB_OPT_USE_GRAPHS: h->use_graphs = v ? 1 : 0; return GB_OK;
+    case GB_OPT_TC_UPDATE: h->tc_update = v ? 1 : 0; return GB_OK;
+    case GB_OPT_SPIN_LIMIT:
+      if (v < 1) return -3;
+      h->spin_limit = v;
+      return GB_OK;
+    case GB_OPT_PROFILE: h->profile = v ? 1 : 0; return GB_OK;
+    default: return -2;
+  }
+}
+
+gb_status gb_get_option(gb_handle *h, gb_option opt, int64_t *v) {
+  if (!h) return -1;
+  if (!v) return -3;
+  switch (opt) {
+    case GB_OPT_INNER_STEP: *v = h->inner_step; return GB_OK;
+    case GB_OPT_USE_GRAPHS: *v = h->use_graphs; return GB_OK;
+    case GB_OPT_TC_UPDATE: *v = h->tc_update; return GB_OK;
+    case GB_OPT_SPIN_LIMIT: *v = h->spin_limit; return GB_OK;
+    case GB_OPT_PROFILE: *v = h->profile; return GB_OK;
+    default: return -2;
+  }
+}
+
+gb_status gb_chol_factor(gb_handle *h, int64_t n, int64_t s, gb_dtype dt, const void *A,
+                         int64_t lda, void *L, int64_t ldl, int *info, void *stream) {
+  return factor_common(false, h, n, s, dt, A, lda, L, ldl, info, stream);
+}
+
+gb_status gb_lu_factor(gb_handle *h, int64_t n, int64_t s, gb_dtype dt, const void *A,
+                       int64_t lda, void *LU, int64_t ldlu, int *info, void *stream) {
+  return factor_common(true, h, n, s, dt, A, lda, LU, ldlu, info, stream);
+}
+
+gb_status gb_chol_solve(gb_handle *h, int64_t n, int64_t nrhs, gb_dtype factor_dt, const void *L,
+                        int64_t ldl, const double *A, int64_t lda, const double *B, int64_t ldb,
+                        double *X, int64_t ldx, const gb_refine_opts *opts,
+                        gb_solve_stats *stats, void *stream) {
+  return solve_entry(false, h, n, nrhs, factor_dt, L, ldl, A, lda, B, ldb, X, ldx, opts, stats,
+                     stream);
+}
+
+gb_status gb_lu_solve(gb_handle *h, int64_t n, int64_t nrhs, gb_dtype factor_dt, const void *LU,
+                      int64_t ldlu, const double *A, int64_t lda, const double *B, int64_t ldb,
+                      double *X, int64_t ldx, const gb_refine_opts *opts, gb_solve_stats *stats,
+                      void *stream) {
+  return solve_entry(true, h, n, nrhs, factor_dt, LU, ldlu, A, lda, B, ldb, X, ldx, opts, stats,
+                     stream);
+}
+
+gb_status gb_backward_error(gb_handle *h, int is_lu, int64_t n, gb_dtype factor_dt,
+                            const double *A, int64_t lda, const void *F, int64_t ldf,
+                            double *out, void *stream) {
+  if (!h) return -1;
+  if (n < 0) return -3;
+  if (!valid_dtype(factor_dt)) return -4;
+  if (n > 0 && !A) return -5;
+  if (lda < std::max<int64_t>(1, n)) return -6;
+  if (n > 0 && !F) return -7;
+  if (ldf < std::max<int64_t>(1, n)) return -8;
+  if (!out) return -9;
+  if (n > 0 && (!is_device_ptr(A) || !is_device_ptr(F))) return -5;
+  DeviceGuard g(h->device);
+  std::lock_guard<std::mutex> lk(h->mu);
+  cudaStream_t st = (cudaStream_t)stream;
+  *out = 0.0;
+  if (n == 0) return GB_OK;
+  if (factor_dt == GB_F64)
+    GB_CUDA_TRY(launch_backward_error<double>(is_lu, A, lda, (const double *)F, ldf, n,
+                                              h->d_scalars, st));
+  else
+    GB_CUDA_TRY(launch_backward_error<float>(is_lu, A, lda, (const float *)F, ldf, n,
+                                             h->d_scalars, st));
+  double acc[2];
+  GB_CUDA_TRY(cudaMemcpyAsync(acc, h->d_scalars, sizeof acc, cudaMemcpyDeviceToHost, st));
+  GB_CUDA_TRY(cudaStreamSynchronize(st));
+  *out = acc[1] > 0 ? std::sqrt(acc[0] / acc[1]) : 0.0;
+  return GB_OK;
+}
+
+}  // extern "C"
+
+extern "C" gb_status gb_chol_factor_batched(gb_handle *h, int64_t count, const int64_t *n,
+                                            void *const *A, const int64_t *lda, gb_dtype dt,
+                                            int64_t s, int *info, void *stream) {
+  (void)h; (void)count; (void)n; (void)A; (void)lda; (void)dt; (void)s; (void)info; (void)stream;
+  return GB_ERR_UNSUPPORTED;
+}
+
+extern "C" uint64_t gb_kernel_launches(void) { return gb::g_launches.load(); }
+
+extern "C" gb_status gb_profile_read(gb_handle *h, gb_profile *out) {
+  if (!h) return -1;
+  if (!out) return -2;
+  DeviceGuard g(h->device);
+  std::lock_guard<std::mutex> lk(h->mu);
+  gb_status r = GB_OK;
+  for (auto &rec : h->prof_pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(rec.stop) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, rec.start, rec.stop) != cudaSuccess) {
+      cudaGetLastError();
+      r = GB_ERR_CUDA;
+    }
+    if (rec.phase >= 0 && rec.phase < GB_NUM_PHASES) {
+      out->launches[rec.phase] += 1;
+      out->ms[rec.phase] += ms;
+      out->flops[rec.phase] += rec.flops;
+      out->bytes[rec.phase] += rec.bytes;
+    }
+    h->prof_pool.push_back(rec.start);
+    h->prof_pool.push_back(rec.stop);
+  }
+  h->prof_pending.clear();
+  return r;
+}

@@ -1,0 +1,171 @@
+// Internal declarations of the gbchol library (not installed, not part of the
+// C ABI).  Kernels live in panel.cu (column steps), update_simt.cu (SIMT
+// rank-s update), update_tc.cu (tcgen05 rank-s update), solve.cu (triangular
+// solves, residual, backward error), batched.cu; the host-side block loop and
+// the exported entry points live in abi.cu.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <mutex>
+#include <vector>
+
+#include "../../include/gbchol.h"
+
+namespace gb {
+
+// ------------------------------------------------------------------ errors
+#define GB_CUDA_TRY(expr)                                  \
+  do {                                                     \
+    cudaError_t _e = (expr);                               \
+    if (_e != cudaSuccess) {                               \
+      ::gb::record_cuda_error(_e, #expr, __FILE__, __LINE__); \
+      return GB_ERR_CUDA;                                  \
+    }                                                      \
+  } while (0)
+
+void record_cuda_error(cudaError_t e, const char *what, const char *file, int line);
+
+// Launch counter behind gb_kernel_launches(); every launcher bumps it.
+extern std::atomic<uint64_t> g_launches;
+inline void count_launch(uint64_t k = 1) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+const char *last_error_message();
+
+// Device error word bits (handle->d_err): set by kernels instead of trapping.
+enum : int {
+  DEV_ERR_TIMEOUT = 1,   // a bounded spin wait gave up
+  DEV_ERR_BOUNDS = 2,    // a self-check found an index out of range
+  DEV_ERR_TMEM = 4,      // tensor-memory allocation returned an unusable address
+};
+
+// ------------------------------------------------------------------ handle
+struct Workspace {
+  void *ptr = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace gb
+
+struct gb_handle {
+  int device = 0;
+  int sm_count = 0;
+  int inner_step = 64;
+  int use_graphs = 1;
+  int tc_update = 0;
+  int64_t spin_limit = 1 << 26;
+  int *d_status = nullptr;   // scratch status word for host `info` pointers
+  int *d_err = nullptr;      // device error word (DEV_ERR_*)
+  int *d_sync = nullptr;     // flags / tickets for single-kernel solves (SYNC_WORDS ints)
+  double *d_scalars = nullptr;  // small FP64 reduction outputs
+  unsigned sync_epoch = 0;
+  gb::Workspace ws[4];       // named workspaces, see WS_* below
+  std::mutex mu;
+  // GB_OPT_PROFILE: event pairs recorded around launches, read later
+  int profile = 0;
+  struct ProfRec {
+    int phase;
+    cudaEvent_t start, stop;
+    double flops, bytes;
+  };
+  std::vector<ProfRec> prof_pending;
+  std::vector<cudaEvent_t> prof_pool;
+};
+
+namespace gb {
+
+enum { WS_STAGE = 0, WS_PANEL = 1, WS_SOLVE = 2, WS_MISC = 3 };
+constexpr int SYNC_WORDS = 1 << 16;
+
+// Make sure workspace `slot` holds >= bytes; waits for `stream` before
+// releasing an older, smaller buffer.
+gb_status ws_reserve(gb_handle *h, int slot, size_t bytes, cudaStream_t stream);
+
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+__host__ __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
+__host__ __device__ __forceinline__ int64_t max64(int64_t a, int64_t b) { return a > b ? a : b; }
+
+// ------------------------------------------------------------ kernels (host)
+// Column steps of one inner block [j0, j0+bw) of the working matrix W (row
+// major, ld), rows j0..n-1.  Storage T, diag-block arithmetic Tc.
+template <typename T, typename Tc>
+cudaError_t launch_chol_diag(T *W, int64_t ld, int64_t j0, int bw, int *status, cudaStream_t st);
+template <typename T>
+cudaError_t launch_chol_rows(T *W, int64_t ld, int64_t row0, int64_t nrows, int64_t j0, int bw,
+                             int *status, cudaStream_t st);
+template <typename T, typename Tc>
+cudaError_t launch_lu_diag(T *W, int64_t ld, int64_t j0, int bw, int *status, cudaStream_t st);
+template <typename T>
+cudaError_t launch_lu_rows(T *W, int64_t ld, int64_t row0, int64_t nrows, int64_t j0, int bw,
+                           int *status, cudaStream_t st);
+template <typename T>
+cudaError_t launch_lu_cols(T *W, int64_t ld, int64_t col0, int64_t ncols, int64_t j0, int bw,
+                           int *status, cudaStream_t st);
+
+// C[i][j] -= sum_k X[i][k] * Y(k, j), 0 <= i < M, 0 <= j < N, 0 <= k < K.
+//   nn = false: Y(k, j) = Y[j * ldy + k]   (Cholesky, Y = R)
+//   nn = true:  Y(k, j) = Y[k * ldy + j]   (LU, Y = U panel)
+//   lower: update only elements with i + diag >= j.
+template <typename T>
+cudaError_t launch_update_simt(T *C, int64_t ldc, const T *X, int64_t ldx, const T *Y,
+                               int64_t ldy, int64_t M, int64_t N, int64_t K, bool nn, bool lower,
+                               int64_t diag, const int *status, cudaStream_t st);
+
+// Elementwise copies.  Lower-triangle copy with zeroed strict upper (chol)
+// or full copy (lu); Tin -> Tout.
+template <typename Tin, typename Tout>
+cudaError_t launch_copy_matrix(const Tin *A, int64_t lda, Tout *W, int64_t ldw, int64_t n,
+                               bool lower_only, cudaStream_t st);
+
+// tcgen05 mixed update (update_tc.cu).  Packs the panel to 16-bit operands and
+// runs the tensor-core kernel.  Returns cudaErrorNotSupported if the device
+// cannot run it.
+struct TcUpdateArgs {
+  float *C;          // working matrix (FP32), rows/cols start at (r0, r0)
+  int64_t ldc;
+  const float *X;    // panel rows (FP32), X[i * ldx + k]
+  int64_t ldx;
+  const float *Y;    // nn = false: Y[j * ldy + k]; nn = true: Y[k * ldy + j]
+  int64_t ldy;
+  int64_t M, N, K;
+  bool nn;
+  bool lower;
+  int64_t diag;
+  bool f16;          // FP16 operands instead of BF16
+  const int *status;
+  int *err;
+  int64_t spin_limit;
+  void *pack;        // workspace for the packed operands
+  size_t pack_bytes;
+};
+size_t tc_pack_bytes(int64_t M, int64_t N, int64_t K, bool nn);
+cudaError_t launch_update_tc(const TcUpdateArgs &a, cudaStream_t st);
+bool tc_supported(int device);
+
+// Solves (solve.cu)
+template <typename Tf, typename Tc>
+cudaError_t launch_trsm(const Tf *F, int64_t ldf, double *B, int64_t ldb, int64_t n,
+                        int64_t nrhs, int kind, int *sync, unsigned epoch, int *err,
+                        int64_t spin_limit, cudaStream_t st);
+enum { TRSM_LOWER = 0, TRSM_LOWER_T = 1, TRSM_UNIT_UPPER = 2 };
+cudaError_t launch_residual(const double *A, int64_t lda, const double *X, int64_t ldx,
+                            const double *B, int64_t ldb, double *R, int64_t ldr, int64_t n,
+                            int64_t nrhs, double *norms, cudaStream_t st);
+cudaError_t launch_inf_norm_rows(const double *A, int64_t lda, int64_t n, double *out,
+                                 cudaStream_t st);
+cudaError_t launch_axpy_cols(double *X, int64_t ldx, const double *D, int64_t ldd, int64_t n,
+                             int64_t nrhs, cudaStream_t st);
+template <typename Tf>
+cudaError_t launch_backward_error(int is_lu, const double *A, int64_t lda, const Tf *F,
+                                  int64_t ldf, int64_t n, double *acc, cudaStream_t st);
+template <typename Tf>
+cudaError_t launch_check_diag(const Tf *F, int64_t ldf, int64_t n, int *flag, cudaStream_t st);
+
+// Batched (batched.cu)
+template <typename T>
+cudaError_t launch_chol_batched(int64_t count, const int *order, const int *nn, T *const *A,
+                                const int64_t *lda, const int *steps, int *info, int *ticket,
+                                int sm_count, cudaStream_t st);
+
+}  // namespace gb

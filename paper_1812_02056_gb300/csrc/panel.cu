@@ -1,0 +1,369 @@
+// Column steps of Algorithms 1 and 2 (arXiv:1812.02056, Sec. 2) for one
+// block of at most 64 columns [j0, j0+bw) of the working matrix W.
+//
+// Every entry that the paper's column step produces,
+//   Cholesky  L_cc = sqrt(A_cc - sum_{k=z}^{c-1} L_ck^2)
+//             L_ic = (A_ic - sum_{k=z}^{c-1} L_ik L_ck) / L_cc      (i > c)
+//   LU        L_ic = A_ic - sum_{k=z}^{c-1} L_ik U_kc               (i >= c)
+//             U_ci = (A_ci - sum_{k=z}^{c-1} L_ck U_ki) / L_cc      (i > c)
+// is formed here with its sum taken in ascending k, one product at a time, as
+// the paper writes it.  The work is split by dependence, not reordered:
+//   *_diag_kernel  the bw x bw diagonal block, whose columns depend on one
+//                  another (one CTA, shared memory, bw dependent steps);
+//   *_rows_kernel  rows below the block: each row is an independent forward
+//                  substitution against the finished diagonal block;
+//   lu_cols_kernel columns of U right of the block, likewise independent.
+// W already holds A minus every delayed update applied before this block.
+#include <math.h>
+
+#include "gb_internal.cuh"
+
+namespace gb {
+namespace {
+
+__device__ __forceinline__ int load_status(const int *status) {
+  return *reinterpret_cast<const volatile int *>(status);
+}
+
+constexpr int DIAG_THREADS = 256;  // 16 x 16 threads, 4 x 4 elements each
+
+// ---------------------------------------------------------------- Cholesky
+template <typename T, typename Tc>
+__global__ void __launch_bounds__(DIAG_THREADS)
+    chol_diag_kernel(T *__restrict__ W, int64_t ld, int64_t j0, int bw, int *status) {
+  __shared__ Tc S[64][65];
+  if (load_status(status) != 0) return;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  T *D = W + j0 * ld + j0;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int i = ty + 16 * a, j = tx + 16 * b;
+      S[i][j] = (i < bw && j <= i) ? (Tc)D[(int64_t)i * ld + j] : Tc(0);
+    }
+  __syncthreads();
+  for (int c = 0; c < bw; ++c) {
+    const Tc d = S[c][c];  // A_cc minus sum_{k<c} L_ck^2, one product at a time
+    if (!(d > Tc(0))) {    // not positive, or NaN: Algorithm 1 assumes this away
+      if (tid == 0) atomicCAS(status, 0, (int)(j0 + c + 1));
+      return;  // d is the same for every thread: the whole CTA leaves
+    }
+    const Tc lcc = sqrt(d);
+    if (tid > c && tid < bw) S[tid][c] = S[tid][c] / lcc;
+    __syncthreads();
+    if (tid == 0) S[c][c] = lcc;
+    // subtract column c's product from the entries still to be finished:
+    // each entry receives its products in ascending k
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int i = ty + 16 * a, j = tx + 16 * b;
+        if (j > c && j <= i && i < bw) S[i][j] = S[i][j] - S[i][c] * S[j][c];
+      }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int i = ty + 16 * a, j = tx + 16 * b;
+      if (i < bw && j <= i) D[(int64_t)i * ld + j] = (T)S[i][j];
+    }
+}
+
+constexpr int ROWS_PER_CTA = 128;
+
+// Rows [row0, row0 + nrows) of the panel columns [j0, j0 + bw): each thread
+// owns one row x and solves x_c = (a_c - sum_{k<c} x_k L_ck) / L_cc.
+template <typename T, int B>
+__global__ void __launch_bounds__(ROWS_PER_CTA)
+    chol_rows_kernel(T *__restrict__ W, int64_t ld, int64_t row0, int64_t nrows, int64_t j0,
+                     int bw, const int *status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T(*LD)[B + 1] = reinterpret_cast<T(*)[B + 1]>(smem_raw);
+  T(*X)[B + 1] = reinterpret_cast<T(*)[B + 1]>(smem_raw + sizeof(T) * B * (B + 1));
+  if (load_status(status) != 0) return;
+  const int tid = threadIdx.x;
+  const int64_t rbase = row0 + (int64_t)blockIdx.x * ROWS_PER_CTA;
+  const int rows_here = (int)min64(ROWS_PER_CTA, row0 + nrows - rbase);
+  for (int idx = tid; idx < B * B; idx += ROWS_PER_CTA) {
+    const int i = idx / B, j = idx % B;
+    LD[i][j] = (i < bw && j <= i) ? W[(j0 + i) * ld + j0 + j] : T(0);
+  }
+  for (int idx = tid; idx < ROWS_PER_CTA * B; idx += ROWS_PER_CTA) {
+    const int r = idx / B, j = idx % B;
+    X[r][j] = (r < rows_here && j < bw) ? W[(rbase + r) * ld + j0 + j] : T(0);
+  }
+  __syncthreads();
+  if (tid < rows_here) {
+    T x[B];
+#pragma unroll
+    for (int c = 0; c < B; ++c) x[c] = X[tid][c];
+#pragma unroll
+    for (int c = 0; c < B; ++c) {
+      if (c < bw) {
+        T v = x[c];
+#pragma unroll
+        for (int k = 0; k < c; ++k) v = v - x[k] * LD[c][k];
+        x[c] = v / LD[c][c];
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < B; ++c) X[tid][c] = x[c];
+  }
+  __syncthreads();
+  for (int idx = tid; idx < ROWS_PER_CTA * B; idx += ROWS_PER_CTA) {
+    const int r = idx / B, j = idx % B;
+    if (r < rows_here && j < bw) W[(rbase + r) * ld + j0 + j] = X[r][j];
+  }
+}
+
+// ---------------------------------------------------------------------- LU
+template <typename T, typename Tc>
+__global__ void __launch_bounds__(DIAG_THREADS)
+    lu_diag_kernel(T *__restrict__ W, int64_t ld, int64_t j0, int bw, int *status) {
+  __shared__ Tc S[64][65];
+  if (load_status(status) != 0) return;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  T *D = W + j0 * ld + j0;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int i = ty + 16 * a, j = tx + 16 * b;
+      S[i][j] = (i < bw && j < bw) ? (Tc)D[(int64_t)i * ld + j] : Tc(0);
+    }
+  __syncthreads();
+  for (int c = 0; c < bw; ++c) {
+    const Tc p = S[c][c];  // L_cc = A_cc - sum_{k<c} L_ck U_kc
+    if (p == Tc(0) || p != p) {
+      if (tid == 0) atomicCAS(status, 0, (int)(j0 + c + 1));
+      return;
+    }
+    if (tid > c && tid < bw) S[c][tid] = S[c][tid] / p;  // U_ci
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int i = ty + 16 * a, j = tx + 16 * b;
+        if (i > c && j > c && i < bw && j < bw) S[i][j] = S[i][j] - S[i][c] * S[c][j];
+      }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int i = ty + 16 * a, j = tx + 16 * b;
+      if (i < bw && j < bw) D[(int64_t)i * ld + j] = (T)S[i][j];
+    }
+}
+
+// Rows of L below the block: x_c = a_c - sum_{k<c} x_k U_kc (no division,
+// U is unitriangular).
+template <typename T, int B>
+__global__ void __launch_bounds__(ROWS_PER_CTA)
+    lu_rows_kernel(T *__restrict__ W, int64_t ld, int64_t row0, int64_t nrows, int64_t j0,
+                   int bw, const int *status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T(*UT)[B + 1] = reinterpret_cast<T(*)[B + 1]>(smem_raw);  // UT[c][k] = U_kc, k < c
+  T(*X)[B + 1] = reinterpret_cast<T(*)[B + 1]>(smem_raw + sizeof(T) * B * (B + 1));
+  if (load_status(status) != 0) return;
+  const int tid = threadIdx.x;
+  const int64_t rbase = row0 + (int64_t)blockIdx.x * ROWS_PER_CTA;
+  const int rows_here = (int)min64(ROWS_PER_CTA, row0 + nrows - rbase);
+  for (int idx = tid; idx < B * B; idx += ROWS_PER_CTA) {
+    const int k = idx / B, c = idx % B;
+    UT[c][k] = (k < bw && c < bw && k < c) ? W[(j0 + k) * ld + j0 + c] : T(0);
+  }
+  for (int idx = tid; idx < ROWS_PER_CTA * B; idx += ROWS_PER_CTA) {
+    const int r = idx / B, j = idx % B;
+    X[r][j] = (r < rows_here && j < bw) ? W[(rbase + r) * ld + j0 + j] : T(0);
+  }
+  __syncthreads();
+  if (tid < rows_here) {
+    T x[B];
+#pragma unroll
+    for (int c = 0; c < B; ++c) x[c] = X[tid][c];
+#pragma unroll
+    for (int c = 0; c < B; ++c) {
+      if (c < bw) {
+        T v = x[c];
+#pragma unroll
+        for (int k = 0; k < c; ++k) v = v - x[k] * UT[c][k];
+        x[c] = v;
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < B; ++c) X[tid][c] = x[c];
+  }
+  __syncthreads();
+  for (int idx = tid; idx < ROWS_PER_CTA * B; idx += ROWS_PER_CTA) {
+    const int r = idx / B, j = idx % B;
+    if (r < rows_here && j < bw) W[(rbase + r) * ld + j0 + j] = X[r][j];
+  }
+}
+
+// Columns of U right of the block: y_c = (a_c - sum_{k<c} L_ck y_k) / L_cc.
+// One thread per column; loads along a row are coalesced across threads.
+template <typename T, int B>
+__global__ void __launch_bounds__(ROWS_PER_CTA)
+    lu_cols_kernel(T *__restrict__ W, int64_t ld, int64_t col0, int64_t ncols, int64_t j0,
+                   int bw, const int *status) {
+  __shared__ T LD[B][B + 1];
+  if (load_status(status) != 0) return;
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < B * B; idx += ROWS_PER_CTA) {
+    const int i = idx / B, j = idx % B;
+    LD[i][j] = (i < bw && j <= i) ? W[(j0 + i) * ld + j0 + j] : T(0);
+  }
+  __syncthreads();
+  const int64_t q = col0 + (int64_t)blockIdx.x * ROWS_PER_CTA + tid;
+  if (q >= col0 + ncols) return;
+  T y[B];
+#pragma unroll
+  for (int c = 0; c < B; ++c) y[c] = (c < bw) ? W[(j0 + c) * ld + q] : T(0);
+#pragma unroll
+  for (int c = 0; c < B; ++c) {
+    if (c < bw) {
+      T v = y[c];
+#pragma unroll
+      for (int k = 0; k < c; ++k) v = v - LD[c][k] * y[k];
+      y[c] = v / LD[c][c];
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < B; ++c)
+    if (c < bw) W[(j0 + c) * ld + q] = y[c];
+}
+
+// ------------------------------------------------------------------- copies
+template <typename Tin, typename Tout>
+__global__ void copy_matrix_kernel(const Tin *__restrict__ A, int64_t lda, Tout *__restrict__ W,
+                                   int64_t ldw, int64_t n, int lower_only) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  for (int64_t i = blockIdx.y; i < n; i += gridDim.y) {
+    Tout v = (!lower_only || j <= i) ? (Tout)A[i * lda + j] : Tout(0);
+    W[i * ldw + j] = v;
+  }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ launchers
+template <typename T, typename Tc>
+cudaError_t launch_chol_diag(T *W, int64_t ld, int64_t j0, int bw, int *status, cudaStream_t st) {
+  if (bw < 1 || bw > 64) return cudaErrorInvalidValue;
+  chol_diag_kernel<T, Tc><<<1, DIAG_THREADS, 0, st>>>(W, ld, j0, bw, status);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <typename T, int B>
+constexpr size_t rows_smem_bytes() {
+  return sizeof(T) * (size_t)(B + ROWS_PER_CTA) * (B + 1);
+}
+
+// Opt a kernel into more than 48 KB of dynamic shared memory (once per
+// instantiation; a repeated call is harmless).
+template <typename K>
+cudaError_t allow_smem(K kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <typename T, int B>
+cudaError_t chol_rows_b(T *W, int64_t ld, int64_t row0, int64_t nrows, int64_t j0, int bw,
+                        int *status, cudaStream_t st) {
+  constexpr size_t smem = rows_smem_bytes<T, B>();
+  static cudaError_t attr = allow_smem(chol_rows_kernel<T, B>, smem);
+  if (attr != cudaSuccess) return attr;
+  const unsigned grid = (unsigned)ceil_div(nrows, ROWS_PER_CTA);
+  chol_rows_kernel<T, B><<<grid, ROWS_PER_CTA, smem, st>>>(W, ld, row0, nrows, j0, bw, status);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <typename T, int B>
+cudaError_t lu_rows_b(T *W, int64_t ld, int64_t row0, int64_t nrows, int64_t j0, int bw,
+                      int *status, cudaStream_t st) {
+  constexpr size_t smem = rows_smem_bytes<T, B>();
+  static cudaError_t attr = allow_smem(lu_rows_kernel<T, B>, smem);
+  if (attr != cudaSuccess) return attr;
+  const unsigned grid = (unsigned)ceil_div(nrows, ROWS_PER_CTA);
+  lu_rows_kernel<T, B><<<grid, ROWS_PER_CTA, smem, st>>>(W, ld, row0, nrows, j0, bw, status);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_chol_rows(T *W, int64_t ld, int64_t row0, int64_t nrows, int64_t j0, int bw,
+                             int *status, cudaStream_t st) {
+  if (nrows <= 0) return cudaSuccess;
+  if (bw < 1 || bw > 64) return cudaErrorInvalidValue;
+  if (bw <= 32) return chol_rows_b<T, 32>(W, ld, row0, nrows, j0, bw, status, st);
+  return chol_rows_b<T, 64>(W, ld, row0, nrows, j0, bw, status, st);
+}
+
+template <typename T, typename Tc>
+cudaError_t launch_lu_diag(T *W, int64_t ld, int64_t j0, int bw, int *status, cudaStream_t st) {
+  if (bw < 1 || bw > 64) return cudaErrorInvalidValue;
+  lu_diag_kernel<T, Tc><<<1, DIAG_THREADS, 0, st>>>(W, ld, j0, bw, status);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_lu_rows(T *W, int64_t ld, int64_t row0, int64_t nrows, int64_t j0, int bw,
+                           int *status, cudaStream_t st) {
+  if (nrows <= 0) return cudaSuccess;
+  if (bw < 1 || bw > 64) return cudaErrorInvalidValue;
+  if (bw <= 32) return lu_rows_b<T, 32>(W, ld, row0, nrows, j0, bw, status, st);
+  return lu_rows_b<T, 64>(W, ld, row0, nrows, j0, bw, status, st);
+}
+
+template <typename T>
+cudaError_t launch_lu_cols(T *W, int64_t ld, int64_t col0, int64_t ncols, int64_t j0, int bw,
+                           int *status, cudaStream_t st) {
+  if (ncols <= 0) return cudaSuccess;
+  if (bw < 1 || bw > 64) return cudaErrorInvalidValue;
+  const unsigned grid = (unsigned)ceil_div(ncols, ROWS_PER_CTA);
+  if (bw <= 32)
+    lu_cols_kernel<T, 32><<<grid, ROWS_PER_CTA, 0, st>>>(W, ld, col0, ncols, j0, bw, status);
+  else
+    lu_cols_kernel<T, 64><<<grid, ROWS_PER_CTA, 0, st>>>(W, ld, col0, ncols, j0, bw, status);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <typename Tin, typename Tout>
+cudaError_t launch_copy_matrix(const Tin *A, int64_t lda, Tout *W, int64_t ldw, int64_t n,
+                               bool lower_only, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  dim3 block(256), grid((unsigned)ceil_div(n, 256), (unsigned)min64(n, 65535));
+  copy_matrix_kernel<Tin, Tout><<<grid, block, 0, st>>>(A, lda, W, ldw, n, lower_only ? 1 : 0);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_chol_diag<double, double>(double *, int64_t, int64_t, int, int *, cudaStream_t);
+template cudaError_t launch_chol_diag<float, float>(float *, int64_t, int64_t, int, int *, cudaStream_t);
+template cudaError_t launch_chol_diag<float, double>(float *, int64_t, int64_t, int, int *, cudaStream_t);
+template cudaError_t launch_chol_rows<double>(double *, int64_t, int64_t, int64_t, int64_t, int, int *, cudaStream_t);
+template cudaError_t launch_chol_rows<float>(float *, int64_t, int64_t, int64_t, int64_t, int, int *, cudaStream_t);
+template cudaError_t launch_lu_diag<double, double>(double *, int64_t, int64_t, int, int *, cudaStream_t);
+template cudaError_t launch_lu_diag<float, float>(float *, int64_t, int64_t, int, int *, cudaStream_t);
+template cudaError_t launch_lu_diag<float, double>(float *, int64_t, int64_t, int, int *, cudaStream_t);
+template cudaError_t launch_lu_rows<double>(double *, int64_t, int64_t, int64_t, int64_t, int, int *, cudaStream_t);
+template cudaError_t launch_lu_rows<float>(float *, int64_t, int64_t, int64_t, int64_t, int, int *, cudaStream_t);
+template cudaError_t launch_lu_cols<double>(double *, int64_t, int64_t, int64_t, int64_t, int, int *, cudaStream_t);
+template cudaError_t launch_lu_cols<float>(float *, int64_t, int64_t, int64_t, int64_t, int, int *, cudaStream_t);
+template cudaError_t launch_copy_matrix<double, double>(const double *, int64_t, double *, int64_t, int64_t, bool, cudaStream_t);
+template cudaError_t launch_copy_matrix<float, float>(const float *, int64_t, float *, int64_t, int64_t, bool, cudaStream_t);
+template cudaError_t launch_copy_matrix<double, float>(const double *, int64_t, float *, int64_t, int64_t, bool, cudaStream_t);
+
+}  // namespace gb

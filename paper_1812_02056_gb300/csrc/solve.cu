@@ -1,0 +1,401 @@
+// Solves with the factors of Algorithms 1 and 2 (arXiv:1812.02056), the
+// FP64 residual of iterative refinement, and the FP64 backward error.
+//
+// Triangular solve: one launch per solve.  The n rows are cut into blocks
+// of TB rows; CTAs take block rows in dependence order from an atomic ticket
+// (so a CTA only ever waits on blocks already owned by running CTAs), apply
+// every finished block's contribution as soon as its flag is published, then
+// substitute within their own diagonal block and publish.  Every wait is
+// bounded by a %globaltimer deadline; on expiry the kernel raises
+// DEV_ERR_TIMEOUT in the error word, every other waiter sees it and returns,
+// and the host reports GB_ERR_TIMEOUT.
+#include <math.h>
+
+#include "gb_internal.cuh"
+
+namespace gb {
+namespace {
+
+constexpr int TB = 32;       // rows per block
+constexpr int NRC = 32;      // right-hand sides per chunk
+constexpr int TRSM_THREADS = 256;
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ int ld_acquire(const int *p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release(int *p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Element (i, k) of op(F) for the three solve kinds.
+template <typename Tf>
+__device__ __forceinline__ Tf op_elem(const Tf *F, int64_t ldf, int kind, int64_t i, int64_t k) {
+  return kind == TRSM_LOWER_T ? F[k * ldf + i] : F[i * ldf + k];
+}
+
+template <typename Tf, typename Tc>
+__global__ void __launch_bounds__(TRSM_THREADS)
+    trsm_kernel(const Tf *__restrict__ F, int64_t ldf, double *B, int64_t ldb, int64_t n,
+                int64_t nrhs, int kind, int *ticket, int *flags, unsigned epoch, int *err,
+                long long wait_ns) {
+  __shared__ Tc Fs[TB][TB + 1];
+  __shared__ Tc Xs[TB][NRC + 1];
+  __shared__ Tc Acc[TB][NRC + 1];
+  __shared__ int s_ib, s_abort;
+  const int tid = threadIdx.x;
+  const int nb = (int)((n + TB - 1) / TB);
+  const bool fwd = (kind == TRSM_LOWER);
+  if (tid == 0) {
+    const int t = atomicAdd(ticket, 1);
+    s_ib = fwd ? t : nb - 1 - t;
+    s_abort = 0;
+  }
+  __syncthreads();
+  const int ib = s_ib;
+  if (ib < 0 || ib >= nb) return;
+  const int64_t r0 = (int64_t)ib * TB;
+  const int rows = (int)min64(TB, n - r0);
+  // thread -> (row, 4 columns) of the chunk
+  const int tr = tid / (NRC / 4), tc = (tid % (NRC / 4)) * 4;
+
+  for (int64_t c0 = 0; c0 < nrhs; c0 += NRC) {
+    const int cols = (int)min64(NRC, nrhs - c0);
+    Tc acc[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      acc[q] = (tr < rows && tc + q < cols) ? (Tc)B[(r0 + tr) * ldb + c0 + tc + q] : Tc(0);
+    // contributions of the finished blocks, in dependence order
+    for (int step = 0; step < (fwd ? ib : nb - 1 - ib); ++step) {
+      const int jb = fwd ? step : nb - 1 - step;
+      if (tid == 0) {
+        const long long t0 = (long long)globaltimer_ns();
+        while (ld_acquire(&flags[jb]) != (int)epoch) {
+          if (ld_acquire(err) & DEV_ERR_TIMEOUT) {
+            s_abort = 1;
+            break;
+          }
+          if ((long long)globaltimer_ns() - t0 > wait_ns) {
+            atomicOr(err, DEV_ERR_TIMEOUT);
+            s_abort = 1;
+            break;
+          }
+          __nanosleep(64);
+        }
+      }
+      __syncthreads();
+      if (s_abort) return;
+      const int64_t k0 = (int64_t)jb * TB;
+      const int kr = (int)min64(TB, n - k0);
+      for (int idx = tid; idx < TB * TB; idx += TRSM_THREADS) {
+        const int i = idx / TB, k = idx % TB;
+        Fs[i][k] = (i < rows && k < kr) ? (Tc)op_elem(F, ldf, kind, r0 + i, k0 + k) : Tc(0);
+      }
+      for (int idx = tid; idx < TB * NRC; idx += TRSM_THREADS) {
+        const int k = idx / NRC, c = idx % NRC;
+        Xs[k][c] = (k < kr && c < cols) ? (Tc)__ldcg(&B[(k0 + k) * ldb + c0 + c]) : Tc(0);
+      }
+      __syncthreads();
+#pragma unroll 8
+      for (int k = 0; k < TB; ++k) {
+        const Tc f = Fs[tr][k];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q] = acc[q] - f * Xs[k][tc + q];
+      }
+      __syncthreads();
+    }
+    // substitution inside the diagonal block
+    for (int idx = tid; idx < TB * TB; idx += TRSM_THREADS) {
+      const int i = idx / TB, k = idx % TB;
+      Fs[i][k] = (i < rows && k < rows) ? (Tc)op_elem(F, ldf, kind, r0 + i, r0 + k) : Tc(0);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) Acc[tr][tc + q] = acc[q];
+    __syncthreads();
+    if (tid < NRC) {
+      const int c = tid;
+      if (fwd) {
+        for (int i = 0; i < rows; ++i) {
+          Tc v = Acc[i][c];
+          for (int k = 0; k < i; ++k) v = v - Fs[i][k] * Acc[k][c];
+          Acc[i][c] = v / Fs[i][i];
+        }
+      } else {
+        for (int i = rows - 1; i >= 0; --i) {
+          Tc v = Acc[i][c];
+          for (int k = i + 1; k < rows; ++k) v = v - Fs[i][k] * Acc[k][c];
+          Acc[i][c] = (kind == TRSM_UNIT_UPPER) ? v : v / Fs[i][i];
+        }
+      }
+    }
+    __syncthreads();
+    for (int idx = tid; idx < TB * NRC; idx += TRSM_THREADS) {
+      const int i = idx / NRC, c = idx % NRC;
+      if (i < rows && c < cols) B[(r0 + i) * ldb + c0 + c] = (double)Acc[i][c];
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    __threadfence();
+    st_release(&flags[ib], (int)epoch);
+  }
+}
+
+// ------------------------------------------------------------- residual
+// R = B - A X in FP64.  CTA: RES_ROWS rows, X staged in shared memory by
+// k-chunks; warp w handles rows w, w + 8, ...; lanes split k.
+constexpr int RES_ROWS = 32;
+constexpr int RES_KC = 128;
+constexpr int RES_NC = 16;
+
+__device__ __forceinline__ void atomic_max_nonneg(double *addr, double v) {
+  // non-negative doubles order like their bit patterns as signed integers
+  atomicMax(reinterpret_cast<long long *>(addr), __double_as_longlong(v));
+}
+
+__global__ void __launch_bounds__(256)
+    residual_kernel(const double *__restrict__ A, int64_t lda, const double *__restrict__ X,
+                    int64_t ldx, const double *__restrict__ B, int64_t ldb, double *__restrict__ R,
+                    int64_t ldr, int64_t n, int64_t nrhs, double *norms) {
+  __shared__ double Xs[RES_KC][RES_NC];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t i0 = (int64_t)blockIdx.x * RES_ROWS;
+  for (int64_t c0 = 0; c0 < nrhs; c0 += RES_NC) {
+    const int cols = (int)min64(RES_NC, nrhs - c0);
+    double acc[RES_ROWS / 8][RES_NC];
+#pragma unroll
+    for (int a = 0; a < RES_ROWS / 8; ++a)
+#pragma unroll
+      for (int c = 0; c < RES_NC; ++c) acc[a][c] = 0.0;
+    for (int64_t k0 = 0; k0 < n; k0 += RES_KC) {
+      const int kr = (int)min64(RES_KC, n - k0);
+      __syncthreads();
+      for (int idx = tid; idx < RES_KC * RES_NC; idx += 256) {
+        const int k = idx / RES_NC, c = idx % RES_NC;
+        Xs[k][c] = (k < kr && c < cols) ? X[(k0 + k) * ldx + c0 + c] : 0.0;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int a = 0; a < RES_ROWS / 8; ++a) {
+        const int64_t i = i0 + warp + 8 * a;
+        if (i >= n) continue;
+        for (int k = lane; k < kr; k += 32) {
+          const double av = A[i * lda + k0 + k];
+#pragma unroll
+          for (int c = 0; c < RES_NC; ++c) acc[a][c] = fma(av, Xs[k][c], acc[a][c]);
+        }
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < RES_ROWS / 8; ++a) {
+      const int64_t i = i0 + warp + 8 * a;
+#pragma unroll
+      for (int c = 0; c < RES_NC; ++c) {
+        double v = acc[a][c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0 && i < n && c < cols) {
+          const double r = B[i * ldb + c0 + c] - v;
+          R[i * ldr + c0 + c] = r;
+          if (norms) {
+            atomic_max_nonneg(&norms[c0 + c], fabs(r));                      // ||r||_inf
+            atomic_max_nonneg(&norms[nrhs + c0 + c], fabs(X[i * ldx + c0 + c]));  // ||x||_inf
+            atomic_max_nonneg(&norms[2 * nrhs + c0 + c], fabs(B[i * ldb + c0 + c]));  // ||b||_inf
+          }
+        }
+      }
+    }
+  }
+}
+
+__global__ void inf_norm_rows_kernel(const double *__restrict__ A, int64_t lda, int64_t n,
+                                     double *out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  if (i >= n) return;
+  double s = 0.0;
+  for (int64_t k = lane; k < n; k += 32) s += fabs(A[i * lda + k]);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) atomic_max_nonneg(out, s);
+}
+
+__global__ void axpy_cols_kernel(double *X, int64_t ldx, const double *D, int64_t ldd, int64_t n,
+                                 int64_t nrhs) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * nrhs) return;
+  const int64_t i = idx / nrhs, c = idx % nrhs;
+  X[i * ldx + c] += D[i * ldd + c];
+}
+
+// ------------------------------------------------------- backward error
+// acc[0] += sum (A - P)^2, acc[1] += sum A^2 over the full square, with
+// P = F F^T (Cholesky) or L U (LU compact, unit U).  32 x 32 output tiles.
+template <typename Tf>
+__global__ void __launch_bounds__(256)
+    backward_error_kernel(int is_lu, const double *__restrict__ A, int64_t lda,
+                          const Tf *__restrict__ F, int64_t ldf, int64_t n, double *acc_out) {
+  __shared__ double Ls[32][33];
+  __shared__ double Rs[32][33];
+  __shared__ double red[2][8];
+  const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+  const int64_t i0 = (int64_t)blockIdx.y * 32, j0 = (int64_t)blockIdx.x * 32;
+  double p[4] = {0, 0, 0, 0};
+  const int64_t kend = min64(n, min64(i0, j0) + 32);
+  for (int64_t k0 = 0; k0 < kend; k0 += 32) {
+    for (int idx = tid; idx < 32 * 32; idx += 256) {
+      const int r = idx / 32, k = idx % 32;
+      const int64_t gi = i0 + r, gk = k0 + k, gj = j0 + r;
+      double lv = 0.0, rv = 0.0;
+      if (gi < n && gk < n && gk <= gi) lv = (double)F[gi * ldf + gk];
+      if (!is_lu) {
+        if (gj < n && gk < n && gk <= gj) rv = (double)F[gj * ldf + gk];
+      } else {
+        // Rs[r][k] = U_{k0+k, j0+r}
+        if (gj < n && gk < n) rv = (gk == gj) ? 1.0 : (gk < gj ? (double)F[gk * ldf + gj] : 0.0);
+      }
+      Ls[r][k] = lv;
+      Rs[r][k] = rv;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int k = 0; k < 32; ++k) {
+      const double rv = Rs[tx][k];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) p[a] = fma(Ls[ty + 8 * a][k], rv, p[a]);
+    }
+    __syncthreads();
+  }
+  double num = 0.0, den = 0.0;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int64_t gi = i0 + ty + 8 * a, gj = j0 + tx;
+    if (gi < n && gj < n) {
+      const double av = A[gi * lda + gj];
+      const double d = av - p[a];
+      num += d * d;
+      den += av * av;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    num += __shfl_xor_sync(0xffffffffu, num, o);
+    den += __shfl_xor_sync(0xffffffffu, den, o);
+  }
+  if (tx == 0) {
+    red[0][ty] = num;
+    red[1][ty] = den;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double a = 0, b = 0;
+    for (int w = 0; w < 8; ++w) {
+      a += red[0][w];
+      b += red[1][w];
+    }
+    atomicAdd(&acc_out[0], a);
+    atomicAdd(&acc_out[1], b);
+  }
+}
+
+template <typename Tf>
+__global__ void check_diag_kernel(const Tf *F, int64_t ldf, int64_t n, int *flag) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double d = (double)F[i * ldf + i];
+  if (!(fabs(d) > 0.0) || !isfinite(d)) atomicOr(flag, 1);
+}
+
+}  // namespace
+
+template <typename Tf, typename Tc>
+cudaError_t launch_trsm(const Tf *F, int64_t ldf, double *B, int64_t ldb, int64_t n,
+                        int64_t nrhs, int kind, int *sync, unsigned epoch, int *err,
+                        int64_t spin_limit, cudaStream_t st) {
+  if (n <= 0 || nrhs <= 0) return cudaSuccess;
+  const int64_t nb = (n + TB - 1) / TB;
+  if (nb + 1 > SYNC_WORDS) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(sync, 0, sizeof(int), st);  // ticket
+  if (e != cudaSuccess) return e;
+  const long long wait_ns = (long long)spin_limit * 100LL;  // spin_limit in units of 100 ns
+  trsm_kernel<Tf, Tc><<<(unsigned)nb, TRSM_THREADS, 0, st>>>(F, ldf, B, ldb, n, nrhs, kind, sync,
+                                                             sync + 1, epoch, err, wait_ns);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual(const double *A, int64_t lda, const double *X, int64_t ldx,
+                            const double *B, int64_t ldb, double *R, int64_t ldr, int64_t n,
+                            int64_t nrhs, double *norms, cudaStream_t st) {
+  if (n <= 0 || nrhs <= 0) return cudaSuccess;
+  if (norms) {
+    cudaError_t e = cudaMemsetAsync(norms, 0, sizeof(double) * 3 * nrhs, st);
+    if (e != cudaSuccess) return e;
+  }
+  residual_kernel<<<(unsigned)ceil_div(n, RES_ROWS), 256, 0, st>>>(A, lda, X, ldx, B, ldb, R, ldr,
+                                                                  n, nrhs, norms);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_inf_norm_rows(const double *A, int64_t lda, int64_t n, double *out,
+                                 cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double), st);
+  if (e != cudaSuccess || n <= 0) return e;
+  inf_norm_rows_kernel<<<(unsigned)ceil_div(n, 8), 256, 0, st>>>(A, lda, n, out);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpy_cols(double *X, int64_t ldx, const double *D, int64_t ldd, int64_t n,
+                             int64_t nrhs, cudaStream_t st) {
+  if (n <= 0 || nrhs <= 0) return cudaSuccess;
+  axpy_cols_kernel<<<(unsigned)ceil_div(n * nrhs, 256), 256, 0, st>>>(X, ldx, D, ldd, n, nrhs);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <typename Tf>
+cudaError_t launch_backward_error(int is_lu, const double *A, int64_t lda, const Tf *F,
+                                  int64_t ldf, int64_t n, double *acc, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(acc, 0, 2 * sizeof(double), st);
+  if (e != cudaSuccess || n <= 0) return e;
+  const int64_t g = (n + 31) / 32;
+  if (g > 65535) return cudaErrorInvalidConfiguration;
+  backward_error_kernel<Tf><<<dim3((unsigned)g, (unsigned)g), 256, 0, st>>>(is_lu, A, lda, F, ldf,
+                                                                          n, acc);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <typename Tf>
+cudaError_t launch_check_diag(const Tf *F, int64_t ldf, int64_t n, int *flag, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), st);
+  if (e != cudaSuccess || n <= 0) return e;
+  check_diag_kernel<Tf><<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(F, ldf, n, flag);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_trsm<double, double>(const double *, int64_t, double *, int64_t,
+                                                 int64_t, int64_t, int, int *, unsigned, int *,
+                                                 int64_t, cudaStream_t);
+template cudaError_t launch_trsm<float, float>(const float *, int64_t, double *, int64_t, int64_t,
+                                               int64_t, int, int *, unsigned, int *, int64_t,
+                                               cudaStream_t);
+template cudaError_t launch_backward_error<double>(int, const double *, int64_t, const double *,
+                                                   int64_t, int64_t, double *, cudaStream_t);
+template cudaError_t launch_backward_error<float>(int, const double *, int64_t, const float *,
+                                                  int64_t, int64_t, double *, cudaStream_t);
+template cudaError_t launch_check_diag<double>(const double *, int64_t, int64_t, int *,
+                                               cudaStream_t);
+template cudaError_t launch_check_diag<float>(const float *, int64_t, int64_t, int *,
+                                              cudaStream_t);
+
+}  // namespace gb

@@ -1,0 +1,126 @@
+"""Parity of the CUDA solves (forward/back substitution, iterative
+refinement) with the FP64 oracle.
+
+* FP64 factor, no refinement: X within 1e-10 (relative to max |X|) of the
+  oracle's solve with the oracle's factor; the matrices here have
+  condition number < 10, so the two solutions agree to ~1e-14.
+* FP32 / mixed factor with refinement: the normwise backward error eta
+  reaches 1e-14 and X agrees with the oracle's FP64 solve within
+  cond(A) * 1e-14.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1812_02056_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def h():
+    from paper_1812_02056_gb300 import _build, binding
+    _build.build()
+    hd = binding.Handle(0)
+    yield hd
+    hd.close()
+
+
+def _t(a, dtype=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV, dtype)
+
+
+@pytest.mark.parametrize("n,nrhs", [(1, 1), (31, 3), (32, 32), (33, 33), (200, 1), (257, 64),
+                                    (300, 70)])
+def test_chol_solve_f64(h, n, nrhs):
+    A = I.spd_gram(n, 100 + n)
+    B = I.rhs(n, nrhs, 200 + n)
+    L, info = h.chol_factor(_t(A), 32, "f64")
+    X, stats = h.chol_solve(L, _t(B), "f64")
+    Lo, _ = oracle.chol(A, 32)
+    Xo = oracle.chol_solve(Lo, B)
+    Xg = X.cpu().numpy()
+    assert np.abs(Xg - Xo).max() <= 1e-10 * max(np.abs(Xo).max(), 1e-300)
+    assert stats.iterations == 0 and stats.converged == 1
+
+
+@pytest.mark.parametrize("n,nrhs", [(5, 2), (100, 16), (257, 33)])
+def test_lu_solve_f64(h, n, nrhs):
+    A = I.lu_diag_dominant(n, 300 + n)
+    B = I.rhs(n, nrhs, 400 + n)
+    LU, info = h.lu_factor(_t(A), 64, "f64")
+    X, _ = h.lu_solve(LU, _t(B), "f64")
+    Lo, Uo, _ = oracle.lu(A, 64)
+    Xo = oracle.lu_solve(Lo, Uo, B)
+    assert np.abs(X.cpu().numpy() - Xo).max() <= 1e-10 * np.abs(Xo).max()
+
+
+@pytest.mark.parametrize("dtype", ["f32", "mix_bf16", "mix_f16"])
+def test_chol_refinement_reaches_fp64(h, dtype):
+    n, nrhs = 512, 16
+    A = I.spd_logspaced(n, 7, cond=1e4)
+    B = I.rhs(n, nrhs, 8)
+    Ad = _t(A)
+    Ain = _t(A, torch.float32) if dtype == "f32" else Ad
+    L, info = h.chol_factor(Ain, 64, dtype)
+    assert int(info.item()) == 0
+    X, stats = h.chol_solve(L, _t(B), dtype, A=Ad, tol=1e-14, max_iter=50)
+    assert stats.converged == 1 and stats.eta <= 1e-14
+    Lo, _ = oracle.chol(A, 64)
+    Xo = oracle.chol_solve(Lo, B)
+    assert np.abs(X.cpu().numpy() - Xo).max() <= 1e4 * 1e-13 * np.abs(Xo).max()
+    # the host-side definition of eta agrees with the reported one
+    Xg = X.cpu().numpy()
+    R = B - A @ Xg
+    eta = max(np.abs(R[:, c]).max() / (np.abs(A).sum(1).max() * np.abs(Xg[:, c]).max()
+                                        + np.abs(B[:, c]).max()) for c in range(nrhs))
+    assert eta <= 2e-14
+
+
+def test_lu_refinement_f32(h):
+    n, nrhs = 300, 4
+    A = I.lu_diag_dominant(n, 17)
+    B = I.rhs(n, nrhs, 18)
+    LU, info = h.lu_factor(_t(A, torch.float32), 64, "f32")
+    X, stats = h.lu_solve(LU, _t(B), "f32", A=_t(A), tol=1e-15)
+    assert stats.converged == 1 and stats.eta <= 1e-15
+    Xo = np.linalg.solve(A, B)
+    assert np.abs(X.cpu().numpy() - Xo).max() <= 1e-12 * np.abs(Xo).max()
+
+
+def test_solve_host_buffers(h):
+    from paper_1812_02056_gb300 import binding
+    n, nrhs = 130, 5
+    A = I.spd_gram(n, 1)
+    B = I.rhs(n, nrhs, 2)
+    Lo, _ = oracle.chol(A, 16)
+    X = np.zeros((n, nrhs))
+    st, stats = h.gb_chol_solve(n, nrhs, binding.GB_F64, Lo, n, A, n, B, nrhs, X, nrhs, 1e-15, 5)
+    assert st == 0 and stats.eta <= 1e-15
+    assert np.abs(X - np.linalg.solve(A, B)).max() <= 1e-12 * np.abs(X).max()
+
+
+def test_solve_breakdown_on_zero_pivot(h):
+    from paper_1812_02056_gb300 import binding
+    n = 40
+    L = torch.eye(n, dtype=torch.float64, device=DEV)
+    L[17, 17] = 0.0
+    B = torch.ones((n, 2), dtype=torch.float64, device=DEV)
+    X = torch.empty_like(B)
+    st, _ = h.gb_chol_solve(n, 2, binding.GB_F64, L, n, None, n, B, 2, X, 2)
+    assert st == binding.GB_ERR_BREAKDOWN
+
+
+def test_refinement_reports_non_convergence(h):
+    from paper_1812_02056_gb300 import binding
+    n, nrhs = 64, 2
+    A = I.spd_gram(n, 3)
+    B = I.rhs(n, nrhs, 4)
+    Lo, _ = oracle.chol(A, 8)
+    Lbad = Lo * 1.5  # a factor of 2.25 A: refinement cannot reach 1e-30 in 1 step
+    X = torch.empty((n, nrhs), dtype=torch.float64, device=DEV)
+    st, stats = h.gb_chol_solve(n, nrhs, binding.GB_F64, _t(Lbad), n, _t(A), n, _t(B), nrhs, X,
+                                nrhs, 1e-30, 1)
+    assert st == binding.GB_ERR_NOT_CONVERGED and stats.converged == 0 and stats.iterations == 1

@@ -37,12 +37,14 @@ MUTATIONS = {
     "chol_checkpoint_not_moved": ("      z = c;\n    }\n    /* L_cc", "    }\n    /* L_cc"),
     "chol_col_first_term_dropped": ("for (int64_t k = z; k < c; ++k) v = v - L[i * ldl + k] * L[c * ldl + k];",
                                     "for (int64_t k = z + 1; k < c; ++k) v = v - L[i * ldl + k] * L[c * ldl + k];"),
-    "lu_no_divide": ("U[c * ldu + i] = v / lcc;", "U[c * ldu + i] = v;"),
-    "lu_update_transposed": ("sij = sij + L[i * ldl + k] * U[k * ldu + j];",
-                             "sij = sij + L[i * ldl + k] * U[j * ldu + k];"),
-    "lu_col_wrong_factor": ("v = v - L[i * ldl + k] * U[k * ldu + c];",
-                            "v = v - L[i * ldl + k] * U[c * ldu + k];"),
-    "lu_row_sign": ("v = v - L[c * ldl + k] * U[k * ldu + i];", "v = v + L[c * ldl + k] * U[k * ldu + i];"),
+    "lu_no_divide": ("U[c * ldu + i] = urow[i] / lcc;", "U[c * ldu + i] = urow[i];"),
+    "lu_update_transposed": ("srow[j] = srow[j] + lik * U[k * ldu + j];",
+                             "srow[j] = srow[j] + lik * U[j * ldu + k];"),
+    "lu_col_wrong_factor": ("ucol[k] = U[k * ldu + c];", "ucol[k] = U[c * ldu + k];"),
+    "lu_row_sign": ("urow[i] = urow[i] - lck * U[k * ldu + i];",
+                    "urow[i] = urow[i] + lck * U[k * ldu + i];"),
+    "lu_update_first_term_dropped": ("for (int64_t k = z; k < c; ++k) {\n              const double lik = L[i * ldl + k];\n              for (int64_t j = c; j < n; ++j) srow[j]",
+                                     "for (int64_t k = z + 1; k < c; ++k) {\n              const double lik = L[i * ldl + k];\n              for (int64_t j = c; j < n; ++j) srow[j]"),
 }
 
 
