@@ -216,6 +216,29 @@ gb_status gb_lu_solve(gb_handle *h, int64_t n, int64_t nrhs, gb_dtype factor_dt,
                       double *X, int64_t ldx, const gb_refine_opts *opts, gb_solve_stats *stats,
                       void *stream);
 
+/* --------------------------------------------------- the rank-s update */
+/*
+ * gb_rank_update -- the delayed update of Algorithms 1 and 2
+ * (arXiv:1812.02056 Sec. 2): S := X op(Y) "using a fast rectangular matrix
+ * multiplication", then C -= S, with S never stored.
+ *
+ *  dt       GB_F64: C, X, Y double, FP64 arithmetic (CUDA cores);
+ *           GB_F32: float, FP32 arithmetic (CUDA cores);
+ *           GB_MIX_BF16 / GB_MIX_F16: C, X, Y float; X and Y are rounded to
+ *           BF16 / FP16 and multiplied on the tensor cores (tcgen05) with FP32
+ *           accumulation; C stays FP32.
+ *  lower    1: update only C[i][j] with i >= j (Cholesky, op(Y) = Y^T, M = N
+ *           and X = Y allowed); 0: every element.
+ *  y_is_kxn 0: op(Y) = Y^T with Y stored N x K (row j of Y is column j of
+ *           op(Y)); 1: op(Y) = Y stored K x N (LU's R_U).
+ *  C        M x N (ldc); X M x K (ldx); Y as above (ldy).  Device pointers.
+ * Asynchronous on `stream`.  Workspace: the mixed dtypes pack X and Y into
+ * the handle's workspace.
+ */
+gb_status gb_rank_update(gb_handle *h, gb_dtype dt, int lower, int y_is_kxn, int64_t M,
+                         int64_t N, int64_t K, void *C, int64_t ldc, const void *X, int64_t ldx,
+                         const void *Y, int64_t ldy, void *stream);
+
 /* ---------------------------------------------------------- diagnostics */
 /* Phases of a factorization, as timed under GB_OPT_PROFILE. */
 typedef enum gb_phase {

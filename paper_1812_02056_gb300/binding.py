@@ -68,6 +68,8 @@ SIGNATURES = {
     "gb_backward_error": (_I32, [_P, _I32, _I64, _I32, _P, _I64, _P, _I64,
                                  ctypes.POINTER(_D), _P]),
     "gb_chol_factor_batched": (_I32, [_P, _I64, _P, _P, _P, _I32, _I64, _P, _P]),
+    "gb_rank_update": (_I32, [_P, _I32, _I32, _I32, _I64, _I64, _I64, _P, _I64, _P, _I64, _P,
+                              _I64, _P]),
     "gb_profile_read": (_I32, [_P, _P]),
     "gb_kernel_launches": (ctypes.c_uint64, []),
     "gb_measure_fma_peak": (_I32, [_P, _I32, ctypes.POINTER(_D)]),
@@ -236,6 +238,10 @@ class Handle:
         return self.lib.gb_chol_factor_batched(self.h, count, _ptr(n_arr), _ptr(ptr_arr),
                                                _ptr(lda_arr), dt, s, _ptr(info),
                                                _stream_ptr(stream))
+
+    def gb_rank_update(self, dt, lower, y_is_kxn, M, N, K, C, ldc, X, ldx, Y, ldy, stream=None):
+        return self.lib.gb_rank_update(self.h, dt, int(lower), int(y_is_kxn), M, N, K, _ptr(C), ldc,
+                                       _ptr(X), ldx, _ptr(Y), ldy, _stream_ptr(stream))
 
     # --------------------------------------------------- tensor conveniences
     def chol_factor(self, A, s: int, dtype: str = "f64", out=None, stream=None):

@@ -809,3 +809,61 @@ extern "C" gb_status gb_profile_read(gb_handle *h, gb_profile *out) {
   h->prof_pending.clear();
   return r;
 }
+
+extern "C" gb_status gb_rank_update(gb_handle *h, gb_dtype dt, int lower, int y_is_kxn, int64_t M,
+                                    int64_t N, int64_t K, void *C, int64_t ldc, const void *X,
+                                    int64_t ldx, const void *Y, int64_t ldy, void *stream) {
+  if (!h) return -1;
+  if (!valid_dtype(dt)) return -2;
+  if (M < 0) return -5;
+  if (N < 0) return -6;
+  if (K < 0) return -7;
+  if (M > 0 && N > 0 && !C) return -8;
+  if (ldc < std::max<int64_t>(1, N)) return -9;
+  if (M > 0 && K > 0 && !X) return -10;
+  if (ldx < std::max<int64_t>(1, K)) return -11;
+  if (N > 0 && K > 0 && !Y) return -12;
+  if (ldy < std::max<int64_t>(1, y_is_kxn ? N : K)) return -13;
+  if (M == 0 || N == 0 || K == 0) return GB_OK;
+  DeviceGuard g(h->device);
+  std::lock_guard<std::mutex> lk(h->mu);
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool nn = y_is_kxn != 0;
+  int *status = h->d_status;
+  GB_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), st));
+  if (dt == GB_F64) {
+    GB_CUDA_TRY(launch_update_simt<double>((double *)C, ldc, (const double *)X, ldx,
+                                           (const double *)Y, ldy, M, N, K, nn, lower != 0, 0,
+                                           status, st));
+  } else if (dt == GB_F32) {
+    GB_CUDA_TRY(launch_update_simt<float>((float *)C, ldc, (const float *)X, ldx,
+                                          (const float *)Y, ldy, M, N, K, nn, lower != 0, 0,
+                                          status, st));
+  } else {
+    TcUpdateArgs a{};
+    a.C = (float *)C;
+    a.ldc = ldc;
+    a.X = (const float *)X;
+    a.ldx = ldx;
+    a.Y = (const float *)Y;
+    a.ldy = ldy;
+    a.M = M;
+    a.N = N;
+    a.K = K;
+    a.nn = nn;
+    a.lower = lower != 0;
+    a.diag = 0;
+    a.f16 = dt == GB_MIX_F16;
+    a.status = status;
+    a.err = h->d_err;
+    a.spin_limit = h->spin_limit;
+    gb_status r = ws_reserve(h, WS_PANEL, tc_pack_bytes(M, N, K, nn), st);
+    if (r != GB_OK) return r;
+    a.pack = h->ws[WS_PANEL].ptr;
+    a.pack_bytes = h->ws[WS_PANEL].bytes;
+    cudaError_t e = launch_update_tc(a, st);
+    if (e == cudaErrorNotSupported) return GB_ERR_UNSUPPORTED;
+    GB_CUDA_TRY(e);
+  }
+  return GB_OK;
+}

@@ -53,7 +53,7 @@ struct gb_handle {
   int sm_count = 0;
   int inner_step = 64;
   int use_graphs = 1;
-  int tc_update = 0;
+  int tc_update = 1;
   int64_t spin_limit = 1 << 26;
   int *d_status = nullptr;   // scratch status word for host `info` pointers
   int *d_err = nullptr;      // device error word (DEV_ERR_*)

@@ -53,15 +53,18 @@ __global__ void __launch_bounds__(DIAG_THREADS)
     if (tid > c && tid < bw) S[tid][c] = S[tid][c] / lcc;
     __syncthreads();
     if (tid == 0) S[c][c] = lcc;
-    // subtract column c's product from the entries still to be finished:
-    // each entry receives its products in ascending k
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const int i = ty + 16 * a, j = tx + 16 * b;
-        if (j > c && j <= i && i < bw) S[i][j] = S[i][j] - S[i][c] * S[j][c];
-      }
+    // subtract column c's product from the entries still to be finished
+    // (lower triangle of the trailing (bw-c-1)^2 block, enumerated densely so
+    // that no lane idles); each entry receives its products in ascending k
+    const int m = bw - c - 1;
+    const int tri = m * (m + 1) / 2;
+    for (int e = tid; e < tri; e += DIAG_THREADS) {
+      int r = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+      while (r * (r + 1) / 2 > e) --r;
+      while ((r + 1) * (r + 2) / 2 <= e) ++r;
+      const int i = c + 1 + r, j = c + 1 + (e - r * (r + 1) / 2);
+      S[i][j] = S[i][j] - S[i][c] * S[j][c];
+    }
     __syncthreads();
   }
 #pragma unroll
@@ -73,7 +76,7 @@ __global__ void __launch_bounds__(DIAG_THREADS)
     }
 }
 
-constexpr int ROWS_PER_CTA = 128;
+constexpr int ROWS_PER_CTA = 64;  // one row per thread; small CTAs spread rows over all SMs
 
 // Rows [row0, row0 + nrows) of the panel columns [j0, j0 + bw): each thread
 // owns one row x and solves x_c = (a_c - sum_{k<c} x_k L_ck) / L_cc.
@@ -101,13 +104,16 @@ __global__ void __launch_bounds__(ROWS_PER_CTA)
     T x[B];
 #pragma unroll
     for (int c = 0; c < B; ++c) x[c] = X[tid][c];
+    // x_c is final once every x_k (k < c) has been subtracted; subtracting
+    // x_c's product from all later entries right away keeps each entry's
+    // products in ascending k while exposing independent work
 #pragma unroll
     for (int c = 0; c < B; ++c) {
       if (c < bw) {
-        T v = x[c];
+        const T xc = x[c] / LD[c][c];
+        x[c] = xc;
 #pragma unroll
-        for (int k = 0; k < c; ++k) v = v - x[k] * LD[c][k];
-        x[c] = v / LD[c][c];
+        for (int c2 = c + 1; c2 < B; ++c2) x[c2] = x[c2] - xc * LD[c2][c];
       }
     }
 #pragma unroll
@@ -144,13 +150,11 @@ __global__ void __launch_bounds__(DIAG_THREADS)
     }
     if (tid > c && tid < bw) S[c][tid] = S[c][tid] / p;  // U_ci
     __syncthreads();
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const int i = ty + 16 * a, j = tx + 16 * b;
-        if (i > c && j > c && i < bw && j < bw) S[i][j] = S[i][j] - S[i][c] * S[c][j];
-      }
+    const int m = bw - c - 1;  // trailing m x m block, enumerated densely
+    for (int e = tid; e < m * m; e += DIAG_THREADS) {
+      const int i = c + 1 + e / m, j = c + 1 + e % m;
+      S[i][j] = S[i][j] - S[i][c] * S[c][j];
+    }
     __syncthreads();
   }
 #pragma unroll
@@ -191,10 +195,9 @@ __global__ void __launch_bounds__(ROWS_PER_CTA)
 #pragma unroll
     for (int c = 0; c < B; ++c) {
       if (c < bw) {
-        T v = x[c];
+        const T xc = x[c];
 #pragma unroll
-        for (int k = 0; k < c; ++k) v = v - x[k] * UT[c][k];
-        x[c] = v;
+        for (int c2 = c + 1; c2 < B; ++c2) x[c2] = x[c2] - xc * UT[c2][c];
       }
     }
 #pragma unroll
@@ -229,10 +232,10 @@ __global__ void __launch_bounds__(ROWS_PER_CTA)
 #pragma unroll
   for (int c = 0; c < B; ++c) {
     if (c < bw) {
-      T v = y[c];
+      const T yc = y[c] / LD[c][c];
+      y[c] = yc;
 #pragma unroll
-      for (int k = 0; k < c; ++k) v = v - LD[c][k] * y[k];
-      y[c] = v / LD[c][c];
+      for (int c2 = c + 1; c2 < B; ++c2) y[c2] = y[c2] - LD[c2][c] * yc;
     }
   }
 #pragma unroll

