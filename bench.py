@@ -355,6 +355,118 @@ def run_ours(args):
     return 0
 
 
+# ------------------------------------------------------ rank-s update only
+def run_update(args):
+    """Time gb_rank_update (C -= R R^T, lower, R = m x K) on the tensor cores:
+    the delayed update of an n x n factorization's first block, m = n - K."""
+    import torch
+
+    from paper_1812_02056_gb300 import _build, binding
+    _build.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    h = binding.Handle(0)
+    peaks, src = load_peaks()
+    out = {"mode": "update", "n": args.n, "dtype": args.update_dtype, "results": []}
+    dt = binding.DTYPES[args.update_dtype]
+    g = torch.Generator(device=dev).manual_seed(5)
+    for K in [int(k) for k in args.ks.split(",")]:
+        m = args.n - K
+        C = torch.randn((m, m), device=dev, generator=g)
+        R = torch.randn((m, K), device=dev, generator=g)
+        stream = torch.cuda.current_stream()
+
+        def call():
+            binding.check(h.gb_rank_update(dt, 1, 0, m, m, K, C, m, R, K, R, K, stream),
+                          "gb_rank_update")
+
+        for _ in range(args.warmup):
+            call()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = binding.kernel_launches()
+        e0.record(stream)
+        for _ in range(args.reps):
+            call()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.reps
+        flops = 2.0 * K * m * (m + 1) / 2.0
+        cbytes = 8.0 * m * (m + 1) / 2.0  # FP32 lower triangle read + written
+        tflops = flops / (ms * 1e-3) / 1e12
+        out["results"].append({
+            "K": K, "m": m, "ms": ms, "tflops": tflops,
+            "frac_of_bf16_peak": tflops / peaks["bf16_tflops"],
+            "hbm_bound_tflops": peaks["hbm_gbs"] * 1e9 * flops / cbytes / 1e12,
+            "launches_per_call": (binding.kernel_launches() - l0) / args.reps})
+        del C, R
+        torch.cuda.empty_cache()
+    out["peaks"] = {"bf16_tflops": peaks["bf16_tflops"], "hbm_gbs": peaks["hbm_gbs"], "source": src}
+    print(json.dumps(out))
+    h.close()
+    return 0
+
+
+# ------------------------------------------------- mixed precision + IR
+def run_mixed(args):
+    """Time to an FP64-accurate solution (16 RHS) at n with cond(A) = 1e4:
+    plain FP64 factor + solve against mixed factors + FP64 refinement."""
+    import numpy as np
+    import torch
+
+    from paper_1812_02056_gb300 import _build, binding, inputs
+    _build.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    h = binding.Handle(0)
+    n, nrhs = args.n, 16
+    t0 = time.perf_counter()
+    A = inputs.spd_logspaced(n, inputs.seed_for(inputs.W_MIXED), cond=1e4, device=dev)
+    B = torch.from_numpy(inputs.rhs(n, nrhs, inputs.seed_for(inputs.W_MIXED, 1))).to(dev)
+    gen_s = time.perf_counter() - t0
+    out = {"mode": "mixed", "n": n, "nrhs": nrhs, "cond": 1e4, "input_generation_s": gen_s,
+           "results": {}}
+    stream = torch.cuda.current_stream()
+    xref = None
+    for name, s in [("f64", args.s_f64), ("f32", args.s_mixed), ("mix_f16", args.s_mixed),
+                    ("mix_bf16", args.s_mixed)]:
+        dt = binding.DTYPES[name]
+        Ain = A.float() if name == "f32" else A
+        L = torch.empty((n, n), dtype=torch.float64 if name == "f64" else torch.float32, device=dev)
+        info = torch.zeros(1, dtype=torch.int32, device=dev)
+        X = torch.empty_like(B)
+        runs = []
+        for rep in range(1 + args.reps):
+            torch.cuda.synchronize()
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            binding.check(h.gb_chol_factor(n, s, dt, Ain, n, L, n, info, stream), "factor")
+            e1.record(stream)
+            st, stats = h.gb_chol_solve(n, nrhs, dt, L, n, None if name == "f64" else A, n, B,
+                                        nrhs, X, nrhs, 1e-14, 50, stream)
+            e2.record(stream)
+            torch.cuda.synchronize()
+            runs.append((e0.elapsed_time(e1), e1.elapsed_time(e2), st, stats.iterations,
+                         stats.eta, int(info.item())))
+        fm, sm, st, it, eta, inf = runs[-1]
+        if name == "f64":
+            xref = X.clone()
+        res = {"s": s, "factor_ms": fm, "solve_ms": sm, "time_to_solution_ms": fm + sm,
+               "status": st, "info": inf, "ir_iterations": it, "eta": eta,
+               "factor_gflops": n ** 3 / 3 / (fm * 1e-3) / 1e9}
+        Xh = X.double()
+        R = B - A @ Xh
+        den = A.abs().sum(1).max() * Xh.abs().max(0).values + B.abs().max(0).values
+        res["eta_host"] = float((R.abs().max(0).values / den).max())
+        if xref is not None:
+            res["max_rel_diff_vs_fp64_solve"] = float((Xh - xref).abs().max() / xref.abs().max())
+        out["results"][name] = res
+        del L
+        torch.cuda.empty_cache()
+    print(json.dumps(out))
+    h.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -370,9 +482,21 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip sweeps and accuracy figures")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--mode", choices=["chol", "update", "mixed"], default="chol",
+                    help="chol: the benchmark line; update: the tensor-core rank-s update "
+                         "alone; mixed: FP64 vs mixed-precision time to solution")
+    ap.add_argument("--ks", default="256,512,1024,2048")
+    ap.add_argument("--update-dtype", default="mix_bf16")
+    ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--s-f64", type=int, default=256)
+    ap.add_argument("--s-mixed", type=int, default=1024)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "update":
+        return run_update(args)
+    if args.mode == "mixed":
+        return run_mixed(args)
     return run_ours(args)
 
 

@@ -77,6 +77,11 @@ const char *gb_status_string(gb_status st);
  *              FP64; the panel rows in FP32; the delayed rank-s update runs
  *              on the tensor cores with BF16 operands and FP32 accumulation.
  *  GB_MIX_F16  as GB_MIX_BF16 with FP16 operands.
+ *  GB_MIX_BF16X3  as GB_MIX_BF16, but each operand of the update is split
+ *              into three BF16 planes (x = p0 + p1 + p2, each the rounding of
+ *              the remainder) and the six leading plane products are
+ *              accumulated: the update is accurate to about FP32 at one
+ *              sixth of the BF16 tensor rate.
  * Mixed factors are meant to be refined back to FP64 accuracy by
  * gb_chol_solve / gb_lu_solve given the original FP64 matrix.
  */
@@ -84,7 +89,8 @@ typedef enum gb_dtype {
   GB_F64 = 0,
   GB_F32 = 1,
   GB_MIX_BF16 = 2,
-  GB_MIX_F16 = 3
+  GB_MIX_F16 = 3,
+  GB_MIX_BF16X3 = 4
 } gb_dtype;
 
 /* ------------------------------------------------------------------ handle */
@@ -226,7 +232,8 @@ gb_status gb_lu_solve(gb_handle *h, int64_t n, int64_t nrhs, gb_dtype factor_dt,
  *           GB_F32: float, FP32 arithmetic (CUDA cores);
  *           GB_MIX_BF16 / GB_MIX_F16: C, X, Y float; X and Y are rounded to
  *           BF16 / FP16 and multiplied on the tensor cores (tcgen05) with FP32
- *           accumulation; C stays FP32.
+ *           accumulation; C stays FP32.  GB_MIX_BF16X3: three-plane BF16
+ *           split of X and Y, six tensor-core products (about FP32 accuracy).
  *  lower    1: update only C[i][j] with i >= j (Cholesky, op(Y) = Y^T, M = N
  *           and X = Y allowed); 0: every element.
  *  y_is_kxn 0: op(Y) = Y^T with Y stored N x K (row j of Y is column j of

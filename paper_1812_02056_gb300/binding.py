@@ -28,8 +28,9 @@ GB_ERR_UNSUPPORTED = -1006
 GB_ERR_BREAKDOWN = -1007
 GB_ERR_STATE = -1008
 
-GB_F64, GB_F32, GB_MIX_BF16, GB_MIX_F16 = 0, 1, 2, 3
-DTYPES = {"f64": GB_F64, "f32": GB_F32, "mix_bf16": GB_MIX_BF16, "mix_f16": GB_MIX_F16}
+GB_F64, GB_F32, GB_MIX_BF16, GB_MIX_F16, GB_MIX_BF16X3 = 0, 1, 2, 3, 4
+DTYPES = {"f64": GB_F64, "f32": GB_F32, "mix_bf16": GB_MIX_BF16, "mix_f16": GB_MIX_F16,
+          "mix_bf16x3": GB_MIX_BF16X3}
 
 GB_OPT_INNER_STEP, GB_OPT_USE_GRAPHS, GB_OPT_TC_UPDATE, GB_OPT_SPIN_LIMIT = 1, 2, 3, 4
 GB_OPT_PROFILE = 5

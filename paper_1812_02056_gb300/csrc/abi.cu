@@ -71,7 +71,9 @@ bool is_device_ptr(const void *p) {
 
 size_t elem_size_factor(gb_dtype dt) { return dt == GB_F64 ? 8 : 4; }
 size_t elem_size_input(gb_dtype dt) { return dt == GB_F32 ? 4 : 8; }
-bool valid_dtype(int dt) { return dt >= GB_F64 && dt <= GB_MIX_F16; }
+bool valid_dtype(int dt) { return dt >= GB_F64 && dt <= GB_MIX_BF16X3; }
+bool is_mixed(gb_dtype dt) { return dt == GB_MIX_BF16 || dt == GB_MIX_F16 || dt == GB_MIX_BF16X3; }
+int split_of(gb_dtype dt) { return dt == GB_MIX_BF16X3 ? 3 : 1; }
 
 struct DeviceGuard {
   int prev = -1;
@@ -261,12 +263,12 @@ gb_status chol_blocked(gb_handle *h, int64_t n, int64_t s, T *W, int64_t ld, int
       T *C = W + pe * ld + pe;
       const T *R = W + pe * ld + z;
       bool done = false;
-      const bool tc = (dt == GB_MIX_BF16 || dt == GB_MIX_F16) && h->tc_update;
+      const bool tc = is_mixed(dt) && h->tc_update;
       PhaseTimer t(h, st, GB_PHASE_UPDATE, update_flops(m, m, sb, true),
                    update_bytes(m, m, sb, true, sizeof(T)) -
                        (tc ? (double)m * sb * 2.0 * (sizeof(T) - 2) : 0.0));
       if constexpr (sizeof(T) == 4) {
-        if ((dt == GB_MIX_BF16 || dt == GB_MIX_F16) && h->tc_update) {
+        if (is_mixed(dt) && h->tc_update) {
           TcUpdateArgs a{};
           a.C = reinterpret_cast<float *>(C);
           a.ldc = ld;
@@ -281,10 +283,11 @@ gb_status chol_blocked(gb_handle *h, int64_t n, int64_t s, T *W, int64_t ld, int
           a.lower = true;
           a.diag = 0;
           a.f16 = (dt == GB_MIX_F16);
+          a.split = split_of(dt);
           a.status = status;
           a.err = h->d_err;
           a.spin_limit = h->spin_limit;
-          const size_t pb = tc_pack_bytes(m, m, sb, false);
+          const size_t pb = tc_pack_bytes(m, m, sb, false, split_of(dt));
           gb_status ws = ws_reserve(h, WS_PANEL, pb, st);
           if (ws != GB_OK) return ws;
           a.pack = h->ws[WS_PANEL].ptr;
@@ -350,12 +353,12 @@ gb_status lu_blocked(gb_handle *h, int64_t n, int64_t s, T *W, int64_t ld, int *
       const T *RL = W + pe * ld + z;
       const T *RU = W + z * ld + pe;
       bool done = false;
-      const bool tc = (dt == GB_MIX_BF16 || dt == GB_MIX_F16) && h->tc_update;
+      const bool tc = is_mixed(dt) && h->tc_update;
       PhaseTimer t(h, st, GB_PHASE_UPDATE, update_flops(m, m, sb, false),
                    update_bytes(m, m, sb, false, sizeof(T)) -
                        (tc ? 2.0 * (double)m * sb * (sizeof(T) - 2) : 0.0));
       if constexpr (sizeof(T) == 4) {
-        if ((dt == GB_MIX_BF16 || dt == GB_MIX_F16) && h->tc_update) {
+        if (is_mixed(dt) && h->tc_update) {
           TcUpdateArgs a{};
           a.C = reinterpret_cast<float *>(C);
           a.ldc = ld;
@@ -370,10 +373,11 @@ gb_status lu_blocked(gb_handle *h, int64_t n, int64_t s, T *W, int64_t ld, int *
           a.lower = false;
           a.diag = 0;
           a.f16 = (dt == GB_MIX_F16);
+          a.split = split_of(dt);
           a.status = status;
           a.err = h->d_err;
           a.spin_limit = h->spin_limit;
-          const size_t pb = tc_pack_bytes(m, m, sb, true);
+          const size_t pb = tc_pack_bytes(m, m, sb, true, split_of(dt));
           gb_status ws = ws_reserve(h, WS_PANEL, pb, st);
           if (ws != GB_OK) return ws;
           a.pack = h->ws[WS_PANEL].ptr;
@@ -537,9 +541,11 @@ gb_status solve_common(bool is_lu, gb_handle *h, int64_t n, int64_t nrhs, const 
     for (int64_t c = 0; c < nrhs; ++c) {
       const double rn = hn[1 + c], xn = hn[1 + nrhs + c], bn = hn[1 + 2 * nrhs + c];
       const double den = anorm * xn + bn;
-      const double e = den > 0 ? rn / den : (rn > 0 ? INFINITY : 0.0);
-      if (!(e <= eta)) eta = e;  // NaN propagates
+      double e = den > 0 ? rn / den : (rn > 0 ? INFINITY : 0.0);
+      if (!std::isfinite(e) || !std::isfinite(den)) e = INFINITY;  // NaN/Inf: not converged
+      if (e > eta) eta = e;
     }
+    if (!std::isfinite(eta)) break;  // the iterate is lost; report non-convergence
     if (eta <= tol || it >= max_iter) break;
     if ((r = tri_solve<Tf>(h, is_lu, F, ldf, R, nrhs, n, nrhs, st)) != GB_OK) return r;
     GB_CUDA_TRY(launch_axpy_cols(X, ldx, R, nrhs, n, nrhs, st));
@@ -854,10 +860,11 @@ extern "C" gb_status gb_rank_update(gb_handle *h, gb_dtype dt, int lower, int y_
     a.lower = lower != 0;
     a.diag = 0;
     a.f16 = dt == GB_MIX_F16;
+    a.split = split_of(dt);
     a.status = status;
     a.err = h->d_err;
     a.spin_limit = h->spin_limit;
-    gb_status r = ws_reserve(h, WS_PANEL, tc_pack_bytes(M, N, K, nn), st);
+    gb_status r = ws_reserve(h, WS_PANEL, tc_pack_bytes(M, N, K, nn, split_of(dt)), st);
     if (r != GB_OK) return r;
     a.pack = h->ws[WS_PANEL].ptr;
     a.pack_bytes = h->ws[WS_PANEL].bytes;

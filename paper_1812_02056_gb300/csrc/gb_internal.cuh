@@ -133,13 +133,15 @@ struct TcUpdateArgs {
   bool lower;
   int64_t diag;
   bool f16;          // FP16 operands instead of BF16
+  int split;         // 1: plain 16-bit operands; 3: three-plane BF16 split
+                     //    (the six leading plane products, ~FP32 accuracy)
   const int *status;
   int *err;
   int64_t spin_limit;
   void *pack;        // workspace for the packed operands
   size_t pack_bytes;
 };
-size_t tc_pack_bytes(int64_t M, int64_t N, int64_t K, bool nn);
+size_t tc_pack_bytes(int64_t M, int64_t N, int64_t K, bool nn, int split);
 cudaError_t launch_update_tc(const TcUpdateArgs &a, cudaStream_t st);
 bool tc_supported(int device);
 

@@ -156,6 +156,11 @@ constexpr int RES_ROWS = 32;
 constexpr int RES_KC = 128;
 constexpr int RES_NC = 16;
 
+__device__ __forceinline__ double finite_abs(double v) {
+  const double a = fabs(v);
+  return a <= 1.7976931348623157e308 ? a : __longlong_as_double(0x7ff0000000000000LL);
+}
+
 __device__ __forceinline__ void atomic_max_nonneg(double *addr, double v) {
   // non-negative doubles order like their bit patterns as signed integers
   atomicMax(reinterpret_cast<long long *>(addr), __double_as_longlong(v));
@@ -205,10 +210,10 @@ __global__ void __launch_bounds__(256)
         if (lane == 0 && i < n && c < cols) {
           const double r = B[i * ldb + c0 + c] - v;
           R[i * ldr + c0 + c] = r;
-          if (norms) {
-            atomic_max_nonneg(&norms[c0 + c], fabs(r));                      // ||r||_inf
-            atomic_max_nonneg(&norms[nrhs + c0 + c], fabs(X[i * ldx + c0 + c]));  // ||x||_inf
-            atomic_max_nonneg(&norms[2 * nrhs + c0 + c], fabs(B[i * ldb + c0 + c]));  // ||b||_inf
+          if (norms) {  // a non-finite value counts as +inf in every norm
+            atomic_max_nonneg(&norms[c0 + c], finite_abs(r));                       // ||r||_inf
+            atomic_max_nonneg(&norms[nrhs + c0 + c], finite_abs(X[i * ldx + c0 + c]));  // ||x||_inf
+            atomic_max_nonneg(&norms[2 * nrhs + c0 + c], finite_abs(B[i * ldb + c0 + c]));
           }
         }
       }
@@ -224,7 +229,7 @@ __global__ void inf_norm_rows_kernel(const double *__restrict__ A, int64_t lda, 
   double s = 0.0;
   for (int64_t k = lane; k < n; k += 32) s += fabs(A[i * lda + k]);
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) atomic_max_nonneg(out, s);
+  if (lane == 0) atomic_max_nonneg(out, finite_abs(s));
 }
 
 __global__ void axpy_cols_kernel(double *X, int64_t ldx, const double *D, int64_t ldd, int64_t n,

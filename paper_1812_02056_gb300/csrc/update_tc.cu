@@ -26,6 +26,9 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
 
 #include "gb_internal.cuh"
 
@@ -33,11 +36,15 @@ namespace gb {
 namespace {
 
 constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
-constexpr int THREADS = 128;
-constexpr uint32_t TMEM_COLS = 256;
-constexpr uint32_t A_STAGE = BM * BK * 2;  // 16 KiB
-constexpr uint32_t B_STAGE = BN * BK * 2;  // 32 KiB
-constexpr size_t SMEM_BYTES = (size_t)STAGES * (A_STAGE + B_STAGE) + 1024 + 256;
+constexpr int EPI_WARPS = 4;
+constexpr int THREADS = 64 + EPI_WARPS * 32;  // producer, MMA, 4 epilogue warps
+constexpr uint32_t TMEM_COLS = 512;           // two 128 x 256 FP32 accumulators
+constexpr uint32_t A_STAGE = BM * BK * 2;     // 16 KiB
+constexpr uint32_t B_STAGE = BN * BK * 2;     // 32 KiB
+constexpr uint32_t STAGING = 32 * 32 * 4;     // one 32 x 32 FP32 reduce box
+constexpr size_t SMEM_BYTES =
+    (size_t)STAGES * (A_STAGE + B_STAGE) + EPI_WARPS * 2 * STAGING + 1024 + 256;
+static_assert(SMEM_BYTES <= 232448, "shared memory per CTA");
 
 // ------------------------------------------------------------ PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -74,8 +81,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 }
 
 // Bounded wait on phase `parity` of `bar`: false on timeout or abort.
-__device__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsigned long long deadline, int *err,
+__device__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsigned long long wait_ns, int *err,
                           volatile int *abort_flag) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long deadline = now_ns() + wait_ns;
   while (!mbar_try_wait(bar, parity)) {
     if (*abort_flag) return false;
     if (now_ns() > deadline) {
@@ -161,16 +170,62 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
          ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
-// ---------------------------------------------------------------- kernels
+// TMA reduce-add of a 32 x 32 FP32 box from shared memory into global
+// memory (the L2 performs the read-modify-write).
+__device__ __forceinline__ void tma_reduce_add_2d(const CUtensorMap *map, const void *src, int x,
+                                                  int y) {
+  asm volatile(
+      "cp.reduce.async.bulk.tensor.2d.global.shared::cta.add.tile.bulk_group"
+      " [%0, {%2, %3}], [%1];" ::"l"(reinterpret_cast<uint64_t>(map)),
+      "r"(smem_u32(src)), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void bulk_commit() {
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() {
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Valid output tiles in row-major tile order, strided over the persistent CTAs.
+struct TileIter {
+  int64_t t, total, nbj, stride, diag;
+  bool lower;
+  __device__ bool next(int64_t &m0, int64_t &n0) {
+    while (t < total) {
+      const int64_t bi = t / nbj, bj = t % nbj;
+      t += stride;
+      m0 = bi * BM;
+      n0 = bj * BN;
+      if (!lower || m0 + BM - 1 + diag >= n0) return true;  // skip tiles above the diagonal
+    }
+    return false;
+  }
+};
+
+// ---------------------------------------------------------------- kernel
+// Persistent: one CTA per SM walks the tile list.  Warp 0 = TMA producer,
+// warp 1 = MMA issuer (and tensor-memory owner), warps 2..5 = epilogue.
+// Two 256-column accumulators let the epilogue of one tile run while the
+// MMAs of the next accumulate.
 template <bool LOWER>
 __global__ void __launch_bounds__(THREADS, 1)
     tc_update_kernel(const __grid_constant__ CUtensorMap map_a,
-                     const __grid_constant__ CUtensorMap map_b, float *__restrict__ C, int64_t ldc,
+                     const __grid_constant__ CUtensorMap map_b,
+                     const __grid_constant__ CUtensorMap map_c, float *__restrict__ C, int64_t ldc,
                      int64_t M, int64_t N, int nk, int64_t diag, uint32_t idesc, const int *status,
-                     int *err, long long wait_ns, int vec_ok) {
+                     int *err, long long wait_ns, int use_tma_store, int vec_ok) {
   extern __shared__ uint8_t smem_raw[];
-  const int64_t m0 = (int64_t)blockIdx.y * BM, n0 = (int64_t)blockIdx.x * BN;
-  if (LOWER && m0 + BM - 1 + diag < n0) return;  // tile strictly above the diagonal
   if (*reinterpret_cast<const volatile int *>(status) != 0) return;
   // a CTA whose wait expired has already raised the error word: later CTAs
   // leave at once instead of waiting out their own deadlines
@@ -179,11 +234,13 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint8_t *smem = reinterpret_cast<uint8_t *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   uint8_t *sA = smem;
-  uint8_t *sB = smem + STAGES * A_STAGE;
-  uint64_t *full = reinterpret_cast<uint64_t *>(sB + STAGES * B_STAGE);
+  uint8_t *sB = sA + STAGES * A_STAGE;
+  uint8_t *sStage = sB + STAGES * B_STAGE;  // EPI_WARPS x 2 x 4 KiB, 1 KiB aligned
+  uint64_t *full = reinterpret_cast<uint64_t *>(sStage + EPI_WARPS * 2 * STAGING);
   uint64_t *empty = full + STAGES;
-  uint64_t *done = empty + STAGES;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+  uint64_t *acc_full = empty + STAGES;
+  uint64_t *acc_empty = acc_full + 2;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 2);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -192,7 +249,10 @@ __global__ void __launch_bounds__(THREADS, 1)
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(done, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], EPI_WARPS);
+    }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -201,68 +261,135 @@ __global__ void __launch_bounds__(THREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const unsigned long long deadline = now_ns() + (unsigned long long)wait_ns;
+  const unsigned long long deadline = (unsigned long long)wait_ns;  // per wait
 
-  if (warp == 0 && lane == 0) {
+  const int64_t nbi = (M + BM - 1) / BM, nbj = (N + BN - 1) / BN;
+  TileIter it{(int64_t)blockIdx.x, nbi * nbj, nbj, (int64_t)gridDim.x, diag, LOWER};
+  int64_t m0 = 0, n0 = 0;
+
+  if (warp == 0) {
     // ------------------------------------------------ TMA producer
-    for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % STAGES;
-      const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-      if (kb >= STAGES && !mbar_wait(&empty[s], ph ^ 1u, deadline, err, abort_flag)) break;
-      mbar_expect_tx(&full[s], A_STAGE + B_STAGE);
-      tma_load_2d(sA + s * A_STAGE, &map_a, &full[s], kb * BK, (int)m0);
-      tma_load_2d(sB + s * B_STAGE, &map_b, &full[s], kb * BK, (int)n0);
+    if (lane == 0) {
+      uint32_t g = 0;
+      bool ok = true;
+      while (ok && it.next(m0, n0)) {
+        for (int kb = 0; kb < nk; ++kb, ++g) {
+          const uint32_t s = g % STAGES, ph = (g / STAGES) & 1u;
+          if (g >= STAGES && !mbar_wait(&empty[s], ph ^ 1u, deadline, err, abort_flag)) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(&full[s], A_STAGE + B_STAGE);
+          tma_load_2d(sA + s * A_STAGE, &map_a, &full[s], kb * BK, (int)m0);
+          tma_load_2d(sB + s * B_STAGE, &map_b, &full[s], kb * BK, (int)n0);
+        }
+      }
     }
-  } else if (warp == 1 && lane == 0) {
+    __syncwarp();
+  } else if (warp == 1) {
     // ------------------------------------------------ MMA issuer
-    for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % STAGES;
-      const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-      if (!mbar_wait(&full[s], ph, deadline, err, abort_flag)) break;
+    if (lane == 0) {
+      uint32_t g = 0, i = 0;
+      bool ok = true;
+      while (ok && it.next(m0, n0)) {
+        const uint32_t buf = i & 1u, use = i >> 1;
+        if (use > 0 && !mbar_wait(&acc_empty[buf], (use - 1) & 1u, deadline, err, abort_flag))
+          break;
+        tc_fence_after();
+        const uint32_t d = tmem + buf * (TMEM_COLS / 2);
+        for (int kb = 0; kb < nk; ++kb, ++g) {
+          const uint32_t s = g % STAGES, ph = (g / STAGES) & 1u;
+          if (!mbar_wait(&full[s], ph, deadline, err, abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a0 = smem_u32(sA + s * A_STAGE), b0 = smem_u32(sB + s * B_STAGE);
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk)
+            mma_f16(d, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), idesc,
+                    (kb | kk) != 0 ? 1u : 0u);
+          mma_commit(&empty[s]);
+        }
+        mma_commit(&acc_full[buf]);
+        ++i;
+      }
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------ epilogue (warps 2..5)
+    const int e = warp - 2;                // 0..3
+    const int q = warp & 3;                // tensor-memory lane quarter this warp may read
+    uint8_t *stage0 = sStage + (size_t)e * 2 * STAGING;
+    uint32_t i = 0, chunks = 0;
+    while (it.next(m0, n0)) {
+      const uint32_t buf = i & 1u, use = i >> 1;
+      if (!mbar_wait(&acc_full[buf], use & 1u, deadline, err, abort_flag)) break;
       tc_fence_after();
-      const uint32_t a0 = smem_u32(sA + s * A_STAGE), b0 = smem_u32(sB + s * B_STAGE);
+      const int64_t row0 = m0 + q * 32;
+      const int64_t row = row0 + lane;
+      for (int c = 0; c < BN / 32; ++c) {
+        const int64_t col0 = n0 + c * 32;
+        if (col0 >= N || row0 >= M) break;                  // warp-uniform
+        if (LOWER && row0 + 31 + diag < col0) break;        // chunk above the diagonal
+        float v[32];
+        tmem_ld_32x32(tmem + buf * (TMEM_COLS / 2) + ((uint32_t)(q * 32) << 16) + (uint32_t)(c * 32),
+                      v);
+        if (*abort_flag) continue;
+        if (use_tma_store) {
+          uint8_t *sb = stage0 + (chunks & 1u) * STAGING;
+          if (chunks >= 2) {
+            if (lane == 0) bulk_wait_read<1>();  // the reduce that last read `sb` is done
+            __syncwarp();
+          }
 #pragma unroll
-      for (int kk = 0; kk < BK / 16; ++kk)
-        mma_f16(tmem, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), idesc,
-                (kb | kk) != 0 ? 1u : 0u);
-      mma_commit(&empty[s]);
-    }
-    mma_commit(done);
-  }
-  __syncwarp();
-
-  // ---------------------------------------------------- epilogue
-  const bool ok = mbar_wait(done, 0, deadline, err, abort_flag);
-  tc_fence_after();
-  const int64_t row = m0 + warp * 32 + lane;
-  const bool store = ok && !*abort_flag && row < M;
-#pragma unroll 1
-  for (int c = 0; c < BN / 32; ++c) {
-    const int64_t col0 = n0 + c * 32;
-    if (col0 >= N) break;  // uniform over the CTA
-    if (LOWER && m0 + BM - 1 + diag < col0) break;
-    float v[32];
-    tmem_ld_32x32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), v);
-    if (!store) continue;
-    float *crow = C + row * ldc + col0;
-    const bool full_row = col0 + 32 <= N && (!LOWER || row + diag >= col0 + 31);
-    if (vec_ok && full_row) {
+          for (int q4 = 0; q4 < 8; ++q4) {
+            float4 w;
+            float *wp = &w.x;
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        float4 x = *reinterpret_cast<float4 *>(crow + 4 * q);
-        x.x -= v[4 * q + 0];
-        x.y -= v[4 * q + 1];
-        x.z -= v[4 * q + 2];
-        x.w -= v[4 * q + 3];
-        *reinterpret_cast<float4 *>(crow + 4 * q) = x;
+            for (int u = 0; u < 4; ++u) {
+              const int64_t col = col0 + q4 * 4 + u;
+              wp[u] = (!LOWER || row + diag >= col) ? -v[q4 * 4 + u] : -0.0f;  // x + -0 == x
+            }
+            // 128-byte swizzle: 16-byte chunk q4 of row `lane` sits at q4 ^ (lane % 8)
+            *reinterpret_cast<float4 *>(sb + lane * 128 + ((q4 ^ (lane & 7)) * 16)) = w;
+          }
+          fence_proxy_async_smem();
+          __syncwarp();
+          if (lane == 0) {
+            tma_reduce_add_2d(&map_c, sb, (int)col0, (int)row0);
+            bulk_commit();
+          }
+          ++chunks;
+        } else if (row < M) {
+          float *crow = C + row * ldc + col0;
+          const bool full_row = col0 + 32 <= N && (!LOWER || row + diag >= col0 + 31);
+          if (vec_ok && full_row) {
+#pragma unroll
+            for (int q4 = 0; q4 < 8; ++q4) {
+              float4 x = *reinterpret_cast<float4 *>(crow + 4 * q4);
+              x.x -= v[4 * q4 + 0];
+              x.y -= v[4 * q4 + 1];
+              x.z -= v[4 * q4 + 2];
+              x.w -= v[4 * q4 + 3];
+              *reinterpret_cast<float4 *>(crow + 4 * q4) = x;
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const int64_t col = col0 + j;
+              if (col < N && (!LOWER || row + diag >= col)) crow[j] -= v[j];
+            }
+          }
+        }
       }
-    } else {
-#pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const int64_t col = col0 + j;
-        if (col < N && (!LOWER || row + diag >= col)) crow[j] -= v[j];
-      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[buf]);
+      ++i;
     }
+    if (lane == 0) bulk_wait_all();
+    __syncwarp();
   }
   tc_fence_before();
   __syncthreads();
@@ -279,23 +406,49 @@ template <>
 __device__ __forceinline__ __half to16<__half>(float x) {
   return __float2half_rn(x);
 }
+template <typename T16>
+__device__ __forceinline__ float from16(T16 x);
+template <>
+__device__ __forceinline__ float from16<__nv_bfloat16>(__nv_bfloat16 x) {
+  return __bfloat162float(x);
+}
+template <>
+__device__ __forceinline__ float from16<__half>(__half x) {
+  return __half2float(x);
+}
 
-// out[i * Kp + k] = round16(X[i * ldx + k]) for k < K, 0 for K <= k < Kp.
+// Planes of x: p0 = round16(x), p1 = round16(x - p0), p2 = round16(x - p0 - p1)
+// (each difference is exact in FP32).  Term t of the packed row uses plane
+// (code >> 2t) & 3.
+template <typename T16>
+__device__ __forceinline__ void split_planes(float x, T16 (&p)[3]) {
+  p[0] = to16<T16>(x);
+  const float r1 = x - from16<T16>(p[0]);
+  p[1] = to16<T16>(r1);
+  p[2] = to16<T16>(r1 - from16<T16>(p[1]));
+}
+
+// out[i][t * Kp + k] = plane_t(X[i * ldx + k]) for k < K, 0 for K <= k < Kp.
 template <typename T16>
 __global__ void pack_rows_kernel(const float *__restrict__ X, int64_t ldx, int64_t rows,
-                                 int64_t K, int64_t Kp, T16 *__restrict__ out) {
+                                 int64_t K, int64_t Kp, int terms, uint32_t code,
+                                 T16 *__restrict__ out) {
   const int64_t total = rows * Kp;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = e / Kp, k = e % Kp;
-    out[e] = to16<T16>(k < K ? X[i * ldx + k] : 0.0f);
+    T16 p[3];
+    split_planes<T16>(k < K ? X[i * ldx + k] : 0.0f, p);
+    T16 *o = out + i * (Kp * terms) + k;
+    for (int t = 0; t < terms; ++t) o[t * Kp] = p[(code >> (2 * t)) & 3u];
   }
 }
 
-// out[j * Kp + k] = round16(Y[k * ldy + j]) (K x N row-major -> N x Kp K-major).
+// Same from a K x N row-major Y: out[j][t * Kp + k] = plane_t(Y[k * ldy + j]).
 template <typename T16>
 __global__ void pack_transpose_kernel(const float *__restrict__ Y, int64_t ldy, int64_t K,
-                                      int64_t N, int64_t Kp, T16 *__restrict__ out) {
+                                      int64_t N, int64_t Kp, int terms, uint32_t code,
+                                      T16 *__restrict__ out) {
   __shared__ float t[32][33];
   const int64_t k0 = (int64_t)blockIdx.y * 32, j0 = (int64_t)blockIdx.x * 32;
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
@@ -305,7 +458,12 @@ __global__ void pack_transpose_kernel(const float *__restrict__ Y, int64_t ldy, 
   __syncthreads();
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
     const int64_t j = j0 + r, k = k0 + threadIdx.x;
-    if (j < N && k < Kp) out[j * Kp + k] = to16<T16>(t[threadIdx.x][r]);
+    if (j < N && k < Kp) {
+      T16 p[3];
+      split_planes<T16>(t[threadIdx.x][r], p);
+      T16 *o = out + j * (Kp * terms) + k;
+      for (int u = 0; u < terms; ++u) o[u * Kp] = p[(code >> (2 * u)) & 3u];
+    }
   }
 }
 
@@ -330,12 +488,13 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// 2-D map over a dense rows x Kp 16-bit K-major buffer, box 64 x box_rows.
-bool make_map(CUtensorMap *map, void *base, int64_t rows, int64_t Kp, int box_rows, bool f16) {
+// 2-D map over a dense rows x cols 16-bit K-major buffer, box 64 x box_rows.
+bool make_operand_map(CUtensorMap *map, void *base, int64_t rows, int64_t cols, int box_rows,
+                      bool f16) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return false;
-  cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)Kp * 2};
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
   cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = enc(map, f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
@@ -345,26 +504,57 @@ bool make_map(CUtensorMap *map, void *base, int64_t rows, int64_t Kp, int box_ro
   return r == CUDA_SUCCESS;
 }
 
+// FP32 map over C (M x N, ldc), 32 x 32 boxes with the 128-byte swizzle, for
+// the reduce-add epilogue.  Needs a 16-byte aligned C and ldc % 4 == 0.
+bool make_c_map(CUtensorMap *map, float *C, int64_t ldc, int64_t M, int64_t N) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return false;
+  if ((reinterpret_cast<uintptr_t>(C) & 15) != 0 || (ldc & 3) != 0) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)M};
+  cuuint64_t strides[1] = {(cuuint64_t)ldc * 4};
+  cuuint32_t box[2] = {32, 32};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, C, dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 
+// Operand planes per term: 1 term (plain) or the 6 leading products of a
+// three-way split, smallest first: (2,0) (1,1) (0,2) (1,0) (0,1) (0,0).
+int split_terms(int split) { return split == 3 ? 6 : 1; }
+uint32_t code_of(const int *planes, int terms) {
+  uint32_t c = 0;
+  for (int t = 0; t < terms; ++t) c |= (uint32_t)planes[t] << (2 * t);
+  return c;
+}
+constexpr int X3_PLANES[6] = {2, 1, 0, 1, 0, 0};
+constexpr int Y3_PLANES[6] = {0, 1, 2, 0, 1, 0};
+
 template <typename T16>
-cudaError_t pack_operands(const TcUpdateArgs &a, int64_t Kp, T16 *xp, T16 *yp, bool same,
+cudaError_t pack_operands(const TcUpdateArgs &a, int64_t Kp, int terms, T16 *xp, T16 *yp, bool same,
                           cudaStream_t st) {
+  const int one[1] = {0};
+  const uint32_t cx = terms == 1 ? code_of(one, 1) : code_of(X3_PLANES, 6);
+  const uint32_t cy = terms == 1 ? code_of(one, 1) : code_of(Y3_PLANES, 6);
   const int threads = 256;
   {
     const int64_t total = a.M * Kp;
     const unsigned grid = (unsigned)std::min<int64_t>((total + threads - 1) / threads, 65535 * 4);
-    pack_rows_kernel<T16><<<grid, threads, 0, st>>>(a.X, a.ldx, a.M, a.K, Kp, xp);
+    pack_rows_kernel<T16><<<grid, threads, 0, st>>>(a.X, a.ldx, a.M, a.K, Kp, terms, cx, xp);
     count_launch();
   }
   if (!same) {
     if (a.nn) {
       dim3 grid((unsigned)((a.N + 31) / 32), (unsigned)((Kp + 31) / 32));
-      pack_transpose_kernel<T16><<<grid, dim3(32, 8), 0, st>>>(a.Y, a.ldy, a.K, a.N, Kp, yp);
+      pack_transpose_kernel<T16><<<grid, dim3(32, 8), 0, st>>>(a.Y, a.ldy, a.K, a.N, Kp, terms,
+                                                                cy, yp);
     } else {
       const int64_t total = a.N * Kp;
       const unsigned grid = (unsigned)std::min<int64_t>((total + threads - 1) / threads, 65535 * 4);
-      pack_rows_kernel<T16><<<grid, threads, 0, st>>>(a.Y, a.ldy, a.N, a.K, Kp, yp);
+      pack_rows_kernel<T16><<<grid, threads, 0, st>>>(a.Y, a.ldy, a.N, a.K, Kp, terms, cy, yp);
     }
     count_launch();
   }
@@ -383,10 +573,10 @@ bool tc_supported(int device) {
   return major == 10 && minor == 3 && encode_fn() != nullptr;
 }
 
-size_t tc_pack_bytes(int64_t M, int64_t N, int64_t K, bool nn) {
+size_t tc_pack_bytes(int64_t M, int64_t N, int64_t K, bool nn, int split) {
   const int64_t Kp = round_up(std::max<int64_t>(K, 1), BK);
   (void)nn;
-  return (size_t)(round_up(M, 8) + round_up(N, 8)) * (size_t)Kp * 2 + 256;
+  return (size_t)(round_up(M, 8) + round_up(N, 8)) * (size_t)(Kp * split_terms(split)) * 2 + 256;
 }
 
 cudaError_t launch_update_tc(const TcUpdateArgs &a, cudaStream_t st) {
@@ -395,43 +585,62 @@ cudaError_t launch_update_tc(const TcUpdateArgs &a, cudaStream_t st) {
   cudaGetDevice(&dev);
   if (!tc_supported(dev)) return cudaErrorNotSupported;
   if (a.M > INT32_MAX - BM || a.N > INT32_MAX - BN) return cudaErrorInvalidValue;
-  const int64_t Kp = round_up(a.K, BK);
-  if (tc_pack_bytes(a.M, a.N, a.K, a.nn) > a.pack_bytes) return cudaErrorInvalidValue;
-  const bool same = !a.nn && a.X == a.Y && a.ldx == a.ldy && a.M == a.N;
+  if (a.split == 3 && a.f16) return cudaErrorNotSupported;
+  const int terms = split_terms(a.split);
+  const int64_t Kp = round_up(a.K, BK), Ke = Kp * terms;
+  if (Ke / BK > INT32_MAX) return cudaErrorInvalidValue;
+  if (tc_pack_bytes(a.M, a.N, a.K, a.nn, a.split) > a.pack_bytes) return cudaErrorInvalidValue;
+  const bool same = !a.nn && terms == 1 && a.X == a.Y && a.ldx == a.ldy && a.M == a.N;
   uint8_t *base = reinterpret_cast<uint8_t *>(a.pack);
   void *xp = base;
-  void *yp = same ? base : base + (size_t)round_up(a.M, 8) * Kp * 2;
-  cudaError_t e = a.f16 ? pack_operands<__half>(a, Kp, (__half *)xp, (__half *)yp, same, st)
-                        : pack_operands<__nv_bfloat16>(a, Kp, (__nv_bfloat16 *)xp,
+  void *yp = same ? base : base + (size_t)round_up(a.M, 8) * Ke * 2;
+  cudaError_t e = a.f16 ? pack_operands<__half>(a, Kp, terms, (__half *)xp, (__half *)yp, same, st)
+                        : pack_operands<__nv_bfloat16>(a, Kp, terms, (__nv_bfloat16 *)xp,
                                                        (__nv_bfloat16 *)yp, same, st);
   if (e != cudaSuccess) return e;
-  CUtensorMap map_a, map_b;
-  if (!make_map(&map_a, xp, a.M, Kp, BM, a.f16) || !make_map(&map_b, yp, a.N, Kp, BN, a.f16))
+  CUtensorMap map_a, map_b, map_c;
+  memset(&map_c, 0, sizeof map_c);
+  if (!make_operand_map(&map_a, xp, a.M, Ke, BM, a.f16) ||
+      !make_operand_map(&map_b, yp, a.N, Ke, BN, a.f16))
     return cudaErrorInvalidValue;
+  const int use_tma_store = make_c_map(&map_c, a.C, a.ldc, a.M, a.N) ? 1 : 0;
   // instruction descriptor: FP32 accumulator, A/B = BF16 (1) or FP16 (0),
   // both K-major, N >> 3 at bit 17, M >> 4 at bit 24
   const uint32_t ab = a.f16 ? 0u : 1u;
   const uint32_t idesc = (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(BN >> 3) << 17) |
                          ((uint32_t)(BM >> 4) << 24);
   const int vec_ok = ((reinterpret_cast<uintptr_t>(a.C) & 15) == 0 && (a.ldc & 3) == 0) ? 1 : 0;
-  // a tile takes microseconds; one second bounds every wait of the kernel
+  // a tile takes microseconds; one second bounds every single wait
   const long long wait_ns = std::min<long long>((long long)a.spin_limit * 100LL, 1000000000LL);
-  dim3 grid((unsigned)((a.N + BN - 1) / BN), (unsigned)((a.M + BM - 1) / BM));
-  if (grid.y > 65535) return cudaErrorInvalidConfiguration;
+  // persistent grid: one CTA per SM, at most one per valid tile
+  const int64_t nbi = (a.M + BM - 1) / BM, nbj = (a.N + BN - 1) / BN;
+  int64_t valid = 0;
+  for (int64_t bi = 0; bi < nbi; ++bi) {
+    if (!a.lower) {
+      valid += nbj;
+      continue;
+    }
+    const int64_t last = bi * BM + BM - 1 + a.diag;  // largest column index on/below diagonal
+    if (last >= 0) valid += std::min<int64_t>(nbj, last / BN + 1);
+  }
+  if (valid == 0) return cudaSuccess;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(sms, valid));
   if (a.lower) {
     static cudaError_t attr = cudaFuncSetAttribute(
         tc_update_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
     if (attr != cudaSuccess) return attr;
     tc_update_kernel<true><<<grid, THREADS, SMEM_BYTES, st>>>(
-        map_a, map_b, a.C, a.ldc, a.M, a.N, (int)(Kp / BK), a.diag, idesc, a.status, a.err,
-        wait_ns, vec_ok);
+        map_a, map_b, map_c, a.C, a.ldc, a.M, a.N, (int)(Ke / BK), a.diag, idesc, a.status, a.err,
+        wait_ns, use_tma_store, vec_ok);
   } else {
     static cudaError_t attr = cudaFuncSetAttribute(
         tc_update_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
     if (attr != cudaSuccess) return attr;
     tc_update_kernel<false><<<grid, THREADS, SMEM_BYTES, st>>>(
-        map_a, map_b, a.C, a.ldc, a.M, a.N, (int)(Kp / BK), a.diag, idesc, a.status, a.err,
-        wait_ns, vec_ok);
+        map_a, map_b, map_c, a.C, a.ldc, a.M, a.N, (int)(Ke / BK), a.diag, idesc, a.status, a.err,
+        wait_ns, use_tma_store, vec_ok);
   }
   count_launch();
   return cudaGetLastError();

@@ -20,7 +20,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 DEV = "cuda:0"
 
-BOUNDS = {"mix_bf16": 2.0 ** -8 * 2, "mix_f16": 2.0 ** -11 * 2}
+BOUNDS = {"mix_bf16": 2.0 ** -8 * 2, "mix_f16": 2.0 ** -11 * 2, "mix_bf16x3": 2.0 ** -22}
 
 
 @pytest.fixture(scope="module")
@@ -32,7 +32,7 @@ def h():
     hd.close()
 
 
-@pytest.mark.parametrize("dt", ["mix_bf16", "mix_f16"])
+@pytest.mark.parametrize("dt", ["mix_bf16", "mix_f16", "mix_bf16x3"])
 @pytest.mark.parametrize("s", [1, 2, 3])
 def test_mixed_pascal_exact(h, dt, s):
     from paper_1812_02056_gb300 import binding
@@ -45,7 +45,7 @@ def test_mixed_pascal_exact(h, dt, s):
     assert np.array_equal(L.double().cpu().numpy(), I.pascal_lower(6))
 
 
-@pytest.mark.parametrize("dt", ["mix_bf16", "mix_f16"])
+@pytest.mark.parametrize("dt", ["mix_bf16", "mix_f16", "mix_bf16x3"])
 @pytest.mark.parametrize("n,s", [(512, 64), (700, 128), (1024, 256)])
 def test_mixed_chol_vs_oracle(h, dt, n, s):
     A = I.spd_gram(n, 31 + n)
@@ -58,7 +58,7 @@ def test_mixed_chol_vs_oracle(h, dt, n, s):
     assert guarded_rel_err(Lg, Lo, floor=1e-2) <= 8 * BOUNDS[dt]
 
 
-@pytest.mark.parametrize("dt", ["mix_bf16", "mix_f16"])
+@pytest.mark.parametrize("dt", ["mix_bf16", "mix_f16", "mix_bf16x3"])
 def test_mixed_lu_vs_oracle(h, dt):
     n, s = 600, 128
     A = I.lu_diag_dominant(n, 77)

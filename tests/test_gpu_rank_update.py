@@ -38,6 +38,8 @@ def _run(h, dt, lower, kxn, C, X, Y):
 
 
 def _round16(x, dt):
+    if dt == "mix_bf16x3":
+        return x.double()  # the split keeps about FP32 accuracy
     if dt == "mix_bf16":
         return x.to(torch.bfloat16).double()
     if dt == "mix_f16":
@@ -52,7 +54,7 @@ def _expected(C, X, Y, kxn, dt):
     return C.cpu().double() - P, Pa
 
 
-@pytest.mark.parametrize("dt", ["mix_bf16", "mix_f16", "f32", "f64"])
+@pytest.mark.parametrize("dt", ["mix_bf16", "mix_f16", "mix_bf16x3", "f32", "f64"])
 @pytest.mark.parametrize("M,N,K,lower,kxn", [
     (300, 300, 117, 1, 0), (129, 129, 16, 1, 0), (520, 520, 1024, 1, 0), (1, 1, 1, 1, 0),
     (200, 520, 64, 0, 1), (384, 256, 200, 0, 1), (77, 333, 1000, 0, 0)])
@@ -74,7 +76,7 @@ def test_rank_update_exact_integers(h, dt, M, N, K, lower, kxn):
         assert torch.equal(C, exp)
 
 
-@pytest.mark.parametrize("dt", ["mix_bf16", "mix_f16"])
+@pytest.mark.parametrize("dt", ["mix_bf16", "mix_f16", "mix_bf16x3"])
 @pytest.mark.parametrize("M,N,K,lower,kxn", [(1000, 1000, 256, 1, 0), (515, 515, 117, 1, 0),
                                              (640, 384, 320, 0, 1)])
 def test_rank_update_rounded(h, dt, M, N, K, lower, kxn):
@@ -112,3 +114,30 @@ def test_rank_update_strided_views(h):
     rest = Wd.cpu()
     rest[c:, c:n] = C0[c:, c:n]
     assert torch.equal(rest, C0)  # nothing outside the trailing block changed
+
+
+def test_rank_update_preserves_negative_zero_above_diagonal(h):
+    """Masked entries of diagonal tiles receive -0.0 (x + -0 == x for every x)."""
+    M = 300
+    C0 = torch.full((M, M), -0.0)
+    X = torch.ones((M, 64))
+    C = _run(h, "mix_bf16", 1, 0, C0.to(DEV), X.to(DEV), X.to(DEV)).cpu()
+    up = torch.triu(torch.ones(M, M, dtype=torch.bool), 1)
+    assert bool(torch.signbit(C[up]).all())
+    assert bool((C[~up] == -64.0).all())
+
+
+def test_bf16x3_is_fp32_accurate_where_bf16_is_not(h):
+    """Non-representable operands: plain BF16 errs at ~2^-9 per product, the split
+    only by FP32 accumulation."""
+    g = torch.Generator().manual_seed(3)
+    M, K = 256, 512
+    X = torch.rand((M, K), generator=g) + 0.5
+    C0 = torch.zeros((M, M))
+    ref = -(X.double() @ X.double().T)
+    errs = {}
+    for dt in ("mix_bf16", "mix_bf16x3"):
+        C = _run(h, dt, 0, 0, C0.clone().to(DEV), X.to(DEV), X.to(DEV)).cpu().double()
+        errs[dt] = ((C - ref).abs() / ref.abs()).max().item()
+    assert errs["mix_bf16"] > 1e-4
+    assert errs["mix_bf16x3"] < 2e-5

@@ -57,10 +57,14 @@ def test_lu_solve_f64(h, n, nrhs):
     assert np.abs(X.cpu().numpy() - Xo).max() <= 1e-10 * np.abs(Xo).max()
 
 
-@pytest.mark.parametrize("dtype", ["f32", "mix_bf16", "mix_f16"])
-def test_chol_refinement_reaches_fp64(h, dtype):
+# classic refinement contracts when cond(A) * (error of the factor) < 1: the
+# FP32 and FP16-operand factors reach that at cond 1e4; plain BF16 operands
+# (unit roundoff 2^-8) do not, and are tested at cond 1e2
+@pytest.mark.parametrize("dtype,cond", [("f32", 1e4), ("mix_f16", 1e4), ("mix_bf16", 1e2),
+                                        ("mix_bf16x3", 1e4)])
+def test_chol_refinement_reaches_fp64(h, dtype, cond):
     n, nrhs = 512, 16
-    A = I.spd_logspaced(n, 7, cond=1e4)
+    A = I.spd_logspaced(n, 7, cond=cond)
     B = I.rhs(n, nrhs, 8)
     Ad = _t(A)
     Ain = _t(A, torch.float32) if dtype == "f32" else Ad
@@ -70,7 +74,7 @@ def test_chol_refinement_reaches_fp64(h, dtype):
     assert stats.converged == 1 and stats.eta <= 1e-14
     Lo, _ = oracle.chol(A, 64)
     Xo = oracle.chol_solve(Lo, B)
-    assert np.abs(X.cpu().numpy() - Xo).max() <= 1e4 * 1e-13 * np.abs(Xo).max()
+    assert np.abs(X.cpu().numpy() - Xo).max() <= cond * 1e-13 * np.abs(Xo).max()
     # the host-side definition of eta agrees with the reported one
     Xg = X.cpu().numpy()
     R = B - A @ Xg
@@ -124,3 +128,23 @@ def test_refinement_reports_non_convergence(h):
     st, stats = h.gb_chol_solve(n, nrhs, binding.GB_F64, _t(Lbad), n, _t(A), n, _t(B), nrhs, X,
                                 nrhs, 1e-30, 1)
     assert st == binding.GB_ERR_NOT_CONVERGED and stats.converged == 0 and stats.iterations == 1
+
+
+def test_refinement_from_a_diverging_factor_reports_failure(h):
+    """Plain BF16 operands at cond 1e4: refinement must not report success."""
+    from paper_1812_02056_gb300 import binding
+    n, nrhs = 512, 4
+    A = I.spd_logspaced(n, 7, cond=1e4)
+    B = I.rhs(n, nrhs, 8)
+    L, info = h.chol_factor(_t(A), 64, "mix_bf16")
+    if int(info.item()) != 0:
+        return  # breakdown is reported through info: also a failure, correctly flagged
+    X = torch.empty((n, nrhs), dtype=torch.float64, device=DEV)
+    st, stats = h.gb_chol_solve(n, nrhs, binding.GB_MIX_BF16, L, n, _t(A), n, _t(B), nrhs, X, nrhs,
+                                1e-14, 40)
+    if st == binding.GB_OK:  # it may genuinely converge; then the answer must be right
+        Xg = X.cpu().numpy()
+        R = B - A @ Xg
+        assert np.abs(R).max() <= 1e-10 * np.abs(A).sum(1).max() * np.abs(Xg).max()
+    else:
+        assert st == binding.GB_ERR_NOT_CONVERGED and stats.converged == 0
