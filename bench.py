@@ -428,14 +428,16 @@ def run_mixed(args):
     stream = torch.cuda.current_stream()
     xref = None
     for name, s in [("f64", args.s_f64), ("f32", args.s_mixed), ("mix_f16", args.s_mixed),
-                    ("mix_bf16", args.s_mixed)]:
+                    ("mix_bf16", args.s_mixed), ("mix_bf16x3", args.s_mixed)]:
         dt = binding.DTYPES[name]
         Ain = A.float() if name == "f32" else A
         L = torch.empty((n, n), dtype=torch.float64 if name == "f64" else torch.float32, device=dev)
         info = torch.zeros(1, dtype=torch.int32, device=dev)
         X = torch.empty_like(B)
         runs = []
+        h.set_option(binding.GB_OPT_PROFILE, 1)
         for rep in range(1 + args.reps):
+            h.profile_read()  # keep only the last repetition's phases
             torch.cuda.synchronize()
             e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
             e0.record(stream)
@@ -447,12 +449,16 @@ def run_mixed(args):
             torch.cuda.synchronize()
             runs.append((e0.elapsed_time(e1), e1.elapsed_time(e2), st, stats.iterations,
                          stats.eta, int(info.item())))
+        prof = h.profile_read().as_dict()
+        h.set_option(binding.GB_OPT_PROFILE, 0)
         fm, sm, st, it, eta, inf = runs[-1]
         if name == "f64":
             xref = X.clone()
         res = {"s": s, "factor_ms": fm, "solve_ms": sm, "time_to_solution_ms": fm + sm,
                "status": st, "info": inf, "ir_iterations": it, "eta": eta,
-               "factor_gflops": n ** 3 / 3 / (fm * 1e-3) / 1e9}
+               "factor_gflops": n ** 3 / 3 / (fm * 1e-3) / 1e9,
+               "factor_phase_ms": {k: round(v["ms"], 3) for k, v in prof.items()},
+               "factor_phase_launches": {k: v["launches"] for k, v in prof.items()}}
         Xh = X.double()
         R = B - A @ Xh
         den = A.abs().sum(1).max() * Xh.abs().max(0).values + B.abs().max(0).values
