@@ -246,6 +246,37 @@ gb_status gb_rank_update(gb_handle *h, gb_dtype dt, int lower, int y_is_kxn, int
                          int64_t N, int64_t K, void *C, int64_t ldc, const void *X, int64_t ldx,
                          const void *Y, int64_t ldy, void *stream);
 
+/*
+ * gb_chol_solve_noalloc -- X = (L L^T)^{-1} B by forward and back
+ * substitution with a factor from gb_chol_factor, for callers that cannot
+ * allocate device memory.  The paper has no counterpart: it is a plain
+ * solve (no refinement) that needs no handle.
+ *
+ * Who needs it: code that runs while a stream is being captured into a CUDA
+ * graph, inside a budgeted memory pool or a real-time section, or in a
+ * plugin that must not call cudaMalloc -- gb_create allocates a handle's
+ * scratch, this call does not.  Its scratch (the ticket and per-block flags
+ * that order the single-launch solve, an error word and a breakdown word)
+ * is a file-scope __device__ array that every GPU loading the library holds
+ * until exit.
+ *
+ *  n <= 131072 (larger n returns GB_ERR_UNSUPPORTED); nrhs >= 0.
+ *  L, B, X     device pointers (host pointers are rejected: staging them
+ *              would allocate); layouts as gb_chol_solve; X may alias B.
+ *  factor_dt   as gb_chol_solve (L double for GB_F64, float otherwise).
+ * Runs on the current device and waits for `stream` (to read the breakdown
+ * and error words).  Every call shares the one array and leaves its
+ * contents behind; each call clears what must start at zero.  Calls that
+ * overlap on the GPU race on the array: do not issue them concurrently.  The
+ * first call on a device looks up the array's address with that device
+ * current; make that first call before any stream capture.
+ * Returns GB_ERR_BREAKDOWN for a zero or non-finite diagonal entry of L and
+ * GB_ERR_TIMEOUT if a bounded device wait expired.
+ */
+gb_status gb_chol_solve_noalloc(int64_t n, int64_t nrhs, gb_dtype factor_dt, const void *L,
+                                int64_t ldl, const double *B, int64_t ldb, double *X,
+                                int64_t ldx, void *stream);
+
 /* ---------------------------------------------------------- diagnostics */
 /* Phases of a factorization, as timed under GB_OPT_PROFILE. */
 typedef enum gb_phase {

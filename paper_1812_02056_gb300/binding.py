@@ -69,6 +69,7 @@ SIGNATURES = {
     "gb_backward_error": (_I32, [_P, _I32, _I64, _I32, _P, _I64, _P, _I64,
                                  ctypes.POINTER(_D), _P]),
     "gb_chol_factor_batched": (_I32, [_P, _I64, _P, _P, _P, _I32, _I64, _P, _P]),
+    "gb_chol_solve_noalloc": (_I32, [_I64, _I64, _I32, _P, _I64, _P, _I64, _P, _I64, _P]),
     "gb_rank_update": (_I32, [_P, _I32, _I32, _I32, _I64, _I64, _I64, _P, _I64, _P, _I64, _P,
                               _I64, _P]),
     "gb_profile_read": (_I32, [_P, _P]),
@@ -109,6 +110,12 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             fn.argtypes = args
         _lib = lib
         return lib
+
+
+def gb_chol_solve_noalloc(n, nrhs, dt, L, ldl, B, ldb, X, ldx, stream=None) -> int:
+    """Solve without a handle or any allocation (include/gbchol.h)."""
+    return load().gb_chol_solve_noalloc(n, nrhs, dt, _ptr(L), ldl, _ptr(B), ldb, _ptr(X), ldx,
+                                        _stream_ptr(stream))
 
 
 def kernel_launches() -> int:
