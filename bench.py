@@ -473,6 +473,94 @@ def run_mixed(args):
     return 0
 
 
+# ------------------------------------------------------------ batched
+def run_batched(args):
+    """10,000 SPD matrices, n uniform on [16, 512], FP32 and FP64, factored by
+    one persistent launch (steps from the autotuner), captured in a CUDA graph
+    and replayed; GFLOP/s = sum n^3/3 / time."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_1812_02056_gb300 import _build, binding, inputs
+    _build.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    h = binding.Handle(0)
+    sizes = inputs.batch_sizes(args.batch_count, 16, 512, inputs.seed_for(inputs.W_BATCHED))
+    flops = float((sizes.astype(np.float64) ** 3).sum() / 3.0)
+    out = {"mode": "batched", "count": int(len(sizes)), "n_range": [16, 512],
+           "sum_n3_over_3": flops, "results": {}}
+    peaks, _ = load_peaks()
+    for dtype in ("f32", "f64"):
+        tt = torch.float32 if dtype == "f32" else torch.float64
+        buf, offs = inputs.batch_spd_device(sizes, inputs.seed_for(inputs.W_BATCHED, 1), dev, tt)
+        outb = torch.empty_like(buf)
+        esz = buf.element_size()
+        dt = binding.DTYPES[dtype]
+        steps = np.zeros(16, dtype=np.int32)
+        t0 = time.perf_counter()
+        binding.check(h.gb_batched_tune(dt, 512, steps), "tune")
+        tune_s = time.perf_counter() - t0
+        a_arr = (buf.data_ptr() + offs * esz).astype(np.uint64)
+        l_arr = (outb.data_ptr() + offs * esz).astype(np.uint64)
+        n_arr = sizes.astype(np.int64)
+        binding.check(h.gb_batched_plan(len(sizes), n_arr, a_arr, n_arr, l_arr, n_arr, dt, 0),
+                      "plan")
+        info = torch.zeros(len(sizes), dtype=torch.int32, device=dev)
+        st = torch.cuda.Stream()
+        with torch.cuda.stream(st):
+            binding.check(h.gb_batched_run(info, st), "warm")
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=st):
+            binding.check(h.gb_batched_run(info, st), "capture")
+        for _ in range(args.warmup):
+            g.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        bad = int((info != 0).sum().item())
+        rng = np.random.default_rng(1)
+        errs = []
+        for i in rng.choice(len(sizes), 4, replace=False):
+            n = int(sizes[i])
+            A = buf[offs[i]:offs[i] + n * n].view(n, n).double().cpu().numpy()
+            L = outb[offs[i]:offs[i] + n * n].view(n, n).double().cpu().numpy()
+            errs.append(oracle.chol_backward_error(A, L))
+        gf = flops / (ms * 1e-3) / 1e9
+        sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        alu = sms * (4 if dtype == "f64" else 256) * sm_mhz * 1e6 / 1e9
+        out["results"][dtype] = {
+            "ms_per_batch": ms, "gflops": gf, "alu_peak_gflops": alu, "frac_of_alu_peak": gf / alu,
+            "breakdowns": bad, "tuned_steps_by_32": steps[:16].tolist(), "tune_s": tune_s,
+            "sample_backward_error_max": max(errs), "graph_replays": args.steps,
+            "bytes_in_out": 2 * int((sizes ** 2).sum()) * esz}
+        del buf, outb, g
+        torch.cuda.empty_cache()
+    # CPU oracle on a bounded sample of the same workload
+    idx = np.random.default_rng(2).choice(len(sizes), args.batch_cpu_sample, replace=False)
+    mats = [inputs.spd_gram(int(sizes[i]), inputs.seed_for(inputs.W_BATCHED, 2) + int(i))
+            for i in idx]
+    t0 = time.perf_counter()
+    for A in mats:
+        oracle.chol(A, 32)
+    el = time.perf_counter() - t0
+    fs = float(sum(int(sizes[i]) ** 3 for i in idx) / 3.0)
+    out["cpu_baseline"] = {"value": fs / el / 1e9, "unit": "GFLOP/s", "kind": "oracle",
+                           "cores": oracle.num_threads(),
+                           "sample": f"{len(idx)} matrices of the workload, FP64, s=32"}
+    print(json.dumps(out))
+    h.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -488,7 +576,7 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip sweeps and accuracy figures")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--mode", choices=["chol", "update", "mixed"], default="chol",
+    ap.add_argument("--mode", choices=["chol", "update", "mixed", "batched"], default="chol",
                     help="chol: the benchmark line; update: the tensor-core rank-s update "
                          "alone; mixed: FP64 vs mixed-precision time to solution")
     ap.add_argument("--ks", default="256,512,1024,2048")
@@ -496,6 +584,8 @@ def main():
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--s-f64", type=int, default=256)
     ap.add_argument("--s-mixed", type=int, default=1024)
+    ap.add_argument("--batch-count", type=int, default=10000)
+    ap.add_argument("--batch-cpu-sample", type=int, default=200)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -503,6 +593,8 @@ def main():
         return run_update(args)
     if args.mode == "mixed":
         return run_mixed(args)
+    if args.mode == "batched":
+        return run_batched(args)
     return run_ours(args)
 
 

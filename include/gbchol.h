@@ -124,9 +124,12 @@ typedef enum gb_option {
                                update (default); 0: the SIMT FP32 update.   */
   GB_OPT_SPIN_LIMIT = 4,    /* limit of bounded device waits, in units of
                                100 ns of %globaltimer (default 2^26, ~6.7 s). */
-  GB_OPT_PROFILE = 5        /* 1: record CUDA events around every launch of
+  GB_OPT_PROFILE = 5,       /* 1: record CUDA events around every launch of
                                the factorizations (read with
                                gb_profile_read); default 0.                 */
+  GB_OPT_BATCHED_EXACT = 6  /* 1: the batched kernel rounds every product and
+                               every subtraction separately (no FMA), as the
+                               FP64 oracle does; default 0.                  */
 } gb_option;
 
 gb_status gb_set_option(gb_handle *h, gb_option opt, int64_t value);
@@ -326,20 +329,55 @@ gb_status gb_backward_error(gb_handle *h, int is_lu, int64_t n, gb_dtype factor_
 /* ---------------------------------------------------------------- batched */
 /*
  * gb_chol_factor_batched -- Algorithm 1 applied independently to `count`
- * matrices of possibly different orders, in one persistent launch.
+ * matrices of possibly different orders, in ONE persistent launch: CTAs
+ * take matrices longest first (LPT on n^3) from a device ticket.  A matrix
+ * whose packed lower triangle fits in shared memory (FP64 n <= 225, FP32
+ * n <= 319) runs all of Algorithm 1 in shared memory; a larger one is first
+ * copied to L, keeps its s-wide panel in shared memory and receives the
+ * delayed update in place in L.
  *
  *  n[count]    orders (host array), 0 <= n[i] <= 1024.
- *  A[count]    device pointers (host array of pointers) to the matrices,
- *              factored in place: on return the lower triangle holds L and
- *              the strict upper triangle is zero.
+ *  A[count]    device pointers (host array of pointers) to the inputs; only
+ *              the lower triangles are read.
  *  lda[count]  leading dimensions (host array), lda[i] >= n[i].
+ *  L[count]    device pointers to the outputs (L[i] may equal A[i]): the
+ *              lower triangle receives the factor, the strict upper
+ *              triangle is zeroed.
+ *  ldl[count]  leading dimensions of the outputs.
  *  dt          GB_F64 (double matrices) or GB_F32 (float matrices).
- *  s           step (s >= 1), or 0 for the tuned step per order.
+ *  s           step for every matrix (s >= 1), or 0 for the tuned step of
+ *              each matrix's order (gb_batched_tune; a default rule before).
  *  info        count ints (device or host), per-matrix status as above.
+ * Uploads the plan (waits for `stream` once), then launches; with a device
+ * `info` the launch itself is asynchronous.
  */
 gb_status gb_chol_factor_batched(gb_handle *h, int64_t count, const int64_t *n, void *const *A,
-                                 const int64_t *lda, gb_dtype dt, int64_t s, int *info,
-                                 void *stream);
+                                 const int64_t *lda, void *const *L, const int64_t *ldl,
+                                 gb_dtype dt, int64_t s, int *info, void *stream);
+
+/*
+ * gb_batched_plan / gb_batched_run -- the two halves of
+ * gb_chol_factor_batched.  gb_batched_plan validates the arrays, orders the
+ * matrices and uploads the plan into the handle (synchronous; arguments as
+ * above).  gb_batched_run(h, info, stream) launches the persistent kernel
+ * over the last plan: a ticket reset and one kernel, nothing else, so a
+ * caller can capture it into a CUDA graph and replay it (out of place, the
+ * inputs stay intact).  info: device array of the plan's count ints.
+ */
+gb_status gb_batched_plan(gb_handle *h, int64_t count, const int64_t *n, void *const *A,
+                          const int64_t *lda, void *const *L, const int64_t *ldl, gb_dtype dt,
+                          int64_t s, void *stream);
+gb_status gb_batched_run(gb_handle *h, int *info, void *stream);
+
+/*
+ * gb_batched_tune -- the autotuner of the batched call: for every bucket of
+ * 32 orders up to n_max it times the persistent kernel on two waves of
+ * synthetic SPD matrices (n I + ones) for steps s in {8, 16, 32, 48, 64, 96,
+ * 128} and keeps the fastest in the handle (used when s = 0).  steps_out
+ * (optional) receives ceil(n_max / 32) steps.  Allocates and frees its own
+ * test matrices; synchronous.
+ */
+gb_status gb_batched_tune(gb_handle *h, gb_dtype dt, int64_t n_max, int *steps_out, void *stream);
 
 #ifdef __cplusplus
 } /* extern "C" */

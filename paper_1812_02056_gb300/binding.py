@@ -34,6 +34,7 @@ DTYPES = {"f64": GB_F64, "f32": GB_F32, "mix_bf16": GB_MIX_BF16, "mix_f16": GB_M
 
 GB_OPT_INNER_STEP, GB_OPT_USE_GRAPHS, GB_OPT_TC_UPDATE, GB_OPT_SPIN_LIMIT = 1, 2, 3, 4
 GB_OPT_PROFILE = 5
+GB_OPT_BATCHED_EXACT = 6
 
 
 class GbError(RuntimeError):
@@ -68,10 +69,13 @@ SIGNATURES = {
                            ctypes.POINTER(RefineOpts), ctypes.POINTER(SolveStats), _P]),
     "gb_backward_error": (_I32, [_P, _I32, _I64, _I32, _P, _I64, _P, _I64,
                                  ctypes.POINTER(_D), _P]),
-    "gb_chol_factor_batched": (_I32, [_P, _I64, _P, _P, _P, _I32, _I64, _P, _P]),
+    "gb_chol_factor_batched": (_I32, [_P, _I64, _P, _P, _P, _P, _P, _I32, _I64, _P, _P]),
+    "gb_batched_plan": (_I32, [_P, _I64, _P, _P, _P, _P, _P, _I32, _I64, _P]),
+    "gb_batched_run": (_I32, [_P, _P, _P]),
     "gb_chol_solve_noalloc": (_I32, [_I64, _I64, _I32, _P, _I64, _P, _I64, _P, _I64, _P]),
     "gb_rank_update": (_I32, [_P, _I32, _I32, _I32, _I64, _I64, _I64, _P, _I64, _P, _I64, _P,
                               _I64, _P]),
+    "gb_batched_tune": (_I32, [_P, _I32, _I64, _P, _P]),
     "gb_profile_read": (_I32, [_P, _P]),
     "gb_kernel_launches": (ctypes.c_uint64, []),
     "gb_measure_fma_peak": (_I32, [_P, _I32, ctypes.POINTER(_D)]),
@@ -242,10 +246,39 @@ class Handle:
               "gb_backward_error")
         return out.value
 
-    def gb_chol_factor_batched(self, count, n_arr, ptr_arr, lda_arr, dt, s, info, stream=None):
-        return self.lib.gb_chol_factor_batched(self.h, count, _ptr(n_arr), _ptr(ptr_arr),
-                                               _ptr(lda_arr), dt, s, _ptr(info),
-                                               _stream_ptr(stream))
+    def gb_chol_factor_batched(self, count, n_arr, a_arr, lda_arr, l_arr, ldl_arr, dt, s, info,
+                               stream=None):
+        return self.lib.gb_chol_factor_batched(self.h, count, _ptr(n_arr), _ptr(a_arr),
+                                               _ptr(lda_arr), _ptr(l_arr), _ptr(ldl_arr), dt, s,
+                                               _ptr(info), _stream_ptr(stream))
+
+    def gb_batched_plan(self, count, n_arr, a_arr, lda_arr, l_arr, ldl_arr, dt, s, stream=None):
+        return self.lib.gb_batched_plan(self.h, count, _ptr(n_arr), _ptr(a_arr), _ptr(lda_arr),
+                                        _ptr(l_arr), _ptr(ldl_arr), dt, s, _stream_ptr(stream))
+
+    def gb_batched_run(self, info, stream=None):
+        return self.lib.gb_batched_run(self.h, _ptr(info), _stream_ptr(stream))
+
+    def gb_batched_tune(self, dt, n_max, steps_out=None, stream=None):
+        return self.lib.gb_batched_tune(self.h, dt, n_max, _ptr(steps_out), _stream_ptr(stream))
+
+    def chol_factor_batched(self, mats, s: int = 0, dtype: str = "f64", outs=None, stream=None):
+        """Factor a list of square CUDA tensors (in place unless `outs` is
+        given) in one launch; returns the per-matrix info as a numpy array."""
+        import numpy as np
+        import torch
+        cnt = len(mats)
+        outs = mats if outs is None else outs
+        n_arr = np.array([m.shape[0] for m in mats], dtype=np.int64)
+        a_arr = np.array([m.data_ptr() for m in mats], dtype=np.uint64)
+        lda = np.array([max(1, m.stride(0)) for m in mats], dtype=np.int64)
+        l_arr = np.array([m.data_ptr() for m in outs], dtype=np.uint64)
+        ldl = np.array([max(1, m.stride(0)) for m in outs], dtype=np.int64)
+        info = torch.zeros(max(cnt, 1), dtype=torch.int32, device=mats[0].device if mats else "cuda")
+        check(self.gb_chol_factor_batched(cnt, n_arr, a_arr, lda, l_arr, ldl, DTYPES[dtype], s,
+                                          info, stream), "gb_chol_factor_batched")
+        torch.cuda.synchronize()
+        return info[:cnt].cpu().numpy()
 
     def gb_rank_update(self, dt, lower, y_is_kxn, M, N, K, C, ldc, X, ldx, Y, ldy, stream=None):
         return self.lib.gb_rank_update(self.h, dt, int(lower), int(y_is_kxn), M, N, K, _ptr(C), ldc,

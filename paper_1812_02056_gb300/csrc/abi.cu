@@ -706,6 +706,7 @@ gb_status gb_set_option(gb_handle *h, gb_option opt, int64_t v) {
       h->spin_limit = v;
       return GB_OK;
     case GB_OPT_PROFILE: h->profile = v ? 1 : 0; return GB_OK;
+    case GB_OPT_BATCHED_EXACT: h->batched_exact = v ? 1 : 0; return GB_OK;
     default: return -2;
   }
 }
@@ -719,6 +720,7 @@ gb_status gb_get_option(gb_handle *h, gb_option opt, int64_t *v) {
     case GB_OPT_TC_UPDATE: *v = h->tc_update; return GB_OK;
     case GB_OPT_SPIN_LIMIT: *v = h->spin_limit; return GB_OK;
     case GB_OPT_PROFILE: *v = h->profile; return GB_OK;
+    case GB_OPT_BATCHED_EXACT: *v = h->batched_exact; return GB_OK;
     default: return -2;
   }
 }
@@ -781,11 +783,247 @@ gb_status gb_backward_error(gb_handle *h, int is_lu, int64_t n, gb_dtype factor_
 
 }  // extern "C"
 
+namespace gb {
+namespace {
+
+// Step for a matrix of order n when the caller passes s = 0: the tuned
+// bucket entry if gb_batched_tune ran, else a rule measured on GB300
+// (small orders: Crout-like wide steps are latency-bound; 32 balances the
+// column steps against the delayed update).
+int batched_default_step(const gb_handle *h, int dtype_index, int n) {
+  const int b = std::min(BATCH_BUCKETS - 1, std::max(0, (n - 1) / 32));
+  const int t = h->batched_step[dtype_index][b];
+  if (t > 0) return t;
+  return n <= 32 ? n : 32;
+}
+
+// Build the plan (LPT order, steps) on the host and upload it into the
+// handle's batched workspace; remembered in h->plan.
+gb_status batched_upload(gb_handle *h, int64_t count, const int64_t *n, void *const *A,
+                         const int64_t *lda, void *const *L, const int64_t *ldl, gb_dtype dt,
+                         const int *steps, cudaStream_t st) {
+  const int di = dt == GB_F64 ? 0 : 1;
+  std::vector<int> order((size_t)count), nn((size_t)count), ss((size_t)count);
+  for (int64_t i = 0; i < count; ++i) {
+    order[i] = (int)i;
+    nn[i] = (int)n[i];
+    ss[i] = steps ? steps[i] : batched_default_step(h, di, (int)n[i]);
+  }
+  // longest processing time first: orders by n^3, descending
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return nn[a] > nn[b]; });
+  const size_t c = (size_t)count;
+  const size_t off_n = c * 4, off_s = 2 * c * 4, off_a = ((3 * c * 4 + 15) / 16) * 16;
+  const size_t off_la = off_a + c * 8, off_l = off_la + c * 8, off_ll = off_l + c * 8;
+  const size_t off_t = off_ll + c * 8, total = off_t + 16;
+  std::vector<unsigned char> blob(total, 0);
+  memcpy(blob.data(), order.data(), c * 4);
+  memcpy(blob.data() + off_n, nn.data(), c * 4);
+  memcpy(blob.data() + off_s, ss.data(), c * 4);
+  memcpy(blob.data() + off_a, A, c * 8);
+  memcpy(blob.data() + off_la, lda, c * 8);
+  memcpy(blob.data() + off_l, L, c * 8);
+  memcpy(blob.data() + off_ll, ldl, c * 8);
+  gb_status r = ws_reserve(h, WS_MISC, total, st);
+  if (r != GB_OK) return r;
+  unsigned char *d = (unsigned char *)h->ws[WS_MISC].ptr;
+  GB_CUDA_TRY(cudaMemcpyAsync(d, blob.data(), total, cudaMemcpyHostToDevice, st));
+  GB_CUDA_TRY(cudaStreamSynchronize(st));  // the host blob goes out of scope
+  auto &p = h->plan;
+  p.count = (int)count;
+  p.dt = dt;
+  p.order = (const int *)d;
+  p.n = (const int *)(d + off_n);
+  p.step = (const int *)(d + off_s);
+  p.A = (void *const *)(d + off_a);
+  p.lda = (const int64_t *)(d + off_la);
+  p.L = (void *const *)(d + off_l);
+  p.ldl = (const int64_t *)(d + off_ll);
+  p.ticket = (int *)(d + off_t);
+  return GB_OK;
+}
+
+// Launch the persistent kernel over the uploaded plan (capturable).
+gb_status batched_launch(gb_handle *h, int *info_dev, cudaStream_t st) {
+  const auto &p = h->plan;
+  if (p.count <= 0) return GB_OK;
+  if (p.dt == GB_F64)
+    GB_CUDA_TRY(launch_chol_batched_plan<double>(p.count, p.order, p.n, p.step, p.A, p.lda, p.L,
+                                                 p.ldl, info_dev, p.ticket, h->sm_count,
+                                                 h->batched_exact, st));
+  else
+    GB_CUDA_TRY(launch_chol_batched_plan<float>(p.count, p.order, p.n, p.step, p.A, p.lda, p.L,
+                                                p.ldl, info_dev, p.ticket, h->sm_count,
+                                                h->batched_exact, st));
+  return GB_OK;
+}
+
+gb_status batched_check(gb_handle *h, int64_t count, const int64_t *n, void *const *A,
+                        const int64_t *lda, void *const *L, const int64_t *ldl, gb_dtype dt,
+                        int64_t s) {
+  if (!h) return -1;
+  if (count < 0 || count > (1 << 26)) return -2;
+  if (count > 0 && !n) return -3;
+  if (count > 0 && !A) return -4;
+  if (count > 0 && !lda) return -5;
+  if (count > 0 && !L) return -6;
+  if (count > 0 && !ldl) return -7;
+  if (dt != GB_F64 && dt != GB_F32) return -8;
+  if (s < 0) return -9;
+  for (int64_t i = 0; i < count; ++i) {
+    if (n[i] < 0 || n[i] > BATCH_MAX_N) return -3;
+    if (lda[i] < std::max<int64_t>(1, n[i])) return -5;
+    if (ldl[i] < std::max<int64_t>(1, n[i])) return -7;
+    if (n[i] > 0 && (!A[i] || !is_device_ptr(A[i]))) return -4;
+    if (n[i] > 0 && (!L[i] || !is_device_ptr(L[i]))) return -6;
+  }
+  return GB_OK;
+}
+
+}  // namespace
+}  // namespace gb
+
+extern "C" gb_status gb_batched_plan(gb_handle *h, int64_t count, const int64_t *n,
+                                     void *const *A, const int64_t *lda, void *const *L,
+                                     const int64_t *ldl, gb_dtype dt, int64_t s, void *stream) {
+  gb_status r = batched_check(h, count, n, A, lda, L, ldl, dt, s);
+  if (r != GB_OK) return r;
+  DeviceGuard g(h->device);
+  std::lock_guard<std::mutex> lk(h->mu);
+  std::vector<int> steps;
+  if (s > 0) steps.assign((size_t)count, (int)std::min<int64_t>(s, 1 << 20));
+  if (count == 0) {
+    h->plan = gb_handle::BatchPlanDev{};
+    return GB_OK;
+  }
+  return batched_upload(h, count, n, A, lda, L, ldl, dt, s > 0 ? steps.data() : nullptr,
+                        (cudaStream_t)stream);
+}
+
+extern "C" gb_status gb_batched_run(gb_handle *h, int *info, void *stream) {
+  if (!h) return -1;
+  if (h->plan.count > 0 && !info) return -2;
+  if (h->plan.count > 0 && !is_device_ptr(info)) return -2;
+  DeviceGuard g(h->device);
+  std::lock_guard<std::mutex> lk(h->mu);
+  return batched_launch(h, info, (cudaStream_t)stream);
+}
+
 extern "C" gb_status gb_chol_factor_batched(gb_handle *h, int64_t count, const int64_t *n,
-                                            void *const *A, const int64_t *lda, gb_dtype dt,
-                                            int64_t s, int *info, void *stream) {
-  (void)h; (void)count; (void)n; (void)A; (void)lda; (void)dt; (void)s; (void)info; (void)stream;
-  return GB_ERR_UNSUPPORTED;
+                                            void *const *A, const int64_t *lda, void *const *L,
+                                            const int64_t *ldl, gb_dtype dt, int64_t s, int *info,
+                                            void *stream) {
+  gb_status r = batched_check(h, count, n, A, lda, L, ldl, dt, s);
+  if (r != GB_OK) return r;
+  if (count > 0 && !info) return -10;
+  if (count == 0) return GB_OK;
+  DeviceGuard g(h->device);
+  std::lock_guard<std::mutex> lk(h->mu);
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<int> steps;
+  if (s > 0) steps.assign((size_t)count, (int)std::min<int64_t>(s, 1 << 20));
+  if ((r = batched_upload(h, count, n, A, lda, L, ldl, dt, s > 0 ? steps.data() : nullptr, st)) !=
+      GB_OK)
+    return r;
+  int *info_dev = info;
+  int *info_scratch = nullptr;
+  const bool host_info = !is_device_ptr(info);
+  if (host_info) {
+    if (cudaMallocAsync((void **)&info_scratch, sizeof(int) * count, st) != cudaSuccess) {
+      cudaGetLastError();
+      return GB_ERR_NOMEM;
+    }
+    info_dev = info_scratch;
+  }
+  r = batched_launch(h, info_dev, st);
+  if (r == GB_OK && host_info) {
+    if (cudaMemcpyAsync(info, info_scratch, sizeof(int) * count, cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      r = GB_ERR_CUDA;
+  }
+  if (info_scratch) cudaFreeAsync(info_scratch, st);
+  return r;
+}
+
+extern "C" gb_status gb_batched_tune(gb_handle *h, gb_dtype dt, int64_t n_max, int *steps_out,
+                                     void *stream) {
+  if (!h) return -1;
+  if (dt != GB_F64 && dt != GB_F32) return -2;
+  if (n_max < 1 || n_max > BATCH_MAX_N) return -3;
+  DeviceGuard g(h->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  const int di = dt == GB_F64 ? 0 : 1;
+  const size_t esz = dt == GB_F64 ? 8 : 4;
+  const int per = 2 * std::max(1, h->sm_count);  // two waves of matrices per bucket
+  const int nb = (int)((n_max + 31) / 32);
+  const int cand[] = {8, 16, 32, 48, 64, 96, 128};
+  void *buf = nullptr;
+  const int64_t stride = (int64_t)n_max * n_max;
+  if (cudaMalloc(&buf, (size_t)per * stride * esz) != cudaSuccess) {
+    cudaGetLastError();
+    return GB_ERR_NOMEM;
+  }
+  int *info = nullptr;
+  if (cudaMalloc((void **)&info, sizeof(int) * per) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(buf);
+    return GB_ERR_NOMEM;
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  gb_status r = GB_OK;
+  std::vector<int64_t> nv(per), lv(per);
+  std::vector<void *> pv(per);
+  std::vector<int> sv(per);
+  for (int b = 0; b < nb && r == GB_OK; ++b) {
+    const int n = std::min<int>((int)n_max, 32 * b + 24);  // representative order of the bucket
+    float best = 1e30f;
+    int best_s = 32;
+    for (int c : cand) {
+      if (c > n && c != cand[0]) break;
+      for (int i = 0; i < per; ++i) {
+        nv[i] = n;
+        lv[i] = n;
+        pv[i] = (char *)buf + (size_t)i * stride * esz;
+        sv[i] = std::min(c, n);
+      }
+      for (int rep = 0; rep < 2 && r == GB_OK; ++rep) {  // rep 0 warms up
+        cudaError_t e = dt == GB_F64 ? launch_fill_spd<double>((double *)buf, stride, per, n, st)
+                                     : launch_fill_spd<float>((float *)buf, stride, per, n, st);
+        if (e != cudaSuccess) {
+          record_cuda_error(e, "fill_spd", __FILE__, __LINE__);
+          r = GB_ERR_CUDA;
+          break;
+        }
+        {
+          std::lock_guard<std::mutex> lk(h->mu);
+          r = batched_upload(h, per, nv.data(), pv.data(), lv.data(), pv.data(), lv.data(), dt,
+                             sv.data(), st);
+          if (r == GB_OK) {
+            cudaEventRecord(e0, st);
+            r = batched_launch(h, info, st);
+            cudaEventRecord(e1, st);
+          }
+        }
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep == 1 && ms < best) {
+          best = ms;
+          best_s = sv[0];
+        }
+      }
+    }
+    h->batched_step[di][b] = best_s;
+    if (steps_out) steps_out[b] = best_s;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamSynchronize(st);
+  cudaFree(info);
+  cudaFree(buf);
+  return r;
 }
 
 extern "C" uint64_t gb_kernel_launches(void) { return gb::g_launches.load(); }

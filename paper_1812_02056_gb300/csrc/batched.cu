@@ -1,0 +1,288 @@
+// Batched Algorithm 1 (arXiv:1812.02056, Sec. 2): thousands of independent
+// SPD matrices of uneven orders factored in ONE persistent launch.
+//
+// The host sorts the matrices longest first (n^3, LPT order) and uploads a
+// plan; each CTA takes the next matrix from an atomic ticket and factors it
+// in place with step s:
+//   * small matrices (the packed lower triangle fits in shared memory): the
+//     whole of Algorithm 1 in shared memory -- column steps left-looking over
+//     the columns since the checkpoint z, and every s columns the delayed
+//     update A[c.., c..] -= S with S_ij formed first and then subtracted;
+//   * larger matrices: the s-wide panel L[z.., z..z+sb) lives in shared
+//     memory for its column steps, and the delayed update is applied to the
+//     trailing lower triangle in global memory (L2-resident for n <= 1024).
+// Every sum runs in ascending k, one product at a time.  With `exact` set the
+// kernel uses separately rounded multiply and subtract (no FMA), so its FP64
+// result is the same bits as the oracle's literal mode.
+#include <math.h>
+
+#include "gb_internal.cuh"
+
+namespace gb {
+namespace {
+
+constexpr int BT = 256;  // threads per CTA
+
+template <typename T>
+__device__ __forceinline__ T msub(T acc, T a, T b, bool exact);
+template <>
+__device__ __forceinline__ double msub<double>(double acc, double a, double b, bool exact) {
+  return exact ? __dsub_rn(acc, __dmul_rn(a, b)) : fma(-a, b, acc);
+}
+template <>
+__device__ __forceinline__ float msub<float>(float acc, float a, float b, bool exact) {
+  return exact ? __fsub_rn(acc, __fmul_rn(a, b)) : fmaf(-a, b, acc);
+}
+template <typename T>
+__device__ __forceinline__ T madd(T acc, T a, T b, bool exact);
+template <>
+__device__ __forceinline__ double madd<double>(double acc, double a, double b, bool exact) {
+  return exact ? __dadd_rn(acc, __dmul_rn(a, b)) : fma(a, b, acc);
+}
+template <>
+__device__ __forceinline__ float madd<float>(float acc, float a, float b, bool exact) {
+  return exact ? __fadd_rn(acc, __fmul_rn(a, b)) : fmaf(a, b, acc);
+}
+template <typename T>
+__device__ __forceinline__ T dsqrt(T x);
+template <>
+__device__ __forceinline__ double dsqrt<double>(double x) {
+  return __dsqrt_rn(x);
+}
+template <>
+__device__ __forceinline__ float dsqrt<float>(float x) {
+  return __fsqrt_rn(x);
+}
+template <typename T>
+__device__ __forceinline__ T ddiv(T a, T b);
+template <>
+__device__ __forceinline__ double ddiv<double>(double a, double b) {
+  return __ddiv_rn(a, b);
+}
+template <>
+__device__ __forceinline__ float ddiv<float>(float a, float b) {
+  return __fdiv_rn(a, b);
+}
+
+__device__ __forceinline__ int64_t tri(int64_t i) { return i * (i + 1) / 2; }
+
+// (r, q) with e = r (r + 1) / 2 + q, 0 <= q <= r
+__device__ __forceinline__ void tri_decode(int64_t e, int &r, int &q) {
+  int x = (int)((sqrt(8.0 * (double)e + 1.0) - 1.0) * 0.5);
+  while (tri(x) > e) --x;
+  while (tri(x + 1) <= e) ++x;
+  r = x;
+  q = (int)(e - tri(x));
+}
+
+// ------------------------------------------------- whole matrix in shared memory
+// S holds the packed lower triangle: (i, j), j <= i, at i (i + 1) / 2 + j.
+template <typename T>
+__device__ int chol_in_smem(T *S, int n, int s, bool exact, T *red) {
+  const int tid = threadIdx.x;
+  int z = 0;
+  for (int c = 0; c < n; ++c) {
+    if (c == z + s) {
+      // delayed update: A[i][j] -= S_ij, S_ij = sum_{k=z}^{c-1} L_ik L_jk, c <= j <= i
+      const int m = n - c;
+      const int64_t cnt = tri(m);
+      for (int64_t e = tid; e < cnt; e += BT) {
+        int r, q;
+        tri_decode(e, r, q);
+        const int i = c + r, j = c + q;
+        const T *Li = S + tri(i), *Lj = S + tri(j);
+        T sij = T(0);
+        for (int k = z; k < c; ++k) sij = madd(sij, Li[k], Lj[k], exact);
+        S[tri(i) + j] = S[tri(i) + j] - sij;  // a lone subtraction is never contracted
+      }
+      z = c;
+      __syncthreads();
+    }
+    // column step c: v_i = A_ic - sum_{k=z}^{c-1} L_ik L_ck for i >= c
+    const T *Lc = S + tri(c);
+    for (int i = c + tid; i < n; i += BT) {
+      const T *Li = S + tri(i);
+      T v = Li[c];
+      for (int k = z; k < c; ++k) v = msub(v, Li[k], Lc[k], exact);
+      if (i == c) red[0] = v; else S[tri(i) + c] = v;
+    }
+    __syncthreads();
+    const T d = red[0];
+    if (!(d > T(0))) return c + 1;  // uniform: every thread read the same d
+    const T lcc = dsqrt(d);
+    for (int i = c + 1 + tid; i < n; i += BT) S[tri(i) + c] = ddiv(S[tri(i) + c], lcc);
+    if (tid == 0) S[tri(c) + c] = lcc;
+    __syncthreads();
+  }
+  return 0;
+}
+
+// ------------------------------------------------- panel in shared memory
+// P: rows [z, n) x columns [z, z + sb) of the working matrix, row-major with
+// leading dimension s (the panel width bound).
+template <typename T>
+__device__ int chol_panel_path(T *A, int64_t lda, int n, int s, bool exact, T *P, T *red) {
+  const int tid = threadIdx.x;
+  for (int z = 0; z < n; z += s) {
+    const int sb = min(s, n - z);
+    const int rows = n - z;
+    for (int64_t e = tid; e < (int64_t)rows * sb; e += BT) {
+      const int r = (int)(e / sb), q = (int)(e % sb);
+      P[(int64_t)r * s + q] = A[(int64_t)(z + r) * lda + z + q];
+    }
+    __syncthreads();
+    for (int c = 0; c < sb; ++c) {  // column z + c, local index c
+      const T *Pc = P + (int64_t)c * s;
+      for (int r = c + tid; r < rows; r += BT) {
+        T *Pr = P + (int64_t)r * s;
+        T v = Pr[c];
+        for (int k = 0; k < c; ++k) v = msub(v, Pr[k], Pc[k], exact);
+        if (r == c) red[0] = v; else Pr[c] = v;
+      }
+      __syncthreads();
+      const T d = red[0];
+      if (!(d > T(0))) return z + c + 1;
+      const T lcc = dsqrt(d);
+      for (int r = c + 1 + tid; r < rows; r += BT) P[(int64_t)r * s + c] = ddiv(P[(int64_t)r * s + c], lcc);
+      if (tid == 0) P[(int64_t)c * s + c] = lcc;
+      __syncthreads();
+    }
+    for (int64_t e = tid; e < (int64_t)rows * sb; e += BT) {
+      const int r = (int)(e / sb), q = (int)(e % sb);
+      if (q <= r) A[(int64_t)(z + r) * lda + z + q] = P[(int64_t)r * s + q];
+    }
+    // delayed update of the trailing lower triangle: rows/cols [z+sb, n)
+    const int m = n - z - sb;
+    const int64_t cnt = tri(m);
+    for (int64_t e = tid; e < cnt; e += BT) {
+      int r, q;
+      tri_decode(e, r, q);
+      const T *Pi = P + (int64_t)(sb + r) * s, *Pj = P + (int64_t)(sb + q) * s;
+      T sij = T(0);
+      for (int k = 0; k < sb; ++k) sij = madd(sij, Pi[k], Pj[k], exact);
+      T *a = A + (int64_t)(z + sb + r) * lda + z + sb + q;
+      *a = *a - sij;
+    }
+    __syncthreads();  // global writes of this CTA are visible to it after the barrier
+  }
+  return 0;
+}
+
+struct Plan {
+  int count;
+  const int *order;
+  const int *n;
+  const int *step;
+  void *const *A;       // inputs (lower triangle read)
+  const int64_t *lda;
+  void *const *L;       // outputs (may alias the inputs)
+  const int64_t *ldl;
+  int *info;
+  int *ticket;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(BT) batched_chol_kernel(Plan plan, int64_t smem_elems, int exact) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *buf = reinterpret_cast<T *>(smem_raw);
+  __shared__ T red[1];
+  __shared__ int s_idx;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const int t = atomicAdd(plan.ticket, 1);
+      s_idx = t < plan.count ? plan.order[t] : -1;
+    }
+    __syncthreads();
+    const int idx = s_idx;
+    if (idx < 0) break;
+    const int n = plan.n[idx];
+    const int s = max(1, plan.step[idx]);
+    const T *A = reinterpret_cast<const T *>(plan.A[idx]);
+    const int64_t lda = plan.lda[idx];
+    T *L = reinterpret_cast<T *>(plan.L[idx]);
+    const int64_t ldl = plan.ldl[idx];
+    int info = 0;
+    if (n > 0) {
+      if (tri(n) <= smem_elems) {
+        for (int64_t e = threadIdx.x; e < tri(n); e += BT) {
+          int r, q;
+          tri_decode(e, r, q);
+          buf[e] = A[(int64_t)r * lda + q];
+        }
+        __syncthreads();
+        info = chol_in_smem<T>(buf, n, min(s, n), exact != 0, red);
+        __syncthreads();
+        for (int64_t e = threadIdx.x; e < (int64_t)n * n; e += BT) {
+          const int r = (int)(e / n), q = (int)(e % n);
+          L[(int64_t)r * ldl + q] = q <= r ? buf[tri(r) + q] : T(0);
+        }
+      } else {
+        // the panel path works in place in L: copy A's lower triangle first
+        for (int64_t e = threadIdx.x; e < (int64_t)n * n; e += BT) {
+          const int r = (int)(e / n), q = (int)(e % n);
+          L[(int64_t)r * ldl + q] = q <= r ? A[(int64_t)r * lda + q] : T(0);
+        }
+        __syncthreads();
+        const int sp = (int)min64(s, smem_elems / n);  // panel width that fits
+        info = chol_panel_path<T>(L, ldl, n, max(1, sp), exact != 0, buf, red);
+        __syncthreads();
+      }
+    }
+    if (threadIdx.x == 0) plan.info[idx] = info;
+    __syncthreads();  // s_idx is rewritten next iteration
+  }
+}
+
+// A = n I + ones: symmetric positive definite, exact in every precision.
+template <typename T>
+__global__ void fill_spd_kernel(T *base, int64_t stride, int count, int n) {
+  const int64_t total = (int64_t)count * n * n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t m = e / ((int64_t)n * n), r = (e / n) % n, q = e % n;
+    base[m * stride + r * n + q] = (r == q) ? (T)(n + 1) : T(1);
+  }
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_fill_spd(T *base, int64_t stride, int count, int n, cudaStream_t st) {
+  fill_spd_kernel<T><<<1024, 256, 0, st>>>(base, stride, count, n);
+  count_launch();
+  return cudaGetLastError();
+}
+template cudaError_t launch_fill_spd<double>(double *, int64_t, int, int, cudaStream_t);
+template cudaError_t launch_fill_spd<float>(float *, int64_t, int, int, cudaStream_t);
+
+size_t batched_smem_bytes() { return 200 * 1024; }
+
+template <typename T>
+cudaError_t launch_chol_batched_plan(int count, const int *order, const int *n, const int *step,
+                                     void *const *A, const int64_t *lda, void *const *L,
+                                     const int64_t *ldl, int *info, int *ticket, int sm_count,
+                                     int exact, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  const size_t smem = batched_smem_bytes();
+  static cudaError_t attr = cudaFuncSetAttribute(
+      batched_chol_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (attr != cudaSuccess) return attr;
+  cudaError_t e = cudaMemsetAsync(ticket, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  Plan p{count, order, n, step, A, lda, L, ldl, info, ticket};
+  const int grid = count < sm_count ? count : sm_count;
+  batched_chol_kernel<T><<<grid, BT, smem, st>>>(p, (int64_t)(smem / sizeof(T)), exact);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_chol_batched_plan<double>(int, const int *, const int *, const int *,
+                                                      void *const *, const int64_t *, void *const *,
+                                                      const int64_t *, int *, int *, int, int,
+                                                      cudaStream_t);
+template cudaError_t launch_chol_batched_plan<float>(int, const int *, const int *, const int *,
+                                                     void *const *, const int64_t *, void *const *,
+                                                     const int64_t *, int *, int *, int, int,
+                                                     cudaStream_t);
+
+}  // namespace gb

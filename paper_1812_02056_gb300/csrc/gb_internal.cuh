@@ -71,6 +71,19 @@ struct gb_handle {
   };
   std::vector<ProfRec> prof_pending;
   std::vector<cudaEvent_t> prof_pool;
+  // batched: step per order bucket (index 0 FP64, 1 FP32), 0 = default rule
+  int batched_step[2][32] = {};
+  int batched_exact = 0;
+  // the uploaded batched plan (device addresses inside ws[WS_MISC])
+  struct BatchPlanDev {
+    int count = 0;
+    int dt = -1;
+    const int *order = nullptr, *n = nullptr, *step = nullptr;
+    void *const *A = nullptr;
+    void *const *L = nullptr;
+    const int64_t *lda = nullptr, *ldl = nullptr;
+    int *ticket = nullptr;
+  } plan;
 };
 
 namespace gb {
@@ -164,10 +177,18 @@ cudaError_t launch_backward_error(int is_lu, const double *A, int64_t lda, const
 template <typename Tf>
 cudaError_t launch_check_diag(const Tf *F, int64_t ldf, int64_t n, int *flag, cudaStream_t st);
 
-// Batched (batched.cu)
+// Batched (batched.cu): one persistent launch over a plan in device memory
+// (order = LPT permutation, per-matrix order n, step, pointer, leading
+// dimension, info); `ticket` is reset by the launcher.
+constexpr int BATCH_MAX_N = 1024;
+constexpr int BATCH_BUCKETS = 32;  // step table: orders 1..1024 in buckets of 32
+size_t batched_smem_bytes();
 template <typename T>
-cudaError_t launch_chol_batched(int64_t count, const int *order, const int *nn, T *const *A,
-                                const int64_t *lda, const int *steps, int *info, int *ticket,
-                                int sm_count, cudaStream_t st);
+cudaError_t launch_chol_batched_plan(int count, const int *order, const int *n, const int *step,
+                                     void *const *A, const int64_t *lda, void *const *L,
+                                     const int64_t *ldl, int *info, int *ticket, int sm_count,
+                                     int exact, cudaStream_t st);
+template <typename T>
+cudaError_t launch_fill_spd(T *base, int64_t stride, int count, int n, cudaStream_t st);
 
 }  // namespace gb

@@ -157,3 +157,34 @@ def served_requests(count: int, seed: int, n_lo: int = 32, n_hi: int = 8192,
     n = np.clip(np.round(np.exp(logn)).astype(np.int64), n_lo, n_hi)
     nrhs = g.integers(1, nrhs_hi + 1, size=count).astype(np.int64)
     return arrival, n, nrhs
+
+
+def batch_spd_device(sizes, seed: int, device, dtype=None):
+    """Many SPD matrices ``G G^T + n I`` (G iid N(0, 1), drawn by torch's
+    seeded Philox on ``device``), packed back to back in one flat buffer:
+    returns ``(buf, offsets)`` with matrix ``i`` at
+    ``buf[offsets[i] : offsets[i] + n_i * n_i]`` (row-major, ``ld = n_i``).
+    Matrices of the same order are generated together."""
+    import torch
+    dtype = dtype or torch.float64
+    sizes = np.asarray(sizes, dtype=np.int64)
+    offs = np.zeros(len(sizes), dtype=np.int64)
+    if len(sizes) > 1:
+        offs[1:] = np.cumsum(sizes ** 2)[:-1]
+    total = int((sizes ** 2).sum())
+    buf = torch.empty(max(total, 1), dtype=dtype, device=device)
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    for n in np.unique(sizes):
+        n = int(n)
+        idx = np.nonzero(sizes == n)[0]
+        for c0 in range(0, len(idx), 2048):
+            part = idx[c0:c0 + 2048]
+            G = torch.randn((len(part), n, n), generator=g, device=device, dtype=torch.float64)
+            A = G @ G.transpose(1, 2)
+            A = torch.tril(A) + torch.tril(A, -1).transpose(1, 2)
+            A.diagonal(dim1=1, dim2=2).add_(float(n))
+            A = A.to(dtype).reshape(len(part), n * n)
+            for j, i in enumerate(part):
+                buf[offs[i]:offs[i] + n * n] = A[j]
+    return buf, offs
