@@ -561,6 +561,89 @@ def run_batched(args):
     return 0
 
 
+# ------------------------------------------------------------- served
+def run_served(args):
+    """Poisson stream of factor-and-solve jobs, n log-uniform on [32, 8192],
+    1..64 right-hand sides, A = G G^T + n I, mixed-precision factor with FP64
+    refinement, through the continuous-batching server with an HBM budget of
+    80% of free memory.  Saturated throughput first (all jobs at once), then
+    arrival rates at fractions of it; p50/p99 latency and solves/s."""
+    import threading
+
+    import numpy as np
+    import torch
+
+    from paper_1812_02056_gb300 import _build, binding, inputs
+    _build.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    count = args.served_count
+    _, n_all, k_all = inputs.served_requests(count, inputs.seed_for(inputs.W_SERVED),
+                                              n_lo=32, n_hi=args.served_nmax)
+    t0 = time.perf_counter()
+    jobs = []
+    for i in range(count):
+        n, k = int(n_all[i]), int(k_all[i])
+        A = inputs.spd_gram(n, inputs.seed_for(inputs.W_SERVED, 10 + i), device=dev)
+        B = torch.from_numpy(inputs.rhs(n, k, inputs.seed_for(inputs.W_SERVED, 5000 + i))).to(dev)
+        jobs.append((A, B, torch.empty_like(B)))
+    torch.cuda.synchronize()
+    out = {"mode": "served", "count": count, "dtype": args.served_dtype, "slots": args.slots,
+           "n_range": [32, args.served_nmax], "input_generation_s": time.perf_counter() - t0,
+           "runs": {}}
+    srv = binding.Server(0, 0, args.slots)
+
+    def run(arrivals):
+        srv.reset_stats()
+        tickets = [None] * count
+        start = time.perf_counter()
+
+        def producer():
+            for i in range(count):
+                if arrivals is not None:
+                    d = arrivals[i] - (time.perf_counter() - start)
+                    if d > 0:
+                        time.sleep(d)
+                A, B, X = jobs[i]
+                tickets[i] = srv.submit(A, B, X, dtype=args.served_dtype)
+
+        th = threading.Thread(target=producer)
+        th.start()
+        th.join()
+        res = [srv.wait(t) for t in tickets]
+        st = srv.stats()
+        el = time.perf_counter() - start
+        its = [r.iterations for r in res]
+        return {"p50_ms": st.p50_ms, "p99_ms": st.p99_ms, "max_ms": st.max_ms,
+                "solves_per_s": count / el, "server_solves_per_s": st.solves_per_s,
+                "max_running": st.max_running, "failed": sum(1 for r in res if r.status != 0),
+                "mean_queue_ms": float(np.mean([r.queue_ms for r in res])),
+                "mean_ir_iterations": float(np.mean(its)), "max_eta": max(r.eta for r in res)}
+
+    run(None)  # warm-up: builds, autotunes nothing, fills the allocator pools
+    sat = run(None)
+    out["runs"]["saturated"] = sat
+    rate_sat = sat["solves_per_s"]
+    for frac in (0.25, 0.5, 0.8, 0.95):
+        rate = frac * rate_sat
+        arr = np.cumsum(inputs.rng(inputs.seed_for(inputs.W_SERVED, 77)).exponential(1.0 / rate,
+                                                                                   size=count))
+        r = run(arr)
+        r["offered_rate"] = rate
+        out["runs"][f"rate_{int(frac * 100)}pct"] = r
+    # host check of a sample of the last run's results
+    worst = 0.0
+    for i in range(0, count, max(1, count // 8)):
+        A, B, X = jobs[i]
+        R = B - A @ X
+        den = A.abs().sum(1).max() * X.abs().max(0).values + B.abs().max(0).values
+        worst = max(worst, float((R.abs().max(0).values / den).max()))
+    out["sample_eta_host_max"] = worst
+    srv.close()
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -576,7 +659,8 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip sweeps and accuracy figures")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--mode", choices=["chol", "update", "mixed", "batched"], default="chol",
+    ap.add_argument("--mode", choices=["chol", "update", "mixed", "batched", "served"],
+                    default="chol",
                     help="chol: the benchmark line; update: the tensor-core rank-s update "
                          "alone; mixed: FP64 vs mixed-precision time to solution")
     ap.add_argument("--ks", default="256,512,1024,2048")
@@ -586,6 +670,10 @@ def main():
     ap.add_argument("--s-mixed", type=int, default=1024)
     ap.add_argument("--batch-count", type=int, default=10000)
     ap.add_argument("--batch-cpu-sample", type=int, default=200)
+    ap.add_argument("--served-count", type=int, default=400)
+    ap.add_argument("--served-nmax", type=int, default=8192)
+    ap.add_argument("--served-dtype", default="mix_bf16")
+    ap.add_argument("--slots", type=int, default=8)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -595,6 +683,8 @@ def main():
         return run_mixed(args)
     if args.mode == "batched":
         return run_batched(args)
+    if args.mode == "served":
+        return run_served(args)
     return run_ours(args)
 
 

@@ -280,6 +280,74 @@ gb_status gb_chol_solve_noalloc(int64_t n, int64_t nrhs, gb_dtype factor_dt, con
                                 int64_t ldl, const double *B, int64_t ldb, double *X,
                                 int64_t ldx, void *stream);
 
+/* ---------------------------------------------------------------- served */
+/*
+ * A continuous-batching request server (no counterpart in the paper, which
+ * factors one matrix at a time): factor-and-solve jobs of mixed sizes are
+ * submitted at any time; a scheduler thread admits the oldest job as soon as
+ * a slot is free and its device-memory footprint fits the budget; each slot
+ * owns a handle, a stream and a worker thread, so admitted jobs overlap on
+ * the device.  A job runs gb_chol_factor with a step chosen from (n, dtype)
+ * alone -- never from the load -- and gb_chol_solve, refined in FP64 for the
+ * reduced-precision dtypes, so its result is the same bits alone or among
+ * other jobs.
+ */
+typedef struct gb_server gb_server;
+
+typedef struct gb_request {
+  int64_t n, nrhs;     /* order and number of right-hand sides (>= 1)       */
+  gb_dtype dtype;      /* factor arithmetic                                  */
+  int64_t s;           /* step, or 0 for the served default for (n, dtype)   */
+  const double *A;     /* n x n SPD, full symmetric square, host or device   */
+  int64_t lda;
+  const double *B;     /* n x nrhs right-hand sides, host or device          */
+  int64_t ldb;
+  double *X;           /* n x nrhs solution, host or device                  */
+  int64_t ldx;
+  double tol;          /* refinement target (0: 1e-14)                      */
+  int max_iter;        /* refinement limit (0: 30)                          */
+} gb_request;
+
+typedef struct gb_result {
+  gb_status status;    /* GB_OK, GB_ERR_NOT_CONVERGED, GB_ERR_NOMEM, ...     */
+  int info;            /* factorization breakdown column (0 = none)          */
+  int iterations;      /* refinement corrections                             */
+  double eta;          /* final normwise backward error                      */
+  double queue_ms;     /* submit -> admission                                */
+  double compute_ms;   /* admission -> completion                            */
+  double total_ms;     /* submit -> completion                               */
+} gb_result;
+
+typedef struct gb_server_stats {
+  uint64_t completed, rejected, queued;
+  int running, max_running;      /* jobs on the device now / at most so far   */
+  double p50_ms, p99_ms, max_ms;  /* total latency of completed jobs            */
+  double solves_per_s;            /* completed / (last completion - 1st submit) */
+  size_t budget_bytes, bytes_in_use;
+} gb_server_stats;
+
+/* Create a server on `device` with `max_slots` (1..64) concurrent jobs and
+ * a device-memory budget in bytes (0: 80% of the currently free memory). */
+gb_status gb_server_create(int device, size_t hbm_budget, int max_slots, gb_server **out);
+
+/* Queue a job.  The caller's buffers must stay valid until the job is
+ * waited for; nothing is copied at submission.  Returns GB_ERR_REJECTED if
+ * the job's footprint exceeds the whole budget. */
+gb_status gb_server_submit(gb_server *srv, const gb_request *req, uint64_t *ticket);
+
+/* Wait up to timeout_s seconds (< 0: forever) for a job; on success fills
+ * *out and forgets the ticket; GB_ERR_TIMEOUT if it is still running. */
+gb_status gb_server_wait(gb_server *srv, uint64_t ticket, double timeout_s, gb_result *out);
+
+/* Non-blocking wait: GB_ERR_STATE while the job is pending. */
+gb_status gb_server_poll(gb_server *srv, uint64_t ticket, gb_result *out);
+
+gb_status gb_server_get_stats(gb_server *srv, gb_server_stats *out);
+gb_status gb_server_reset_stats(gb_server *srv);
+
+/* Finish the queued and running jobs, then stop the threads and free. */
+gb_status gb_server_destroy(gb_server *srv);
+
 /* ---------------------------------------------------------- diagnostics */
 /* Phases of a factorization, as timed under GB_OPT_PROFILE. */
 typedef enum gb_phase {

@@ -47,6 +47,28 @@ class RefineOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int)]
 
 
+class Request(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nrhs", ctypes.c_int64), ("dtype", ctypes.c_int),
+                ("s", ctypes.c_int64), ("A", ctypes.c_void_p), ("lda", ctypes.c_int64),
+                ("B", ctypes.c_void_p), ("ldb", ctypes.c_int64), ("X", ctypes.c_void_p),
+                ("ldx", ctypes.c_int64), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("info", ctypes.c_int), ("iterations", ctypes.c_int),
+                ("eta", ctypes.c_double), ("queue_ms", ctypes.c_double),
+                ("compute_ms", ctypes.c_double), ("total_ms", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_uint64), ("rejected", ctypes.c_uint64),
+                ("queued", ctypes.c_uint64), ("running", ctypes.c_int),
+                ("max_running", ctypes.c_int), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
+                ("solves_per_s", ctypes.c_double), ("budget_bytes", ctypes.c_size_t),
+                ("bytes_in_use", ctypes.c_size_t)]
+
+
 class SolveStats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("eta", ctypes.c_double)]
 
@@ -76,6 +98,13 @@ SIGNATURES = {
     "gb_rank_update": (_I32, [_P, _I32, _I32, _I32, _I64, _I64, _I64, _P, _I64, _P, _I64, _P,
                               _I64, _P]),
     "gb_batched_tune": (_I32, [_P, _I32, _I64, _P, _P]),
+    "gb_server_create": (_I32, [_I32, ctypes.c_size_t, _I32, ctypes.POINTER(_P)]),
+    "gb_server_submit": (_I32, [_P, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),
+    "gb_server_wait": (_I32, [_P, ctypes.c_uint64, _D, ctypes.POINTER(Result)]),
+    "gb_server_poll": (_I32, [_P, ctypes.c_uint64, ctypes.POINTER(Result)]),
+    "gb_server_get_stats": (_I32, [_P, ctypes.POINTER(ServerStats)]),
+    "gb_server_reset_stats": (_I32, [_P]),
+    "gb_server_destroy": (_I32, [_P]),
     "gb_profile_read": (_I32, [_P, _P]),
     "gb_kernel_launches": (ctypes.c_uint64, []),
     "gb_measure_fma_peak": (_I32, [_P, _I32, ctypes.POINTER(_D)]),
@@ -337,3 +366,63 @@ class Handle:
         n = A.shape[0]
         return self.gb_backward_error(1 if lu else 0, n, DTYPES[dtype], A, _ld(A), F, _ld(F),
                                       stream)
+
+
+class Server:
+    """Continuous-batching factor-and-solve server (gb_server_*)."""
+
+    def __init__(self, device: int = 0, hbm_budget: int = 0, max_slots: int = 4):
+        self.lib = load()
+        p = ctypes.c_void_p()
+        check(self.lib.gb_server_create(int(device), int(hbm_budget), int(max_slots),
+                                        ctypes.byref(p)), "gb_server_create")
+        self.p = p
+        self._keep = {}
+
+    def submit(self, A, B, X, dtype: str = "mix_bf16", s: int = 0, tol: float = 1e-14,
+               max_iter: int = 30) -> int:
+        """Queue A X = B (tensors or arrays stay referenced until waited for)."""
+        n, nrhs = B.shape
+        r = Request(n, nrhs, DTYPES[dtype], s, _ptr(A), _ld(A), _ptr(B), _ld(B), _ptr(X), _ld(X),
+                    tol, max_iter)
+        t = ctypes.c_uint64()
+        check(self.lib.gb_server_submit(self.p, ctypes.byref(r), ctypes.byref(t)),
+              "gb_server_submit")
+        self._keep[t.value] = (A, B, X)
+        return t.value
+
+    def wait(self, ticket: int, timeout_s: float = -1.0) -> Result:
+        res = Result()
+        check(self.lib.gb_server_wait(self.p, ticket, timeout_s, ctypes.byref(res)),
+              "gb_server_wait")
+        self._keep.pop(ticket, None)
+        return res
+
+    def poll(self, ticket: int):
+        res = Result()
+        st = self.lib.gb_server_poll(self.p, ticket, ctypes.byref(res))
+        if st == GB_ERR_STATE:
+            return None
+        check(st, "gb_server_poll")
+        self._keep.pop(ticket, None)
+        return res
+
+    def stats(self) -> ServerStats:
+        s = ServerStats()
+        check(self.lib.gb_server_get_stats(self.p, ctypes.byref(s)), "gb_server_get_stats")
+        return s
+
+    def reset_stats(self):
+        check(self.lib.gb_server_reset_stats(self.p), "gb_server_reset_stats")
+
+    def close(self):
+        if self.p:
+            self.lib.gb_server_destroy(self.p)
+            self.p = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -99,17 +99,18 @@ def test_batched_out_of_place_and_padded(h):
         big = torch.full((n, n + 3), 7.0, dtype=torch.float64, device=DEV)
         big[:, :n] = m
         padded.append(big[:, :n])
-    outs = [torch.full((m.shape[0], m.shape[0] + 1), 9.0, dtype=torch.float64,
-                       device=DEV)[:, :m.shape[0]] for m in mats]
+    out_big = [torch.full((m.shape[0], m.shape[0] + 1), 9.0, dtype=torch.float64, device=DEV)
+               for m in mats]
+    outs = [b[:, :m.shape[0]] for b, m in zip(out_big, mats)]
     before = [p.clone() for p in padded]
     info = h.chol_factor_batched(padded, s=8, dtype="f64", outs=outs)
     assert np.all(info == 0)
     for p, b in zip(padded, before):
         assert torch.equal(p, b)  # inputs untouched
-    for m, o in zip(mats, outs):
+    for m, o, b in zip(mats, outs, out_big):
         Lo, _ = oracle.chol(m.cpu().numpy(), 8)
         assert guarded_rel_err(o.cpu().numpy(), Lo) <= 1e-10
-        assert bool((o.base[:, m.shape[0]:] == 9.0).all())  # padding untouched
+        assert bool((b[:, m.shape[0]:] == 9.0).all())  # padding untouched
 
 
 def test_batched_graph_capture_and_replay(h):
