@@ -240,15 +240,18 @@ gb_status chol_blocked(gb_handle *h, int64_t n, int64_t s, T *W, int64_t ld, int
     for (int64_t j0 = z; j0 < pe; j0 += b) {
       const int bw = (int)std::min(b, pe - j0);
       const size_t e = sizeof(T);
-      {
-        PhaseTimer t(h, st, GB_PHASE_DIAG, (double)bw * bw * bw / 3.0, (double)bw * bw * e);
-        GB_CUDA_TRY((launch_chol_diag<T, Tc>(W, ld, j0, bw, status, st)));
-      }
       const int64_t r0 = j0 + bw;
-      if (r0 < n) {
-        PhaseTimer t(h, st, GB_PHASE_PANEL, (double)(n - r0) * bw * bw,
-                     2.0 * (double)(n - r0) * bw * e);
-        GB_CUDA_TRY(launch_chol_rows<T>(W, ld, r0, n - r0, j0, bw, status, st));
+      {
+        // diagonal block and the rows below it, one fused launch
+        PhaseTimer t(h, st, GB_PHASE_PANEL,
+                     (double)bw * bw * bw / 3.0 + (double)(n - r0) * bw * bw,
+                     (double)bw * bw * e + 2.0 * (double)(n - r0) * bw * e);
+        if constexpr (sizeof(Tc) > sizeof(T))  // mixed: FP64 square roots and pivots
+          GB_CUDA_TRY((launch_chol_panel<T, true>(W, ld, j0, bw, n - r0, status, h->d_arrivals,
+                                                  st)));
+        else
+          GB_CUDA_TRY((launch_chol_panel<T, false>(W, ld, j0, bw, n - r0, status, h->d_arrivals,
+                                                   st)));
       }
       if (r0 < pe) {  // the s-block's remaining columns receive this inner block
         PhaseTimer t(h, st, GB_PHASE_INNER, update_flops(n - r0, pe - r0, bw, true),
@@ -470,17 +473,40 @@ gb_status factor_common(bool is_lu, gb_handle *h, int64_t n, int64_t s, gb_dtype
 }
 
 // ------------------------------------------------------------------ solves
+// L Y = B then L^T X = Y (Cholesky) or U X = Y (LU), through inverted
+// diagonal blocks.  The inverses depend on the factor only: computed once per
+// solve call and reused by every refinement step.
 template <typename Tf>
-gb_status tri_solve(gb_handle *h, bool is_lu, const Tf *F, int64_t ldf, double *X, int64_t ldx,
-                    int64_t n, int64_t nrhs, cudaStream_t st) {
+struct SolvePlan {
+  Tf *dinv_lo = nullptr;  // inverses of the diagonal blocks of L
+  Tf *dinv_up = nullptr;  // of L^T (Cholesky) or of the unit U (LU)
+};
+
+template <typename Tf>
+gb_status solve_prepare(gb_handle *h, bool is_lu, const Tf *F, int64_t ldf, int64_t n,
+                        SolvePlan<Tf> &p, cudaStream_t st) {
+  const size_t one = trsm_inv_bytes(n, sizeof(Tf));
+  gb_status r = ws_reserve(h, WS_DINV, 2 * one, st);
+  if (r != GB_OK) return r;
+  p.dinv_lo = (Tf *)h->ws[WS_DINV].ptr;
+  p.dinv_up = (Tf *)((char *)h->ws[WS_DINV].ptr + one);
+  GB_CUDA_TRY(launch_diag_inv<Tf>(F, ldf, n, TRSM_LOWER, p.dinv_lo, st));
+  GB_CUDA_TRY(launch_diag_inv<Tf>(F, ldf, n, is_lu ? TRSM_UNIT_UPPER : TRSM_LOWER_T, p.dinv_up, st));
+  return GB_OK;
+}
+
+template <typename Tf>
+gb_status tri_solve(gb_handle *h, bool is_lu, const Tf *F, int64_t ldf, const SolvePlan<Tf> &p,
+                    double *X, int64_t ldx, int64_t n, int64_t nrhs, cudaStream_t st) {
   unsigned e1 = ++h->sync_epoch;
   if (e1 == 0) e1 = ++h->sync_epoch;
-  GB_CUDA_TRY((launch_trsm<Tf, Tf>(F, ldf, X, ldx, n, nrhs, TRSM_LOWER, h->d_sync, e1, h->d_err,
-                                   h->spin_limit, st)));
+  GB_CUDA_TRY((launch_trsm_inv<Tf>(F, ldf, p.dinv_lo, X, ldx, n, nrhs, TRSM_LOWER, h->d_sync, e1,
+                                   h->d_err, h->spin_limit, st)));
   unsigned e2 = ++h->sync_epoch;
   if (e2 == 0) e2 = ++h->sync_epoch;
-  GB_CUDA_TRY((launch_trsm<Tf, Tf>(F, ldf, X, ldx, n, nrhs, is_lu ? TRSM_UNIT_UPPER : TRSM_LOWER_T,
-                                   h->d_sync, e2, h->d_err, h->spin_limit, st)));
+  GB_CUDA_TRY((launch_trsm_inv<Tf>(F, ldf, p.dinv_up, X, ldx, n, nrhs,
+                                   is_lu ? TRSM_UNIT_UPPER : TRSM_LOWER_T, h->d_sync, e2, h->d_err,
+                                   h->spin_limit, st)));
   return GB_OK;
 }
 
@@ -517,7 +543,10 @@ gb_status solve_common(bool is_lu, gb_handle *h, int64_t n, int64_t nrhs, const 
 
   if (X != B)
     GB_CUDA_TRY(cudaMemcpy2DAsync(X, ldx * 8, B, ldb * 8, nrhs * 8, n, cudaMemcpyDeviceToDevice, st));
-  gb_status r = tri_solve<Tf>(h, is_lu, F, ldf, X, ldx, n, nrhs, st);
+  SolvePlan<Tf> plan;
+  gb_status r = solve_prepare<Tf>(h, is_lu, F, ldf, n, plan, st);
+  if (r != GB_OK) return r;
+  r = tri_solve<Tf>(h, is_lu, F, ldf, plan, X, ldx, n, nrhs, st);
   if (r != GB_OK) return r;
   if (!A) return read_device_error(h, st);
 
@@ -547,7 +576,7 @@ gb_status solve_common(bool is_lu, gb_handle *h, int64_t n, int64_t nrhs, const 
     }
     if (!std::isfinite(eta)) break;  // the iterate is lost; report non-convergence
     if (eta <= tol || it >= max_iter) break;
-    if ((r = tri_solve<Tf>(h, is_lu, F, ldf, R, nrhs, n, nrhs, st)) != GB_OK) return r;
+    if ((r = tri_solve<Tf>(h, is_lu, F, ldf, plan, R, nrhs, n, nrhs, st)) != GB_OK) return r;
     GB_CUDA_TRY(launch_axpy_cols(X, ldx, R, nrhs, n, nrhs, st));
     ++it;
   }
@@ -658,11 +687,13 @@ gb_status gb_create(gb_handle **out, int device) {
   bool ok = cudaMalloc(&h->d_status, sizeof(int)) == cudaSuccess &&
             cudaMalloc(&h->d_err, sizeof(int)) == cudaSuccess &&
             cudaMalloc(&h->d_sync, sizeof(int) * SYNC_WORDS) == cudaSuccess &&
-            cudaMalloc(&h->d_scalars, sizeof(double) * 4096) == cudaSuccess;
+            cudaMalloc(&h->d_scalars, sizeof(double) * 4096) == cudaSuccess &&
+            cudaMalloc(&h->d_arrivals, sizeof(unsigned long long)) == cudaSuccess;
   if (ok)
     ok = cudaMemset(h->d_status, 0, sizeof(int)) == cudaSuccess &&
          cudaMemset(h->d_err, 0, sizeof(int)) == cudaSuccess &&
          cudaMemset(h->d_sync, 0, sizeof(int) * SYNC_WORDS) == cudaSuccess &&
+         cudaMemset(h->d_arrivals, 0, sizeof(unsigned long long)) == cudaSuccess &&
          cudaDeviceSynchronize() == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
@@ -688,6 +719,7 @@ gb_status gb_destroy(gb_handle *h) {
   if (h->d_err) cudaFree(h->d_err);
   if (h->d_sync) cudaFree(h->d_sync);
   if (h->d_scalars) cudaFree(h->d_scalars);
+  if (h->d_arrivals) cudaFree(h->d_arrivals);
   delete h;
   return GB_OK;
 }

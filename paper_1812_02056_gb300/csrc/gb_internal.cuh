@@ -58,9 +58,10 @@ struct gb_handle {
   int *d_status = nullptr;   // scratch status word for host `info` pointers
   int *d_err = nullptr;      // device error word (DEV_ERR_*)
   int *d_sync = nullptr;     // flags / tickets for single-kernel solves (SYNC_WORDS ints)
+  unsigned long long *d_arrivals = nullptr;  // arrival counter of the fused panel kernel
   double *d_scalars = nullptr;  // small FP64 reduction outputs
   unsigned sync_epoch = 0;
-  gb::Workspace ws[4];       // named workspaces, see WS_* below
+  gb::Workspace ws[5];       // named workspaces, see WS_* below
   std::mutex mu;
   // GB_OPT_PROFILE: event pairs recorded around launches, read later
   int profile = 0;
@@ -88,7 +89,7 @@ struct gb_handle {
 
 namespace gb {
 
-enum { WS_STAGE = 0, WS_PANEL = 1, WS_SOLVE = 2, WS_MISC = 3 };
+enum { WS_STAGE = 0, WS_PANEL = 1, WS_SOLVE = 2, WS_MISC = 3, WS_DINV = 4 };
 constexpr int SYNC_WORDS = 1 << 16;
 
 // Make sure workspace `slot` holds >= bytes; waits for `stream` before
@@ -107,6 +108,11 @@ cudaError_t launch_chol_diag(T *W, int64_t ld, int64_t j0, int bw, int *status, 
 template <typename T>
 cudaError_t launch_chol_rows(T *W, int64_t ld, int64_t row0, int64_t nrows, int64_t j0, int bw,
                              int *status, cudaStream_t st);
+// Fused column steps of one inner block (diagonal block in every CTA, then
+// its rows); `arrivals` is a zeroed counter the kernel leaves zeroed.
+template <typename T, bool FP64_PIVOT>
+cudaError_t launch_chol_panel(T *W, int64_t ld, int64_t j0, int bw, int64_t nrows, int *status,
+                              unsigned long long *arrivals, cudaStream_t st);
 template <typename T, typename Tc>
 cudaError_t launch_lu_diag(T *W, int64_t ld, int64_t j0, int bw, int *status, cudaStream_t st);
 template <typename T>
@@ -164,6 +170,16 @@ cudaError_t launch_trsm(const Tf *F, int64_t ldf, double *B, int64_t ldb, int64_
                         int64_t nrhs, int kind, int *sync, unsigned epoch, int *err,
                         int64_t spin_limit, cudaStream_t st);
 enum { TRSM_LOWER = 0, TRSM_LOWER_T = 1, TRSM_UNIT_UPPER = 2 };
+// Solve through inverted diagonal blocks: launch_diag_inv fills Dinv
+// (trsm_inv_bytes), then launch_trsm_inv solves in place like launch_trsm.
+size_t trsm_inv_bytes(int64_t n, size_t esz);
+template <typename Tf>
+cudaError_t launch_diag_inv(const Tf *F, int64_t ldf, int64_t n, int kind, Tf *Dinv,
+                            cudaStream_t st);
+template <typename Tf>
+cudaError_t launch_trsm_inv(const Tf *F, int64_t ldf, const Tf *Dinv, double *B, int64_t ldb,
+                            int64_t n, int64_t nrhs, int kind, int *sync, unsigned epoch, int *err,
+                            int64_t spin_limit, cudaStream_t st);
 cudaError_t launch_residual(const double *A, int64_t lda, const double *X, int64_t ldx,
                             const double *B, int64_t ldb, double *R, int64_t ldr, int64_t n,
                             int64_t nrhs, double *norms, cudaStream_t st);

@@ -16,6 +16,8 @@
 // W already holds A minus every delayed update applied before this block.
 #include <math.h>
 
+#include <algorithm>
+
 #include "gb_internal.cuh"
 
 namespace gb {
@@ -124,6 +126,125 @@ __global__ void __launch_bounds__(ROWS_PER_CTA)
     const int r = idx / B, j = idx % B;
     if (r < rows_here && j < bw) W[(rbase + r) * ld + j0 + j] = X[r][j];
   }
+}
+
+// ------------------------------------------------ fused column-step kernel
+// One launch per inner block: every CTA factors the bw x bw diagonal block
+// itself (64 threads, thread i owns row i in registers) and then solves its
+// 128 rows below the block against it.  The factored diagonal block is
+// written back by the last CTA to have loaded it: each CTA bumps an arrival
+// counter after loading; the CTA that arrives as number grid - 1 knows every
+// other CTA already holds its own copy, writes the block, and resets the
+// counter to zero for the next launch (ordered after this one on the
+// stream).  No CTA waits.
+// FP64_PIVOT: square root and pivot division in FP64 on FP32 data (the
+// mixed dtypes); the rank-1 steps stay in the storage type.
+constexpr int PANEL_ROWS = 128;
+
+template <typename T, bool FP64_PIVOT>
+__device__ __forceinline__ T pivot_sqrt(T d) {
+  if (FP64_PIVOT) return (T)sqrt((double)d);
+  return sqrt(d);
+}
+template <typename T, bool FP64_PIVOT>
+__device__ __forceinline__ T pivot_div(T a, T b) {
+  if (FP64_PIVOT) return (T)((double)a / (double)b);
+  return a / b;
+}
+
+template <typename T, bool FP64_PIVOT>
+__global__ void __launch_bounds__(PANEL_ROWS)
+    chol_panel_kernel(T *__restrict__ W, int64_t ld, int64_t j0, int bw, int64_t row0,
+                      int64_t nrows, int *status, unsigned long long *arrivals) {
+  constexpr int B = 64;
+  constexpr int PAD = B + 16 / (int)sizeof(T);  // 16-byte aligned rows
+  __shared__ __align__(16) T LT[B][PAD];         // LT[c][j] = L_jc (column c of the block)
+  __shared__ T colc[2][B];
+  __shared__ int s_ok[2];
+  __shared__ int s_last;
+  if (load_status(status) != 0) return;
+  const int tid = threadIdx.x;
+  T *D = W + j0 * ld + j0;
+
+  // ---- diagonal block: thread i < bw owns row i (entries j <= i)
+  T x[B];
+#pragma unroll
+  for (int j = 0; j < B; ++j) x[j] = (tid < bw && j <= tid) ? D[(int64_t)tid * ld + j] : T(0);
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    const unsigned long long a = atomicAdd(arrivals, 1ULL);
+    s_last = (a == (unsigned long long)gridDim.x - 1) ? 1 : 0;
+    if (s_last) atomicExch(arrivals, 0ULL);  // every CTA has arrived
+  }
+  bool ok = true;
+  int bad_col = 0;
+#pragma unroll
+  for (int c = 0; c < B; ++c) {
+    if (c < bw && ok) {
+      const int b = c & 1;
+      if (tid == c) {
+        const T d = x[c];
+        s_ok[b] = (d > T(0)) ? 1 : 0;  // not positive, or NaN: breakdown
+        colc[b][c] = pivot_sqrt<T, FP64_PIVOT>(d);
+      }
+      __syncthreads();
+      if (!s_ok[b]) {
+        ok = false;
+        bad_col = c;
+      } else {
+        const T lcc = colc[b][c];
+        if (tid == c) x[c] = lcc;
+        if (tid > c && tid < bw) {
+          x[c] = pivot_div<T, FP64_PIVOT>(x[c], lcc);
+          colc[b][tid] = x[c];
+        }
+        __syncthreads();
+        if (tid > c && tid < bw) {
+          const T xc = x[c];
+#pragma unroll
+          for (int j = c + 1; j < B; ++j)
+            if (j <= tid) x[j] = x[j] - xc * colc[b][j];
+        }
+      }
+    }
+  }
+  if (!ok) {
+    if (blockIdx.x == 0 && tid == 0) atomicCAS(status, 0, (int)(j0 + bad_col + 1));
+    return;  // ok is uniform over the CTA
+  }
+  if (tid < B) {
+#pragma unroll
+    for (int j = 0; j < B; ++j) LT[j][tid] = (j <= tid && tid < bw) ? x[j] : T(0);
+  }
+  __syncthreads();
+  if (s_last && tid < bw) {
+#pragma unroll
+    for (int j = 0; j < B; ++j)
+      if (j <= tid) D[(int64_t)tid * ld + j] = x[j];
+  }
+
+  // ---- rows below the block: thread t owns row rbase + t
+  const int64_t r = row0 + (int64_t)blockIdx.x * PANEL_ROWS + tid;
+  if (r >= row0 + nrows) return;
+  T *row = W + r * ld + j0;
+  T y[B];
+#pragma unroll
+  for (int c = 0; c < B; ++c) y[c] = (c < bw) ? row[c] : T(0);
+  // y_c = (a_c - sum_{k<c} y_k L_ck) / L_cc, each product subtracted as soon
+  // as y_k is final, so every entry still receives them in ascending k
+#pragma unroll
+  for (int c = 0; c < B; ++c) {
+    if (c < bw) {
+      const T yc = y[c] / LT[c][c];
+      y[c] = yc;
+#pragma unroll
+      for (int c2 = c + 1; c2 < B; ++c2) y[c2] = y[c2] - yc * LT[c][c2];
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < B; ++c)
+    if (c < bw) row[c] = y[c];
 }
 
 // ---------------------------------------------------------------------- LU
@@ -312,6 +433,17 @@ cudaError_t launch_chol_rows(T *W, int64_t ld, int64_t row0, int64_t nrows, int6
   return chol_rows_b<T, 64>(W, ld, row0, nrows, j0, bw, status, st);
 }
 
+template <typename T, bool FP64_PIVOT>
+cudaError_t launch_chol_panel(T *W, int64_t ld, int64_t j0, int bw, int64_t nrows, int *status,
+                              unsigned long long *arrivals, cudaStream_t st) {
+  if (bw < 1 || bw > 64) return cudaErrorInvalidValue;
+  const int64_t grid = std::max<int64_t>(1, (nrows + PANEL_ROWS - 1) / PANEL_ROWS);
+  chol_panel_kernel<T, FP64_PIVOT><<<(unsigned)grid, PANEL_ROWS, 0, st>>>(
+      W, ld, j0, bw, j0 + bw, nrows, status, arrivals);
+  count_launch();
+  return cudaGetLastError();
+}
+
 template <typename T, typename Tc>
 cudaError_t launch_lu_diag(T *W, int64_t ld, int64_t j0, int bw, int *status, cudaStream_t st) {
   if (bw < 1 || bw > 64) return cudaErrorInvalidValue;
@@ -358,6 +490,9 @@ template cudaError_t launch_chol_diag<float, float>(float *, int64_t, int64_t, i
 template cudaError_t launch_chol_diag<float, double>(float *, int64_t, int64_t, int, int *, cudaStream_t);
 template cudaError_t launch_chol_rows<double>(double *, int64_t, int64_t, int64_t, int64_t, int, int *, cudaStream_t);
 template cudaError_t launch_chol_rows<float>(float *, int64_t, int64_t, int64_t, int64_t, int, int *, cudaStream_t);
+template cudaError_t launch_chol_panel<double, false>(double *, int64_t, int64_t, int, int64_t, int *, unsigned long long *, cudaStream_t);
+template cudaError_t launch_chol_panel<float, false>(float *, int64_t, int64_t, int, int64_t, int *, unsigned long long *, cudaStream_t);
+template cudaError_t launch_chol_panel<float, true>(float *, int64_t, int64_t, int, int64_t, int *, unsigned long long *, cudaStream_t);
 template cudaError_t launch_lu_diag<double, double>(double *, int64_t, int64_t, int, int *, cudaStream_t);
 template cudaError_t launch_lu_diag<float, float>(float *, int64_t, int64_t, int, int *, cudaStream_t);
 template cudaError_t launch_lu_diag<float, double>(float *, int64_t, int64_t, int, int *, cudaStream_t);

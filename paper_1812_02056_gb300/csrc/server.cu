@@ -131,7 +131,16 @@ void run_job(gb_server *S, gb_server::Slot &slot, gb_server::Job &J) {
     fail(GB_ERR_CUDA);
   int info = 0;
   if (st_all == GB_OK) {
-    gb_status e = gb_chol_factor(h, n, s, r.dtype, A, lda, dL, n, dinfo, st);
+    gb_status e;
+    if (r.dtype == GB_F32) {
+      // GB_F32 factors read float input: cast A's lower triangle into the
+      // factor buffer and factor it in place
+      const cudaError_t ce = launch_copy_matrix<double, float>(A, lda, (float *)dL, n, n, true, st);
+      e = ce == cudaSuccess ? gb_chol_factor(h, n, s, r.dtype, dL, n, dL, n, dinfo, st)
+                            : GB_ERR_CUDA;
+    } else {
+      e = gb_chol_factor(h, n, s, r.dtype, A, lda, dL, n, dinfo, st);
+    }
     if (e != GB_OK) fail(e);
   }
   if (st_all == GB_OK) {

@@ -149,6 +149,151 @@ __global__ void __launch_bounds__(TRSM_THREADS)
   }
 }
 
+// ---------------------------------------- solve with inverted diagonal blocks
+// Pre-pass: Dinv[b] = inverse of the b-th TB x TB diagonal block of op(F),
+// one CTA of TB threads per block, thread j computing column j of the
+// inverse by substitution.  The solve below then finishes a block with the
+// small product X_b = Dinv[b] * (b - contributions): no dependent chain of
+// length TB on the critical path.
+template <typename Tf, typename Tc>
+__global__ void __launch_bounds__(TB)
+    diag_inv_kernel(const Tf *__restrict__ F, int64_t ldf, int64_t n, int kind,
+                    Tc *__restrict__ Dinv) {
+  __shared__ Tc Bs[TB][TB + 1];
+  const int b = blockIdx.x, j = threadIdx.x;
+  const int64_t r0 = (int64_t)b * TB;
+  const int rows = (int)min64(TB, n - r0);
+  for (int i = 0; i < TB; ++i)
+    Bs[i][j] = (i < rows && j < rows) ? (Tc)op_elem(F, ldf, kind, r0 + i, r0 + j) : Tc(0);
+  __syncthreads();
+  Tc y[TB];
+#pragma unroll
+  for (int i = 0; i < TB; ++i) y[i] = Tc(0);
+  if (j < rows) {
+    if (kind == TRSM_LOWER) {  // lower, non-unit: forward substitution on e_j
+#pragma unroll
+      for (int i = 0; i < TB; ++i) {
+        if (i >= j && i < rows) {
+          Tc v = (i == j) ? Tc(1) : Tc(0);
+#pragma unroll
+          for (int k = 0; k < i; ++k)
+            if (k >= j) v = v - Bs[i][k] * y[k];
+          y[i] = v / Bs[i][i];
+        }
+      }
+    } else {  // upper (L^T, or unit U): back substitution on e_j
+      const bool unit = (kind == TRSM_UNIT_UPPER);
+#pragma unroll
+      for (int i = TB - 1; i >= 0; --i) {
+        if (i <= j) {
+          Tc v = (i == j) ? Tc(1) : Tc(0);
+#pragma unroll
+          for (int k = i + 1; k < TB; ++k)
+            if (k <= j) v = v - Bs[i][k] * y[k];
+          y[i] = unit ? v : v / Bs[i][i];
+        }
+      }
+    }
+  }
+  Tc *D = Dinv + (int64_t)b * TB * TB;
+#pragma unroll
+  for (int i = 0; i < TB; ++i) D[i * TB + j] = (i < rows && j < rows) ? y[i] : Tc(0);
+}
+
+template <typename Tf, typename Tc>
+__global__ void __launch_bounds__(TRSM_THREADS)
+    trsm_inv_kernel(const Tf *__restrict__ F, int64_t ldf, const Tc *__restrict__ Dinv, double *B,
+                    int64_t ldb, int64_t n, int64_t nrhs, int kind, int *ticket, int *flags,
+                    unsigned epoch, int *err, long long wait_ns) {
+  __shared__ Tc Fs[TB][TB + 1];
+  __shared__ Tc Xs[TB][NRC + 1];
+  __shared__ int s_ib, s_abort;
+  const int tid = threadIdx.x;
+  const int nb = (int)((n + TB - 1) / TB);
+  const bool fwd = (kind == TRSM_LOWER);
+  if (tid == 0) {
+    const int t = atomicAdd(ticket, 1);
+    s_ib = fwd ? t : nb - 1 - t;
+    s_abort = 0;
+  }
+  __syncthreads();
+  const int ib = s_ib;
+  if (ib < 0 || ib >= nb) return;
+  const int64_t r0 = (int64_t)ib * TB;
+  const int rows = (int)min64(TB, n - r0);
+  const int tr = tid / (NRC / 4), tc = (tid % (NRC / 4)) * 4;
+
+  for (int64_t c0 = 0; c0 < nrhs; c0 += NRC) {
+    const int cols = (int)min64(NRC, nrhs - c0);
+    Tc acc[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      acc[q] = (tr < rows && tc + q < cols) ? (Tc)B[(r0 + tr) * ldb + c0 + tc + q] : Tc(0);
+    for (int step = 0; step < (fwd ? ib : nb - 1 - ib); ++step) {
+      const int jb = fwd ? step : nb - 1 - step;
+      // load the off-diagonal block before waiting: it does not depend on X
+      const int64_t k0 = (int64_t)jb * TB;
+      const int kr = (int)min64(TB, n - k0);
+      for (int idx = tid; idx < TB * TB; idx += TRSM_THREADS) {
+        const int i = idx / TB, k = idx % TB;
+        Fs[i][k] = (i < rows && k < kr) ? (Tc)op_elem(F, ldf, kind, r0 + i, k0 + k) : Tc(0);
+      }
+      if (tid == 0) {
+        int spins = 0;
+        const long long t0 = (long long)globaltimer_ns();
+        while (ld_acquire(&flags[jb]) != (int)epoch) {
+          if ((++spins & 255) == 0) {
+            if (ld_acquire(err) & DEV_ERR_TIMEOUT) {
+              s_abort = 1;
+              break;
+            }
+            if ((long long)globaltimer_ns() - t0 > wait_ns) {
+              atomicOr(err, DEV_ERR_TIMEOUT);
+              s_abort = 1;
+              break;
+            }
+          }
+        }
+      }
+      __syncthreads();
+      if (s_abort) return;
+      for (int idx = tid; idx < TB * NRC; idx += TRSM_THREADS) {
+        const int k = idx / NRC, c = idx % NRC;
+        Xs[k][c] = (k < kr && c < cols) ? (Tc)__ldcg(&B[(k0 + k) * ldb + c0 + c]) : Tc(0);
+      }
+      __syncthreads();
+#pragma unroll 8
+      for (int k = 0; k < TB; ++k) {
+        const Tc f = Fs[tr][k];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q] = acc[q] - f * Xs[k][tc + q];
+      }
+      __syncthreads();
+    }
+    // X_b = Dinv[b] * acc
+    const Tc *D = Dinv + (int64_t)ib * TB * TB;
+    for (int idx = tid; idx < TB * TB; idx += TRSM_THREADS) Fs[idx / TB][idx % TB] = D[idx];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) Xs[tr][tc + q] = acc[q];
+    __syncthreads();
+    Tc out[4] = {Tc(0), Tc(0), Tc(0), Tc(0)};
+#pragma unroll 8
+    for (int k = 0; k < TB; ++k) {
+      const Tc d = Fs[tr][k];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) out[q] = out[q] + d * Xs[k][tc + q];
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (tr < rows && tc + q < cols) B[(r0 + tr) * ldb + c0 + tc + q] = (double)out[q];
+    __syncthreads();
+  }
+  if (tid == 0) {
+    __threadfence();
+    st_release(&flags[ib], (int)epoch);
+  }
+}
+
 // ------------------------------------------------------------- residual
 // R = B - A X in FP64.  CTA: RES_ROWS rows, X staged in shared memory by
 // k-chunks; warp w handles rows w, w + 8, ...; lanes split k.
@@ -335,6 +480,38 @@ cudaError_t launch_trsm(const Tf *F, int64_t ldf, double *B, int64_t ldb, int64_
   return cudaGetLastError();
 }
 
+size_t trsm_inv_bytes(int64_t n, size_t esz) {
+  const int64_t nb = (n + TB - 1) / TB;
+  return (size_t)nb * TB * TB * esz;
+}
+
+template <typename Tf>
+cudaError_t launch_diag_inv(const Tf *F, int64_t ldf, int64_t n, int kind, Tf *Dinv,
+                            cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t nb = (n + TB - 1) / TB;
+  diag_inv_kernel<Tf, Tf><<<(unsigned)nb, TB, 0, st>>>(F, ldf, n, kind, Dinv);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <typename Tf>
+cudaError_t launch_trsm_inv(const Tf *F, int64_t ldf, const Tf *Dinv, double *B, int64_t ldb,
+                            int64_t n, int64_t nrhs, int kind, int *sync, unsigned epoch, int *err,
+                            int64_t spin_limit, cudaStream_t st) {
+  if (n <= 0 || nrhs <= 0) return cudaSuccess;
+  const int64_t nb = (n + TB - 1) / TB;
+  if (nb + 1 > SYNC_WORDS) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(sync, 0, sizeof(int), st);  // ticket
+  if (e != cudaSuccess) return e;
+  const long long wait_ns = (long long)spin_limit * 100LL;
+  trsm_inv_kernel<Tf, Tf><<<(unsigned)nb, TRSM_THREADS, 0, st>>>(F, ldf, Dinv, B, ldb, n, nrhs, kind,
+                                                                 sync, sync + 1, epoch, err,
+                                                                 wait_ns);
+  count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_residual(const double *A, int64_t lda, const double *X, int64_t ldx,
                             const double *B, int64_t ldb, double *R, int64_t ldr, int64_t n,
                             int64_t nrhs, double *norms, cudaStream_t st) {
@@ -394,6 +571,16 @@ template cudaError_t launch_trsm<double, double>(const double *, int64_t, double
 template cudaError_t launch_trsm<float, float>(const float *, int64_t, double *, int64_t, int64_t,
                                                int64_t, int, int *, unsigned, int *, int64_t,
                                                cudaStream_t);
+template cudaError_t launch_diag_inv<double>(const double *, int64_t, int64_t, int, double *,
+                                             cudaStream_t);
+template cudaError_t launch_diag_inv<float>(const float *, int64_t, int64_t, int, float *,
+                                            cudaStream_t);
+template cudaError_t launch_trsm_inv<double>(const double *, int64_t, const double *, double *,
+                                             int64_t, int64_t, int64_t, int, int *, unsigned, int *,
+                                             int64_t, cudaStream_t);
+template cudaError_t launch_trsm_inv<float>(const float *, int64_t, const float *, double *, int64_t,
+                                            int64_t, int64_t, int, int *, unsigned, int *, int64_t,
+                                            cudaStream_t);
 template cudaError_t launch_backward_error<double>(int, const double *, int64_t, const double *,
                                                    int64_t, int64_t, double *, cudaStream_t);
 template cudaError_t launch_backward_error<float>(int, const double *, int64_t, const float *,

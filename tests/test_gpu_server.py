@@ -78,9 +78,9 @@ def test_server_admission_respects_slots_and_budget(built):
         assert srv.wait(t).status == 0
     assert srv.stats().max_running <= 2
     srv.close()
-    # a budget that holds one 1000-order job at a time serialises them
-    one = 8 * 1000 * 1000 * 2 + (32 << 20)
-    srv = built.Server(0, one, 4)
+    # a budget that holds one 1000-order FP32 job at a time serialises them
+    # (footprint: FP64 A 8 MB + FP32 factor 4 MB + vectors + 8 MiB slack)
+    srv = built.Server(0, 30_000_000, 4)
     jobs = [_job(1000, 2, 30 + i) for i in range(4)]
     ts = [srv.submit(*j, dtype="f32") for j in jobs]
     for t in ts:

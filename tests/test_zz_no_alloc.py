@@ -4,8 +4,10 @@ Callers running under stream capture, inside a budgeted pool or a plugin
 that must not touch the allocator cannot create a handle (gb_create
 allocates); this entry point keeps its scratch in a static device array.
 The test calls it through the C ABI twice in a row and checks both results
-against the regular gb_chol_solve within the solve tolerance of the suite
-(1e-10 of max |X|).  It lives in a file that pytest collects last and must
+against the regular gb_chol_solve within the solve tolerance of the suite:
+1e-10 of max |X| for FP64 factors, 1e-5 for FP32 factors (the two entry
+points reach X by different, equally valid roundings: substitution here,
+inverted diagonal blocks in the regular solve).  It lives in a file that pytest collects last and must
 pass alone in a fresh process as well as after the other tests.
 """
 import numpy as np
@@ -44,7 +46,8 @@ def test_noalloc_solve_matches_regular_solve_twice(h, dtype, n, nrhs):
         assert st == binding.GB_OK, binding.status_string(st)
         torch.cuda.synchronize()
         got = X.cpu().numpy()
-        assert np.abs(got - ref).max() <= 1e-10 * np.abs(ref).max()
+        tol = 1e-10 if dtype == "f64" else 1e-5
+        assert np.abs(got - ref).max() <= tol * np.abs(ref).max()
 
 
 def test_noalloc_rejects_beyond_maximum_and_host_buffers(h):
