@@ -127,9 +127,13 @@ typedef enum gb_option {
   GB_OPT_PROFILE = 5,       /* 1: record CUDA events around every launch of
                                the factorizations (read with
                                gb_profile_read); default 0.                 */
-  GB_OPT_BATCHED_EXACT = 6  /* 1: the batched kernel rounds every product and
+  GB_OPT_BATCHED_EXACT = 6, /* 1: the batched kernel rounds every product and
                                every subtraction separately (no FMA), as the
                                FP64 oracle does; default 0.                  */
+  GB_OPT_LOOKAHEAD = 7      /* 1 (default): each delayed update first updates
+                               the next s-block's columns, and the rest of it
+                               runs on a second stream while the next block's
+                               column steps proceed; 0: one stream.          */
 } gb_option;
 
 gb_status gb_set_option(gb_handle *h, gb_option opt, int64_t value);

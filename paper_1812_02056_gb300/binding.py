@@ -35,6 +35,7 @@ DTYPES = {"f64": GB_F64, "f32": GB_F32, "mix_bf16": GB_MIX_BF16, "mix_f16": GB_M
 GB_OPT_INNER_STEP, GB_OPT_USE_GRAPHS, GB_OPT_TC_UPDATE, GB_OPT_SPIN_LIMIT = 1, 2, 3, 4
 GB_OPT_PROFILE = 5
 GB_OPT_BATCHED_EXACT = 6
+GB_OPT_LOOKAHEAD = 7
 
 
 class GbError(RuntimeError):

@@ -230,19 +230,89 @@ double update_bytes(int64_t M, int64_t N, int64_t K, bool lower, size_t e) {
 }
 
 // ------------------------------------------------------------ block loops
+// C[i][j] -= sum_k X[i][k] X[j][k] over the lower part of an M x N block
+// (Cholesky's delayed update or part of it), on the tensor cores for the
+// mixed dtypes, on the CUDA cores otherwise.  `pack_slot` names the packed-
+// operand workspace of the stream the call is issued on.
+template <typename T>
+gb_status chol_update(gb_handle *h, gb_dtype dt, T *C, const T *X, const T *Y, int64_t ld,
+                      int64_t M, int64_t N, int64_t K, int *status, int pack_slot,
+                      cudaStream_t st) {
+  if (M <= 0 || N <= 0 || K <= 0) return GB_OK;
+  if constexpr (sizeof(T) == 4) {
+    if (is_mixed(dt) && h->tc_update) {
+      TcUpdateArgs a{};
+      a.C = reinterpret_cast<float *>(C);
+      a.ldc = ld;
+      a.X = reinterpret_cast<const float *>(X);
+      a.ldx = ld;
+      a.Y = reinterpret_cast<const float *>(Y);
+      a.ldy = ld;
+      a.M = M;
+      a.N = N;
+      a.K = K;
+      a.nn = false;
+      a.lower = true;
+      a.diag = 0;
+      a.f16 = (dt == GB_MIX_F16);
+      a.split = split_of(dt);
+      a.status = status;
+      a.err = h->d_err;
+      a.spin_limit = h->spin_limit;
+      gb_status ws = ws_reserve(h, pack_slot, tc_pack_bytes(M, N, K, false, a.split), st);
+      if (ws != GB_OK) return ws;
+      a.pack = h->ws[pack_slot].ptr;
+      a.pack_bytes = h->ws[pack_slot].bytes;
+      GB_CUDA_TRY(launch_update_tc(a, st));
+      return GB_OK;
+    }
+  }
+  GB_CUDA_TRY(launch_update_simt<T>(C, ld, X, ld, Y, ld, M, N, K, false, true, 0, status, st));
+  return GB_OK;
+}
+
+template <typename T, typename Tc>
+gb_status chol_blocked_on(gb_handle *h, int64_t n, int64_t s, T *W, int64_t ld, int *status,
+                          gb_dtype dt, cudaStream_t st, bool la);
+
+// Look-ahead runs the column steps and each next-block update on the
+// high-priority stream and the rest of each update on the low-priority one,
+// forked from and joined back to the caller's stream.
 template <typename T, typename Tc>
 gb_status chol_blocked(gb_handle *h, int64_t n, int64_t s, T *W, int64_t ld, int *status,
                        gb_dtype dt, cudaStream_t st) {
+  const bool la = h->lookahead && h->hi && h->aux && n > s + s;
+  if (!la) return chol_blocked_on<T, Tc>(h, n, s, W, ld, status, dt, st, false);
+  GB_CUDA_TRY(cudaEventRecord(h->ev_fork, st));
+  GB_CUDA_TRY(cudaStreamWaitEvent(h->hi, h->ev_fork, 0));
+  gb_status r = chol_blocked_on<T, Tc>(h, n, s, W, ld, status, dt, h->hi, true);
+  GB_CUDA_TRY(cudaEventRecord(h->ev_join, h->hi));
+  GB_CUDA_TRY(cudaStreamWaitEvent(st, h->ev_join, 0));
+  return r;
+}
+
+template <typename T, typename Tc>
+gb_status chol_blocked_on(gb_handle *h, int64_t n, int64_t s, T *W, int64_t ld, int *status,
+                          gb_dtype dt, cudaStream_t st, bool la) {
   const int64_t b = std::max(1, std::min(64, h->inner_step));
+  const size_t e = sizeof(T);
+  if (la && is_mixed(dt) && h->tc_update) {
+    // both pack workspaces at their largest before anything is in flight
+    const int64_t m0 = n - std::min(s, n);
+    const size_t pb = tc_pack_bytes(m0, m0, std::min(s, n), false, split_of(dt));
+    gb_status r = ws_reserve(h, WS_PANEL, pb, st);
+    if (r == GB_OK) r = ws_reserve(h, WS_PANEL2, pb, h->aux);
+    if (r != GB_OK) return r;
+  }
+  bool rest_pending = false;
   for (int64_t z = 0; z < n; z += s) {
     const int64_t sb = std::min(s, n - z);
     const int64_t pe = z + sb;  // end of this s-block
     for (int64_t j0 = z; j0 < pe; j0 += b) {
       const int bw = (int)std::min(b, pe - j0);
-      const size_t e = sizeof(T);
       const int64_t r0 = j0 + bw;
       {
-        // diagonal block and the rows below it, one fused launch
+        // diagonal block and the rows below it
         PhaseTimer t(h, st, GB_PHASE_PANEL,
                      (double)bw * bw * bw / 3.0 + (double)(n - r0) * bw * bw,
                      (double)bw * bw * e + 2.0 * (double)(n - r0) * bw * e);
@@ -256,53 +326,47 @@ gb_status chol_blocked(gb_handle *h, int64_t n, int64_t s, T *W, int64_t ld, int
       if (r0 < pe) {  // the s-block's remaining columns receive this inner block
         PhaseTimer t(h, st, GB_PHASE_INNER, update_flops(n - r0, pe - r0, bw, true),
                      update_bytes(n - r0, pe - r0, bw, true, e));
-        GB_CUDA_TRY(launch_update_simt<T>(W + r0 * ld + r0, ld, W + r0 * ld + j0, ld,
-                                          W + r0 * ld + j0, ld, n - r0, pe - r0, bw, false, true,
-                                          0, status, st));
+        const T *R = W + r0 * ld + j0;
+        gb_status r = chol_update<T>(h, dt, W + r0 * ld + r0, R, R, ld, n - r0, pe - r0, bw,
+                                     status, WS_PANEL, st);
+        if (r != GB_OK) return r;
       }
     }
-    if (pe < n) {  // delayed rank-sb update of the trailing matrix
-      const int64_t m = n - pe;
-      T *C = W + pe * ld + pe;
-      const T *R = W + pe * ld + z;
-      bool done = false;
-      const bool tc = is_mixed(dt) && h->tc_update;
+    if (pe >= n) break;
+    // delayed rank-sb update A[pe.., pe..] -= R R^T, R = L[pe.., z..pe)
+    const int64_t m = n - pe;
+    const T *R = W + pe * ld + z;
+    if (!la) {
       PhaseTimer t(h, st, GB_PHASE_UPDATE, update_flops(m, m, sb, true),
-                   update_bytes(m, m, sb, true, sizeof(T)) -
-                       (tc ? (double)m * sb * 2.0 * (sizeof(T) - 2) : 0.0));
-      if constexpr (sizeof(T) == 4) {
-        if (is_mixed(dt) && h->tc_update) {
-          TcUpdateArgs a{};
-          a.C = reinterpret_cast<float *>(C);
-          a.ldc = ld;
-          a.X = reinterpret_cast<const float *>(R);
-          a.ldx = ld;
-          a.Y = reinterpret_cast<const float *>(R);
-          a.ldy = ld;
-          a.M = m;
-          a.N = m;
-          a.K = sb;
-          a.nn = false;
-          a.lower = true;
-          a.diag = 0;
-          a.f16 = (dt == GB_MIX_F16);
-          a.split = split_of(dt);
-          a.status = status;
-          a.err = h->d_err;
-          a.spin_limit = h->spin_limit;
-          const size_t pb = tc_pack_bytes(m, m, sb, false, split_of(dt));
-          gb_status ws = ws_reserve(h, WS_PANEL, pb, st);
-          if (ws != GB_OK) return ws;
-          a.pack = h->ws[WS_PANEL].ptr;
-          a.pack_bytes = h->ws[WS_PANEL].bytes;
-          GB_CUDA_TRY(launch_update_tc(a, st));
-          done = true;
-        }
-      }
-      if (!done)
-        GB_CUDA_TRY(launch_update_simt<T>(C, ld, R, ld, R, ld, m, m, sb, false, true, 0, status, st));
+                   update_bytes(m, m, sb, true, e));
+      gb_status r = chol_update<T>(h, dt, W + pe * ld + pe, R, R, ld, m, m, sb, status, WS_PANEL, st);
+      if (r != GB_OK) return r;
+      continue;
+    }
+    const int64_t nb = std::min(s, n - pe);  // width of the next s-block
+    // the previous rest-update wrote the next block's columns: wait for it
+    if (rest_pending) GB_CUDA_TRY(cudaStreamWaitEvent(st, h->ev_rest, 0));
+    {
+      PhaseTimer t(h, st, GB_PHASE_UPDATE, update_flops(m, nb, sb, true),
+                   update_bytes(m, nb, sb, true, e));
+      gb_status r = chol_update<T>(h, dt, W + pe * ld + pe, R, R, ld, m, nb, sb, status, WS_PANEL, st);
+      if (r != GB_OK) return r;
+    }
+    const int64_t q = pe + nb;  // the rest: rows and columns from q on
+    if (q < n) {
+      GB_CUDA_TRY(cudaEventRecord(h->ev_next, st));
+      GB_CUDA_TRY(cudaStreamWaitEvent(h->aux, h->ev_next, 0));
+      const T *Rq = W + q * ld + z;
+      PhaseTimer t(h, h->aux, GB_PHASE_UPDATE, update_flops(n - q, n - q, sb, true),
+                   update_bytes(n - q, n - q, sb, true, e));
+      gb_status r = chol_update<T>(h, dt, W + q * ld + q, Rq, Rq, ld, n - q, n - q, sb, status,
+                                   WS_PANEL2, h->aux);
+      if (r != GB_OK) return r;
+      GB_CUDA_TRY(cudaEventRecord(h->ev_rest, h->aux));
+      rest_pending = true;
     }
   }
+  if (rest_pending) GB_CUDA_TRY(cudaStreamWaitEvent(st, h->ev_rest, 0));
   return GB_OK;
 }
 
@@ -695,6 +759,15 @@ gb_status gb_create(gb_handle **out, int device) {
          cudaMemset(h->d_sync, 0, sizeof(int) * SYNC_WORDS) == cudaSuccess &&
          cudaMemset(h->d_arrivals, 0, sizeof(unsigned long long)) == cudaSuccess &&
          cudaDeviceSynchronize() == cudaSuccess;
+  int prio_lo = 0, prio_hi = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+  if (ok)
+    ok = cudaStreamCreateWithPriority(&h->hi, cudaStreamNonBlocking, prio_hi) == cudaSuccess &&
+         cudaStreamCreateWithPriority(&h->aux, cudaStreamNonBlocking, prio_lo) == cudaSuccess &&
+         cudaEventCreateWithFlags(&h->ev_next, cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&h->ev_rest, cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     gb_destroy(h);
@@ -720,6 +793,12 @@ gb_status gb_destroy(gb_handle *h) {
   if (h->d_sync) cudaFree(h->d_sync);
   if (h->d_scalars) cudaFree(h->d_scalars);
   if (h->d_arrivals) cudaFree(h->d_arrivals);
+  if (h->ev_next) cudaEventDestroy(h->ev_next);
+  if (h->ev_rest) cudaEventDestroy(h->ev_rest);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->hi) cudaStreamDestroy(h->hi);
+  if (h->aux) cudaStreamDestroy(h->aux);
   delete h;
   return GB_OK;
 }
@@ -739,6 +818,7 @@ gb_status gb_set_option(gb_handle *h, gb_option opt, int64_t v) {
       return GB_OK;
     case GB_OPT_PROFILE: h->profile = v ? 1 : 0; return GB_OK;
     case GB_OPT_BATCHED_EXACT: h->batched_exact = v ? 1 : 0; return GB_OK;
+    case GB_OPT_LOOKAHEAD: h->lookahead = v ? 1 : 0; return GB_OK;
     default: return -2;
   }
 }
@@ -753,6 +833,7 @@ gb_status gb_get_option(gb_handle *h, gb_option opt, int64_t *v) {
     case GB_OPT_SPIN_LIMIT: *v = h->spin_limit; return GB_OK;
     case GB_OPT_PROFILE: *v = h->profile; return GB_OK;
     case GB_OPT_BATCHED_EXACT: *v = h->batched_exact; return GB_OK;
+    case GB_OPT_LOOKAHEAD: *v = h->lookahead; return GB_OK;
     default: return -2;
   }
 }

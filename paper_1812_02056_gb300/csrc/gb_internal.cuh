@@ -61,10 +61,16 @@ struct gb_handle {
   unsigned long long *d_arrivals = nullptr;  // arrival counter of the fused panel kernel
   double *d_scalars = nullptr;  // small FP64 reduction outputs
   unsigned sync_epoch = 0;
-  gb::Workspace ws[5];       // named workspaces, see WS_* below
+  gb::Workspace ws[6];       // named workspaces, see WS_* below
   std::mutex mu;
   // GB_OPT_PROFILE: event pairs recorded around launches, read later
   int profile = 0;
+  int lookahead = 1;                  // GB_OPT_LOOKAHEAD
+  cudaStream_t hi = nullptr;          // high priority: column steps and next-block updates
+  cudaStream_t aux = nullptr;         // low priority: the rest of each update
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_next = nullptr;      // next block's columns updated (main stream)
+  cudaEvent_t ev_rest = nullptr;      // rest of the update done (aux stream)
   struct ProfRec {
     int phase;
     cudaEvent_t start, stop;
@@ -89,7 +95,7 @@ struct gb_handle {
 
 namespace gb {
 
-enum { WS_STAGE = 0, WS_PANEL = 1, WS_SOLVE = 2, WS_MISC = 3, WS_DINV = 4 };
+enum { WS_STAGE = 0, WS_PANEL = 1, WS_SOLVE = 2, WS_MISC = 3, WS_DINV = 4, WS_PANEL2 = 5 };
 constexpr int SYNC_WORDS = 1 << 16;
 
 // Make sure workspace `slot` holds >= bytes; waits for `stream` before

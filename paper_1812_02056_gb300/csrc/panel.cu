@@ -130,16 +130,25 @@ __global__ void __launch_bounds__(ROWS_PER_CTA)
 
 // ------------------------------------------------ fused column-step kernel
 // One launch per inner block: every CTA factors the bw x bw diagonal block
-// itself (64 threads, thread i owns row i in registers) and then solves its
-// 128 rows below the block against it.  The factored diagonal block is
-// written back by the last CTA to have loaded it: each CTA bumps an arrival
-// counter after loading; the CTA that arrives as number grid - 1 knows every
-// other CTA already holds its own copy, writes the block, and resets the
-// counter to zero for the next launch (ordered after this one on the
-// stream).  No CTA waits.
-// FP64_PIVOT: square root and pivot division in FP64 on FP32 data (the
-// mixed dtypes); the rank-1 steps stay in the storage type.
-constexpr int PANEL_ROWS = 128;
+// itself and then solves its rows below the block against it.  Work is cut
+// into 16-column chunks: the products of the columns already finished are
+// subtracted by short runtime loops (small loop bodies, reused across
+// iterations), then the chunk's own columns are finished one at a time.
+// Every entry still receives its products in ascending k, one at a time.
+// The factored block is written back by the last CTA to have loaded it:
+// each CTA bumps an arrival counter after loading; the CTA that arrives as
+// number grid - 1 knows every other CTA already holds its own copy, writes
+// the block, and resets the counter to zero for the next launch (ordered
+// after this one on the stream).  No CTA waits.
+// Inside the diagonal block the column below L_cc is scaled by 1 / L_cc
+// (one reciprocal per column, as LAPACK's unblocked Cholesky does); the rows
+// below the block divide by L_cc as the paper writes.
+// FP64_PIVOT: square root and reciprocal in FP64 on FP32 data (the mixed
+// dtypes).  MODE: PANEL_FUSED, PANEL_DIAG (one CTA: factor and write the
+// block), PANEL_ROWS_ONLY (read the finished block, then the rows).
+enum { PANEL_FUSED = 0, PANEL_DIAG = 1, PANEL_ROWS_ONLY = 2 };
+constexpr int PB = 64;   // inner block width bound
+constexpr int CH = 16;   // chunk width
 
 template <typename T, bool FP64_PIVOT>
 __device__ __forceinline__ T pivot_sqrt(T d) {
@@ -152,99 +161,160 @@ __device__ __forceinline__ T pivot_div(T a, T b) {
   return a / b;
 }
 
-template <typename T, bool FP64_PIVOT>
-__global__ void __launch_bounds__(PANEL_ROWS)
+template <typename T>
+struct PanelSmem {
+  static constexpr int PADT = PB + 16 / (int)sizeof(T);  // 16-byte aligned rows
+  static constexpr size_t bytes(int rows) {
+    return sizeof(T) * ((size_t)PB * (PB + 1) + (size_t)PB * PADT + (size_t)PB * rows);
+  }
+};
+
+template <typename T, bool FP64_PIVOT, int MODE, int ROWS>
+__global__ void __launch_bounds__(ROWS)
     chol_panel_kernel(T *__restrict__ W, int64_t ld, int64_t j0, int bw, int64_t row0,
                       int64_t nrows, int *status, unsigned long long *arrivals) {
-  constexpr int B = 64;
-  constexpr int PAD = B + 16 / (int)sizeof(T);  // 16-byte aligned rows
-  __shared__ __align__(16) T LT[B][PAD];         // LT[c][j] = L_jc (column c of the block)
-  __shared__ T colc[2][B];
-  __shared__ int s_ok[2];
-  __shared__ int s_last;
+  constexpr int PADT = PanelSmem<T>::PADT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T(*Ld)[PB + 1] = reinterpret_cast<T(*)[PB + 1]>(smem_raw);  // Ld[i][k] = L_ik, k <= i
+  T(*LdT)[PADT] = reinterpret_cast<T(*)[PADT]>(smem_raw + sizeof(T) * PB * (PB + 1));  // LdT[k][i] = L_ik
+  T(*Ys)[ROWS] = reinterpret_cast<T(*)[ROWS]>(smem_raw + sizeof(T) * (PB * (PB + 1) + PB * PADT));
+  __shared__ T s_piv;
+  __shared__ int s_ok, s_last;
   if (load_status(status) != 0) return;
   const int tid = threadIdx.x;
   T *D = W + j0 * ld + j0;
 
-  // ---- diagonal block: thread i < bw owns row i (entries j <= i)
-  T x[B];
+  // all loads of the block in flight at once: registers first, then shared memory
+  constexpr int PER = PB * PB / ROWS;
+  T blk[PER];
 #pragma unroll
-  for (int j = 0; j < B; ++j) x[j] = (tid < bw && j <= tid) ? D[(int64_t)tid * ld + j] : T(0);
-  __syncthreads();
-  if (tid == 0) {
-    __threadfence();
-    const unsigned long long a = atomicAdd(arrivals, 1ULL);
-    s_last = (a == (unsigned long long)gridDim.x - 1) ? 1 : 0;
-    if (s_last) atomicExch(arrivals, 0ULL);  // every CTA has arrived
+  for (int u = 0; u < PER; ++u) {
+    const int idx = tid + u * ROWS, i = idx / PB, k = idx % PB;
+    blk[u] = (i < bw && k <= i) ? D[(int64_t)i * ld + k] : T(0);
   }
-  bool ok = true;
-  int bad_col = 0;
+  if (MODE == PANEL_ROWS_ONLY) {
 #pragma unroll
-  for (int c = 0; c < B; ++c) {
-    if (c < bw && ok) {
-      const int b = c & 1;
-      if (tid == c) {
-        const T d = x[c];
-        s_ok[b] = (d > T(0)) ? 1 : 0;  // not positive, or NaN: breakdown
-        colc[b][c] = pivot_sqrt<T, FP64_PIVOT>(d);
+    for (int u = 0; u < PER; ++u) {
+      const int idx = tid + u * ROWS, i = idx / PB, k = idx % PB;
+      LdT[k][i] = blk[u];
+    }
+    __syncthreads();
+  } else {
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int idx = tid + u * ROWS, i = idx / PB, k = idx % PB;
+      Ld[i][k] = blk[u];
+      LdT[k][i] = T(0);
+    }
+    __syncthreads();
+    if (MODE == PANEL_DIAG) {
+      if (tid == 0) s_last = 1;
+    } else if (tid == 0) {
+      __threadfence();
+      const unsigned long long a = atomicAdd(arrivals, 1ULL);
+      s_last = (a == (unsigned long long)gridDim.x - 1) ? 1 : 0;
+      if (s_last) atomicExch(arrivals, 0ULL);  // every CTA has arrived
+    }
+    // thread i < bw works on row i of the block; the chunk's 16 columns of
+    // that row stay in registers while the chunk is finished
+    for (int c0 = 0; c0 < bw; c0 += CH) {
+      const int cw = min(CH, bw - c0);
+      const bool mine = tid >= c0 && tid < bw;
+      T v[CH];
+#pragma unroll
+      for (int j = 0; j < CH; ++j) v[j] = (mine && j < cw && c0 + j <= tid) ? Ld[tid][c0 + j] : T(0);
+      if (mine) {  // products of the finished columns k < c0
+        for (int k = 0; k < c0; ++k) {
+          const T lik = Ld[tid][k];
+#pragma unroll
+          for (int j = 0; j < CH; ++j) v[j] = v[j] - lik * LdT[k][c0 + j];
+        }
+      }
+#pragma unroll
+      for (int cc = 0; cc < CH; ++cc) {  // the chunk's columns, one at a time
+        if (cc < cw) {
+          const int c = c0 + cc;
+          if (tid == c) {
+            const T d = v[cc];
+            s_ok = (d > T(0)) ? 1 : 0;  // not positive, or NaN: breakdown
+            const T piv = pivot_sqrt<T, FP64_PIVOT>(d);
+            s_piv = pivot_div<T, FP64_PIVOT>(T(1), piv);  // the column is scaled by 1 / L_cc
+            v[cc] = piv;
+            LdT[c][c] = piv;
+          }
+          __syncthreads();
+          if (!s_ok) {  // uniform
+            if (blockIdx.x == 0 && tid == 0) atomicCAS(status, 0, (int)(j0 + c + 1));
+            return;
+          }
+          if (tid > c && tid < bw) {
+            v[cc] = v[cc] * s_piv;
+            LdT[c][tid] = v[cc];
+          }
+          __syncthreads();
+          if (tid > c && tid < bw) {
+            const T lic = v[cc];
+#pragma unroll
+            for (int cc2 = cc + 1; cc2 < CH; ++cc2)
+              if (c0 + cc2 <= tid) v[cc2] = v[cc2] - lic * LdT[c][c0 + cc2];
+          }
+        }
+      }
+      if (mine) {
+#pragma unroll
+        for (int j = 0; j < CH; ++j)
+          if (j < cw && c0 + j <= tid) Ld[tid][c0 + j] = v[j];
       }
       __syncthreads();
-      if (!s_ok[b]) {
-        ok = false;
-        bad_col = c;
-      } else {
-        const T lcc = colc[b][c];
-        if (tid == c) x[c] = lcc;
-        if (tid > c && tid < bw) {
-          x[c] = pivot_div<T, FP64_PIVOT>(x[c], lcc);
-          colc[b][tid] = x[c];
-        }
-        __syncthreads();
-        if (tid > c && tid < bw) {
-          const T xc = x[c];
-#pragma unroll
-          for (int j = c + 1; j < B; ++j)
-            if (j <= tid) x[j] = x[j] - xc * colc[b][j];
-        }
+    }
+    if (s_last) {
+      for (int idx = tid; idx < PB * PB; idx += ROWS) {
+        const int i = idx / PB, k = idx % PB;
+        if (i < bw && k <= i) D[(int64_t)i * ld + k] = Ld[i][k];
       }
     }
-  }
-  if (!ok) {
-    if (blockIdx.x == 0 && tid == 0) atomicCAS(status, 0, (int)(j0 + bad_col + 1));
-    return;  // ok is uniform over the CTA
-  }
-  if (tid < B) {
-#pragma unroll
-    for (int j = 0; j < B; ++j) LT[j][tid] = (j <= tid && tid < bw) ? x[j] : T(0);
-  }
-  __syncthreads();
-  if (s_last && tid < bw) {
-#pragma unroll
-    for (int j = 0; j < B; ++j)
-      if (j <= tid) D[(int64_t)tid * ld + j] = x[j];
+    if (MODE == PANEL_DIAG) return;
   }
 
-  // ---- rows below the block: thread t owns row rbase + t
-  const int64_t r = row0 + (int64_t)blockIdx.x * PANEL_ROWS + tid;
+  // ---- rows below the block: thread t owns row row0 + blockIdx.x * ROWS + t
+  const int64_t r = row0 + (int64_t)blockIdx.x * ROWS + tid;
   if (r >= row0 + nrows) return;
   T *row = W + r * ld + j0;
-  T y[B];
+  // the row's entries, all loads in flight at once, parked in its column of Ys
 #pragma unroll
-  for (int c = 0; c < B; ++c) y[c] = (c < bw) ? row[c] : T(0);
-  // y_c = (a_c - sum_{k<c} y_k L_ck) / L_cc, each product subtracted as soon
-  // as y_k is final, so every entry still receives them in ascending k
+  for (int u = 0; u < PB; u += 16) {
+    T tmp[16];
 #pragma unroll
-  for (int c = 0; c < B; ++c) {
-    if (c < bw) {
-      const T yc = y[c] / LT[c][c];
-      y[c] = yc;
+    for (int q = 0; q < 16; ++q) tmp[q] = (u + q < bw) ? row[u + q] : T(0);
 #pragma unroll
-      for (int c2 = c + 1; c2 < B; ++c2) y[c2] = y[c2] - yc * LT[c][c2];
-    }
+    for (int q = 0; q < 16; ++q) Ys[u + q][tid] = tmp[q];
   }
+  for (int c0 = 0; c0 < bw; c0 += CH) {
+    const int cw = min(CH, bw - c0);
+    T y[CH];
 #pragma unroll
-  for (int c = 0; c < B; ++c)
-    if (c < bw) row[c] = y[c];
+    for (int j = 0; j < CH; ++j) y[j] = Ys[c0 + j][tid];
+    for (int k = 0; k < c0; ++k) {  // products of the finished columns
+      const T yk = Ys[k][tid];
+#pragma unroll
+      for (int j = 0; j < CH; ++j) y[j] = y[j] - yk * LdT[k][c0 + j];
+    }
+#pragma unroll
+    for (int j = 0; j < CH; ++j) {  // the chunk's columns, one at a time
+      if (j < cw) {
+        const T yj = y[j] / LdT[c0 + j][c0 + j];
+        y[j] = yj;
+#pragma unroll
+        for (int j2 = j + 1; j2 < CH; ++j2) y[j2] = y[j2] - yj * LdT[c0 + j][c0 + j2];
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < CH; ++j)
+      if (j < cw) {
+        Ys[c0 + j][tid] = y[j];
+        row[c0 + j] = y[j];
+      }
+  }
 }
 
 // ---------------------------------------------------------------------- LU
@@ -433,15 +503,33 @@ cudaError_t launch_chol_rows(T *W, int64_t ld, int64_t row0, int64_t nrows, int6
   return chol_rows_b<T, 64>(W, ld, row0, nrows, j0, bw, status, st);
 }
 
+template <typename T, bool FP64_PIVOT, int MODE, int ROWS>
+cudaError_t panel_launch(unsigned grid, T *W, int64_t ld, int64_t j0, int bw, int64_t nrows,
+                         int *status, unsigned long long *arrivals, cudaStream_t st) {
+  constexpr size_t smem = PanelSmem<T>::bytes(ROWS);
+  static cudaError_t attr = allow_smem(chol_panel_kernel<T, FP64_PIVOT, MODE, ROWS>, smem);
+  if (attr != cudaSuccess) return attr;
+  chol_panel_kernel<T, FP64_PIVOT, MODE, ROWS><<<grid, ROWS, smem, st>>>(W, ld, j0, bw, j0 + bw,
+                                                                       nrows, status, arrivals);
+  count_launch();
+  return cudaGetLastError();
+}
+
 template <typename T, bool FP64_PIVOT>
 cudaError_t launch_chol_panel(T *W, int64_t ld, int64_t j0, int bw, int64_t nrows, int *status,
                               unsigned long long *arrivals, cudaStream_t st) {
-  if (bw < 1 || bw > 64) return cudaErrorInvalidValue;
-  const int64_t grid = std::max<int64_t>(1, (nrows + PANEL_ROWS - 1) / PANEL_ROWS);
-  chol_panel_kernel<T, FP64_PIVOT><<<(unsigned)grid, PANEL_ROWS, 0, st>>>(
-      W, ld, j0, bw, j0 + bw, nrows, status, arrivals);
-  count_launch();
-  return cudaGetLastError();
+  if (bw < 1 || bw > PB) return cudaErrorInvalidValue;
+  if (sizeof(T) == 8) {
+    // FP64: the block's DFMA work once (one CTA), then the rows over every SM
+    cudaError_t e = panel_launch<T, FP64_PIVOT, PANEL_DIAG, 64>(1, W, ld, j0, bw, 0, status,
+                                                                 arrivals, st);
+    if (e != cudaSuccess || nrows <= 0) return e;
+    return panel_launch<T, FP64_PIVOT, PANEL_ROWS_ONLY, 64>((unsigned)((nrows + 63) / 64), W, ld,
+                                                             j0, bw, nrows, status, arrivals, st);
+  }
+  const int64_t grid = std::max<int64_t>(1, (nrows + 127) / 128);
+  return panel_launch<T, FP64_PIVOT, PANEL_FUSED, 128>((unsigned)grid, W, ld, j0, bw, nrows,
+                                                        status, arrivals, st);
 }
 
 template <typename T, typename Tc>
