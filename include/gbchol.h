@@ -403,10 +403,11 @@ gb_status gb_backward_error(gb_handle *h, int is_lu, int64_t n, gb_dtype factor_
  * gb_chol_factor_batched -- Algorithm 1 applied independently to `count`
  * matrices of possibly different orders, in ONE persistent launch: CTAs
  * take matrices longest first (LPT on n^3) from a device ticket.  A matrix
- * whose packed lower triangle fits in shared memory (FP64 n <= 225, FP32
- * n <= 319) runs all of Algorithm 1 in shared memory; a larger one is first
- * copied to L, keeps its s-wide panel in shared memory and receives the
- * delayed update in place in L.
+ * whose packed lower triangle fits in shared memory (S = 14080 FP64 or
+ * 28160 FP32 elements per CTA: FP64 n <= 167, FP32 n <= 236) runs all of
+ * Algorithm 1 in shared memory; a larger one is first copied to L, keeps its
+ * panel in shared memory -- so its step is min(s, floor(S / n)) -- and
+ * receives the delayed update in place in L.
  *
  *  n[count]    orders (host array), 0 <= n[i] <= 1024.
  *  A[count]    device pointers (host array of pointers) to the inputs; only

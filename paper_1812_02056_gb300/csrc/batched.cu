@@ -16,6 +16,8 @@
 // result is the same bits as the oracle's literal mode.
 #include <math.h>
 
+#include <algorithm>
+
 #include "gb_internal.cuh"
 
 namespace gb {
@@ -66,34 +68,26 @@ __device__ __forceinline__ float ddiv<float>(float a, float b) {
 
 __device__ __forceinline__ int64_t tri(int64_t i) { return i * (i + 1) / 2; }
 
-// (r, q) with e = r (r + 1) / 2 + q, 0 <= q <= r
-__device__ __forceinline__ void tri_decode(int64_t e, int &r, int &q) {
-  int x = (int)((sqrt(8.0 * (double)e + 1.0) - 1.0) * 0.5);
-  while (tri(x) > e) --x;
-  while (tri(x + 1) <= e) ++x;
-  r = x;
-  q = (int)(e - tri(x));
-}
-
 // ------------------------------------------------- whole matrix in shared memory
 // S holds the packed lower triangle: (i, j), j <= i, at i (i + 1) / 2 + j.
-template <typename T>
-__device__ int chol_in_smem(T *S, int n, int s, bool exact, T *red) {
+template <typename T, bool EXACT>
+__device__ int chol_in_smem(T *S, int n, int s, T *red) {
+  constexpr bool exact = EXACT;
   const int tid = threadIdx.x;
   int z = 0;
   for (int c = 0; c < n; ++c) {
     if (c == z + s) {
       // delayed update: A[i][j] -= S_ij, S_ij = sum_{k=z}^{c-1} L_ik L_jk, c <= j <= i
-      const int m = n - c;
-      const int64_t cnt = tri(m);
-      for (int64_t e = tid; e < cnt; e += BT) {
-        int r, q;
-        tri_decode(e, r, q);
-        const int i = c + r, j = c + q;
-        const T *Li = S + tri(i), *Lj = S + tri(j);
-        T sij = T(0);
-        for (int k = z; k < c; ++k) sij = madd(sij, Li[k], Lj[k], exact);
-        S[tri(i) + j] = S[tri(i) + j] - sij;  // a lone subtraction is never contracted
+      // warp w takes rows c + w, c + w + 8, ...; its lanes take the columns
+      for (int i = c + (tid >> 5); i < n; i += BT / 32) {
+        const T *Li = S + tri(i);
+        for (int j = c + (tid & 31); j <= i; j += 32) {
+          const T *Lj = S + tri(j);
+          T sij = T(0);
+  #pragma unroll 4
+          for (int k = z; k < c; ++k) sij = madd(sij, Li[k], Lj[k], exact);
+          S[tri(i) + j] = S[tri(i) + j] - sij;  // a lone subtraction is never contracted
+        }
       }
       z = c;
       __syncthreads();
@@ -103,6 +97,7 @@ __device__ int chol_in_smem(T *S, int n, int s, bool exact, T *red) {
     for (int i = c + tid; i < n; i += BT) {
       const T *Li = S + tri(i);
       T v = Li[c];
+#pragma unroll 4
       for (int k = z; k < c; ++k) v = msub(v, Li[k], Lc[k], exact);
       if (i == c) red[0] = v; else S[tri(i) + c] = v;
     }
@@ -120,22 +115,22 @@ __device__ int chol_in_smem(T *S, int n, int s, bool exact, T *red) {
 // ------------------------------------------------- panel in shared memory
 // P: rows [z, n) x columns [z, z + sb) of the working matrix, row-major with
 // leading dimension s (the panel width bound).
-template <typename T>
-__device__ int chol_panel_path(T *A, int64_t lda, int n, int s, bool exact, T *P, T *red) {
+template <typename T, bool EXACT>
+__device__ int chol_panel_path(T *A, int64_t lda, int n, int s, T *P, T *red) {
+  constexpr bool exact = EXACT;
   const int tid = threadIdx.x;
   for (int z = 0; z < n; z += s) {
     const int sb = min(s, n - z);
     const int rows = n - z;
-    for (int64_t e = tid; e < (int64_t)rows * sb; e += BT) {
-      const int r = (int)(e / sb), q = (int)(e % sb);
-      P[(int64_t)r * s + q] = A[(int64_t)(z + r) * lda + z + q];
-    }
+    for (int r = tid >> 5; r < rows; r += BT / 32)
+      for (int q = tid & 31; q < sb; q += 32) P[(int64_t)r * s + q] = A[(int64_t)(z + r) * lda + z + q];
     __syncthreads();
     for (int c = 0; c < sb; ++c) {  // column z + c, local index c
       const T *Pc = P + (int64_t)c * s;
       for (int r = c + tid; r < rows; r += BT) {
         T *Pr = P + (int64_t)r * s;
         T v = Pr[c];
+#pragma unroll 4
         for (int k = 0; k < c; ++k) v = msub(v, Pr[k], Pc[k], exact);
         if (r == c) red[0] = v; else Pr[c] = v;
       }
@@ -147,21 +142,21 @@ __device__ int chol_panel_path(T *A, int64_t lda, int n, int s, bool exact, T *P
       if (tid == 0) P[(int64_t)c * s + c] = lcc;
       __syncthreads();
     }
-    for (int64_t e = tid; e < (int64_t)rows * sb; e += BT) {
-      const int r = (int)(e / sb), q = (int)(e % sb);
-      if (q <= r) A[(int64_t)(z + r) * lda + z + q] = P[(int64_t)r * s + q];
-    }
+    for (int r = tid >> 5; r < rows; r += BT / 32)
+      for (int q = tid & 31; q < sb; q += 32)
+        if (q <= r) A[(int64_t)(z + r) * lda + z + q] = P[(int64_t)r * s + q];
     // delayed update of the trailing lower triangle: rows/cols [z+sb, n)
     const int m = n - z - sb;
-    const int64_t cnt = tri(m);
-    for (int64_t e = tid; e < cnt; e += BT) {
-      int r, q;
-      tri_decode(e, r, q);
-      const T *Pi = P + (int64_t)(sb + r) * s, *Pj = P + (int64_t)(sb + q) * s;
-      T sij = T(0);
-      for (int k = 0; k < sb; ++k) sij = madd(sij, Pi[k], Pj[k], exact);
-      T *a = A + (int64_t)(z + sb + r) * lda + z + sb + q;
-      *a = *a - sij;
+    for (int r = tid >> 5; r < m; r += BT / 32) {
+      const T *Pi = P + (int64_t)(sb + r) * s;
+      for (int q = tid & 31; q <= r; q += 32) {
+        const T *Pj = P + (int64_t)(sb + q) * s;
+        T sij = T(0);
+#pragma unroll 4
+        for (int k = 0; k < sb; ++k) sij = madd(sij, Pi[k], Pj[k], exact);
+        T *a = A + (int64_t)(z + sb + r) * lda + z + sb + q;
+        *a = *a - sij;
+      }
     }
     __syncthreads();  // global writes of this CTA are visible to it after the barrier
   }
@@ -181,8 +176,8 @@ struct Plan {
   int *ticket;
 };
 
-template <typename T>
-__global__ void __launch_bounds__(BT) batched_chol_kernel(Plan plan, int64_t smem_elems, int exact) {
+template <typename T, bool EXACT>
+__global__ void __launch_bounds__(BT, 2) batched_chol_kernel(Plan plan, int64_t smem_elems) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *buf = reinterpret_cast<T *>(smem_raw);
   __shared__ T red[1];
@@ -204,27 +199,22 @@ __global__ void __launch_bounds__(BT) batched_chol_kernel(Plan plan, int64_t sme
     int info = 0;
     if (n > 0) {
       if (tri(n) <= smem_elems) {
-        for (int64_t e = threadIdx.x; e < tri(n); e += BT) {
-          int r, q;
-          tri_decode(e, r, q);
-          buf[e] = A[(int64_t)r * lda + q];
-        }
+        for (int r = threadIdx.x >> 5; r < n; r += BT / 32)
+          for (int q = threadIdx.x & 31; q <= r; q += 32) buf[tri(r) + q] = A[(int64_t)r * lda + q];
         __syncthreads();
-        info = chol_in_smem<T>(buf, n, min(s, n), exact != 0, red);
+        info = chol_in_smem<T, EXACT>(buf, n, min(s, n), red);
         __syncthreads();
-        for (int64_t e = threadIdx.x; e < (int64_t)n * n; e += BT) {
-          const int r = (int)(e / n), q = (int)(e % n);
-          L[(int64_t)r * ldl + q] = q <= r ? buf[tri(r) + q] : T(0);
-        }
+        for (int r = threadIdx.x >> 5; r < n; r += BT / 32)
+          for (int q = threadIdx.x & 31; q < n; q += 32)
+            L[(int64_t)r * ldl + q] = q <= r ? buf[tri(r) + q] : T(0);
       } else {
         // the panel path works in place in L: copy A's lower triangle first
-        for (int64_t e = threadIdx.x; e < (int64_t)n * n; e += BT) {
-          const int r = (int)(e / n), q = (int)(e % n);
-          L[(int64_t)r * ldl + q] = q <= r ? A[(int64_t)r * lda + q] : T(0);
-        }
+        for (int r = threadIdx.x >> 5; r < n; r += BT / 32)
+          for (int q = threadIdx.x & 31; q < n; q += 32)
+            L[(int64_t)r * ldl + q] = q <= r ? A[(int64_t)r * lda + q] : T(0);
         __syncthreads();
         const int sp = (int)min64(s, smem_elems / n);  // panel width that fits
-        info = chol_panel_path<T>(L, ldl, n, max(1, sp), exact != 0, buf, red);
+        info = chol_panel_path<T, EXACT>(L, ldl, n, max(1, sp), buf, red);
         __syncthreads();
       }
     }
@@ -255,7 +245,7 @@ cudaError_t launch_fill_spd(T *base, int64_t stride, int count, int n, cudaStrea
 template cudaError_t launch_fill_spd<double>(double *, int64_t, int, int, cudaStream_t);
 template cudaError_t launch_fill_spd<float>(float *, int64_t, int, int, cudaStream_t);
 
-size_t batched_smem_bytes() { return 200 * 1024; }
+size_t batched_smem_bytes() { return 110 * 1024; }  // two CTAs per SM
 
 template <typename T>
 cudaError_t launch_chol_batched_plan(int count, const int *order, const int *n, const int *step,
@@ -264,14 +254,20 @@ cudaError_t launch_chol_batched_plan(int count, const int *order, const int *n, 
                                      int exact, cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
   const size_t smem = batched_smem_bytes();
-  static cudaError_t attr = cudaFuncSetAttribute(
-      batched_chol_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (attr != cudaSuccess) return attr;
+  static cudaError_t attr0 = cudaFuncSetAttribute(
+      batched_chol_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  static cudaError_t attr1 = cudaFuncSetAttribute(
+      batched_chol_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (attr0 != cudaSuccess) return attr0;
+  if (attr1 != cudaSuccess) return attr1;
   cudaError_t e = cudaMemsetAsync(ticket, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
   Plan p{count, order, n, step, A, lda, L, ldl, info, ticket};
-  const int grid = count < sm_count ? count : sm_count;
-  batched_chol_kernel<T><<<grid, BT, smem, st>>>(p, (int64_t)(smem / sizeof(T)), exact);
+  const int grid = std::min(count, 2 * sm_count);
+  if (exact)
+    batched_chol_kernel<T, true><<<grid, BT, smem, st>>>(p, (int64_t)(smem / sizeof(T)));
+  else
+    batched_chol_kernel<T, false><<<grid, BT, smem, st>>>(p, (int64_t)(smem / sizeof(T)));
   count_launch();
   return cudaGetLastError();
 }
