@@ -36,6 +36,22 @@ METRIC = "Cholesky GFLOP/s (n^3/3 flops per factorization)"
 UNIT = "GFLOP/s"
 
 
+def dist_max(x: float, dist=None, device="cpu") -> float:
+    """Max of x over the ranks of the process group (x itself without one)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world: int, steps: int, flops_per_step: float, ms_total: float) -> float:
+    """Whole-job GFLOP/s: every rank did `steps` steps; the slowest rank's
+    time bounds the job (weak scaling, replicas)."""
+    return world * steps * flops_per_step / (ms_total * 1e-3) / 1e9
+
+
 def chol_flops(n: int) -> float:
     return n ** 3 / 3.0
 
@@ -240,14 +256,10 @@ def run_ours(args):
     clk = clocks.stop()
     prof = h.profile_read().as_dict()
     h.set_option(binding.GB_OPT_PROFILE, 0)
-    ms_total = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = dist_max(e0.elapsed_time(e1), dist, dev)
     ms_step = ms_total / args.steps
     flops = chol_flops(n)
-    value = world * args.steps * flops / (ms_total * 1e-3) / 1e9
+    value = job_value(world, args.steps, flops, ms_total)
     assert int(info.item()) == 0
 
     peaks, peak_src = load_peaks()
@@ -311,11 +323,7 @@ def run_ours(args):
         for _ in range(esteps):
             binding.check(h.gb_chol_factor(n, s, dt, Ah, n, Lh, n, infoh, stream), "e2e")
         torch.cuda.synchronize()
-        el = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([el], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
+        el = dist_max(time.perf_counter() - t0, dist, dev)
         assert int(infoh[0]) == 0
         esz = A.element_size()
         e2e = {"value": world * esteps * flops / el / 1e9, "unit": UNIT,
