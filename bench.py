@@ -680,6 +680,51 @@ def run_served(args):
     return 0
 
 
+# ------------------------------------------------------------- Strassen
+def run_strassen(args):
+    """One Strassen level in the delayed update against the classical update:
+    FP64 and FP32 pivot-free LU and Cholesky at n, s (time, GFLOP/s counted
+    with the classical n^3/3 and 2n^3/3, backward error)."""
+    import torch
+
+    from paper_1812_02056_gb300 import _build, binding, inputs
+    _build.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    h = binding.Handle(0)
+    n, s = args.n, args.s
+    out = {"mode": "strassen", "n": n, "s": s, "results": {}}
+    Ac = inputs.spd_gram(n, inputs.seed_for(inputs.W_N8192, 0), device=dev)
+    Al = torch.from_numpy(inputs.lu_diag_dominant(n, inputs.seed_for(inputs.W_N8192, 50))).to(dev)
+    for kind, A64 in (("lu", Al), ("chol", Ac)):
+        for dtype in ("f64", "f32"):
+            A = A64 if dtype == "f64" else A64.float()
+            F = torch.empty_like(A)
+            info = torch.zeros(1, dtype=torch.int32, device=dev)
+            dt = binding.DTYPES[dtype]
+            fn = h.gb_lu_factor if kind == "lu" else h.gb_chol_factor
+            for st_on in (0, 1):
+                h.set_option(binding.GB_OPT_STRASSEN, st_on)
+                fn(n, s, dt, A, n, F, n, info)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(args.reps):
+                    fn(n, s, dt, A, n, F, n, info)
+                e1.record()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / args.reps
+                fl = (2.0 if kind == "lu" else 1.0) * n ** 3 / 3.0
+                be = h.backward_error(A64, F, dtype, lu=(kind == "lu"))
+                out["results"][f"{kind}_{dtype}_{'strassen' if st_on else 'classical'}"] = {
+                    "ms": ms, "gflops": fl / (ms * 1e-3) / 1e9, "backward_error": be,
+                    "info": int(info.item())}
+            h.set_option(binding.GB_OPT_STRASSEN, 0)
+    print(json.dumps(out))
+    h.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -695,7 +740,7 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip sweeps and accuracy figures")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--mode", choices=["chol", "update", "mixed", "batched", "served"],
+    ap.add_argument("--mode", choices=["chol", "update", "mixed", "batched", "served", "strassen"],
                     default="chol",
                     help="chol: the benchmark line; update: the tensor-core rank-s update "
                          "alone; mixed: FP64 vs mixed-precision time to solution")
@@ -721,6 +766,8 @@ def main():
         return run_batched(args)
     if args.mode == "served":
         return run_served(args)
+    if args.mode == "strassen":
+        return run_strassen(args)
     return run_ours(args)
 
 

@@ -130,10 +130,18 @@ typedef enum gb_option {
   GB_OPT_BATCHED_EXACT = 6, /* 1: the batched kernel rounds every product and
                                every subtraction separately (no FMA), as the
                                FP64 oracle does; default 0.                  */
-  GB_OPT_LOOKAHEAD = 7      /* 1 (default): each delayed update first updates
+  GB_OPT_LOOKAHEAD = 7,     /* 1 (default): each delayed update first updates
                                the next s-block's columns, and the rest of it
                                runs on a second stream while the next block's
                                column steps proceed; 0: one stream.          */
+  GB_OPT_STRASSEN = 8       /* 1: the FP64/FP32 delayed updates use one level
+                               of Strassen's multiplication (7 half-size
+                               products; the paper's practical variant, Sec. 2
+                               timing paragraph): LU's update, and the
+                               off-diagonal block of Cholesky's square update
+                               (its diagonal halves stay classical); also
+                               gb_rank_update without the lower mask.
+                               Default 0.                                    */
 } gb_option;
 
 gb_status gb_set_option(gb_handle *h, gb_option opt, int64_t value);

@@ -36,6 +36,7 @@ GB_OPT_INNER_STEP, GB_OPT_USE_GRAPHS, GB_OPT_TC_UPDATE, GB_OPT_SPIN_LIMIT = 1, 2
 GB_OPT_PROFILE = 5
 GB_OPT_BATCHED_EXACT = 6
 GB_OPT_LOOKAHEAD = 7
+GB_OPT_STRASSEN = 8
 
 
 class GbError(RuntimeError):

@@ -234,6 +234,23 @@ double update_bytes(int64_t M, int64_t N, int64_t K, bool lower, size_t e) {
 // (Cholesky's delayed update or part of it), on the tensor cores for the
 // mixed dtypes, on the CUDA cores otherwise.  `pack_slot` names the packed-
 // operand workspace of the stream the call is issued on.
+// C -= X op(Y), no mask, through one Strassen level when the option is on
+// and the block is large enough to profit; `slot` is the stream's workspace.
+template <typename T>
+gb_status general_update(gb_handle *h, T *C, int64_t ldc, const T *X, int64_t ldx, const T *Y,
+                         int64_t ldy, int64_t M, int64_t N, int64_t K, bool nn, int *status,
+                         int slot, cudaStream_t st) {
+  if (h->strassen && std::min(M, N) >= 512 && K >= 32) {
+    gb_status r = ws_reserve(h, slot, strassen_work_bytes(M, N, K, sizeof(T)), st);
+    if (r != GB_OK) return r;
+    GB_CUDA_TRY(launch_update_strassen<T>(C, ldc, X, ldx, Y, ldy, M, N, K, nn, status,
+                                          h->ws[slot].ptr, h->ws[slot].bytes, st));
+    return GB_OK;
+  }
+  GB_CUDA_TRY(launch_update_simt<T>(C, ldc, X, ldx, Y, ldy, M, N, K, nn, false, 0, status, st));
+  return GB_OK;
+}
+
 template <typename T>
 gb_status chol_update(gb_handle *h, gb_dtype dt, T *C, const T *X, const T *Y, int64_t ld,
                       int64_t M, int64_t N, int64_t K, int *status, int pack_slot,
@@ -266,6 +283,19 @@ gb_status chol_update(gb_handle *h, gb_dtype dt, T *C, const T *X, const T *Y, i
       GB_CUDA_TRY(launch_update_tc(a, st));
       return GB_OK;
     }
+  }
+  if (h->strassen && M == N && X == Y && M >= 1024 && K >= 32) {
+    // square lower update: two classical halves on the diagonal, the
+    // off-diagonal block C21 -= R2 R1^T through Strassen
+    const int64_t m1 = M / 2, m2 = M - m1;
+    const int slot = pack_slot == WS_PANEL2 ? WS_STRAS2 : WS_STRAS;
+    GB_CUDA_TRY(launch_update_simt<T>(C, ld, X, ld, X, ld, m1, m1, K, false, true, 0, status, st));
+    gb_status r = general_update<T>(h, C + m1 * ld, ld, X + m1 * ld, ld, X, ld, m2, m1, K, false,
+                                    status, slot, st);
+    if (r != GB_OK) return r;
+    GB_CUDA_TRY(launch_update_simt<T>(C + m1 * ld + m1, ld, X + m1 * ld, ld, X + m1 * ld, ld, m2,
+                                      m2, K, false, true, 0, status, st));
+    return GB_OK;
   }
   GB_CUDA_TRY(launch_update_simt<T>(C, ld, X, ld, Y, ld, M, N, K, false, true, 0, status, st));
   return GB_OK;
@@ -453,8 +483,10 @@ gb_status lu_blocked(gb_handle *h, int64_t n, int64_t s, T *W, int64_t ld, int *
           done = true;
         }
       }
-      if (!done)
-        GB_CUDA_TRY(launch_update_simt<T>(C, ld, RL, ld, RU, ld, m, m, sb, true, false, 0, status, st));
+      if (!done) {
+        gb_status r = general_update<T>(h, C, ld, RL, ld, RU, ld, m, m, sb, true, status, WS_STRAS, st);
+        if (r != GB_OK) return r;
+      }
     }
   }
   return GB_OK;
@@ -819,6 +851,7 @@ gb_status gb_set_option(gb_handle *h, gb_option opt, int64_t v) {
     case GB_OPT_PROFILE: h->profile = v ? 1 : 0; return GB_OK;
     case GB_OPT_BATCHED_EXACT: h->batched_exact = v ? 1 : 0; return GB_OK;
     case GB_OPT_LOOKAHEAD: h->lookahead = v ? 1 : 0; return GB_OK;
+    case GB_OPT_STRASSEN: h->strassen = v ? 1 : 0; return GB_OK;
     default: return -2;
   }
 }
@@ -834,6 +867,7 @@ gb_status gb_get_option(gb_handle *h, gb_option opt, int64_t *v) {
     case GB_OPT_PROFILE: *v = h->profile; return GB_OK;
     case GB_OPT_BATCHED_EXACT: *v = h->batched_exact; return GB_OK;
     case GB_OPT_LOOKAHEAD: *v = h->lookahead; return GB_OK;
+    case GB_OPT_STRASSEN: *v = h->strassen; return GB_OK;
     default: return -2;
   }
 }
@@ -1188,7 +1222,15 @@ extern "C" gb_status gb_rank_update(gb_handle *h, gb_dtype dt, int lower, int y_
   const bool nn = y_is_kxn != 0;
   int *status = h->d_status;
   GB_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), st));
-  if (dt == GB_F64) {
+  if (dt == GB_F64 && !lower) {
+    gb_status r = general_update<double>(h, (double *)C, ldc, (const double *)X, ldx,
+                                         (const double *)Y, ldy, M, N, K, nn, status, WS_STRAS, st);
+    if (r != GB_OK) return r;
+  } else if (dt == GB_F32 && !lower) {
+    gb_status r = general_update<float>(h, (float *)C, ldc, (const float *)X, ldx,
+                                        (const float *)Y, ldy, M, N, K, nn, status, WS_STRAS, st);
+    if (r != GB_OK) return r;
+  } else if (dt == GB_F64) {
     GB_CUDA_TRY(launch_update_simt<double>((double *)C, ldc, (const double *)X, ldx,
                                            (const double *)Y, ldy, M, N, K, nn, lower != 0, 0,
                                            status, st));

@@ -61,11 +61,12 @@ struct gb_handle {
   unsigned long long *d_arrivals = nullptr;  // arrival counter of the fused panel kernel
   double *d_scalars = nullptr;  // small FP64 reduction outputs
   unsigned sync_epoch = 0;
-  gb::Workspace ws[6];       // named workspaces, see WS_* below
+  gb::Workspace ws[8];       // named workspaces, see WS_* below
   std::mutex mu;
   // GB_OPT_PROFILE: event pairs recorded around launches, read later
   int profile = 0;
   int lookahead = 1;                  // GB_OPT_LOOKAHEAD
+  int strassen = 0;                   // GB_OPT_STRASSEN
   cudaStream_t hi = nullptr;          // high priority: column steps and next-block updates
   cudaStream_t aux = nullptr;         // low priority: the rest of each update
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -95,7 +96,8 @@ struct gb_handle {
 
 namespace gb {
 
-enum { WS_STAGE = 0, WS_PANEL = 1, WS_SOLVE = 2, WS_MISC = 3, WS_DINV = 4, WS_PANEL2 = 5 };
+enum { WS_STAGE = 0, WS_PANEL = 1, WS_SOLVE = 2, WS_MISC = 3, WS_DINV = 4, WS_PANEL2 = 5,
+       WS_STRAS = 6, WS_STRAS2 = 7 };
 constexpr int SYNC_WORDS = 1 << 16;
 
 // Make sure workspace `slot` holds >= bytes; waits for `stream` before
@@ -136,6 +138,15 @@ template <typename T>
 cudaError_t launch_update_simt(T *C, int64_t ldc, const T *X, int64_t ldx, const T *Y,
                                int64_t ldy, int64_t M, int64_t N, int64_t K, bool nn, bool lower,
                                int64_t diag, const int *status, cudaStream_t st);
+
+// One level of Strassen for C -= X op(Y) (no lower mask); workspace of
+// strassen_work_bytes.  Odd sizes leave classical remainders.
+size_t strassen_work_bytes(int64_t M, int64_t N, int64_t K, size_t esz);
+template <typename T>
+cudaError_t launch_update_strassen(T *C, int64_t ldc, const T *X, int64_t ldx, const T *Y,
+                                   int64_t ldy, int64_t M, int64_t N, int64_t K, bool nn,
+                                   const int *status, void *work, size_t work_bytes,
+                                   cudaStream_t st);
 
 // Elementwise copies.  Lower-triangle copy with zeroed strict upper (chol)
 // or full copy (lu); Tin -> Tout.

@@ -141,3 +141,52 @@ def test_bf16x3_is_fp32_accurate_where_bf16_is_not(h):
         errs[dt] = ((C - ref).abs() / ref.abs()).max().item()
     assert errs["mix_bf16"] > 1e-4
     assert errs["mix_bf16x3"] < 2e-5
+
+
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+@pytest.mark.parametrize("M,N,K,kxn", [(1024, 1024, 128, 1), (1001, 777, 129, 1),
+                                       (777, 1001, 64, 0), (2048, 600, 255, 0)])
+def test_strassen_matches_classical_on_exact_integers(h, dt, M, N, K, kxn):
+    """Every sum Strassen forms is exact for small integers, so one level must
+    give the same bits as the classical update (odd sizes take the classical
+    remainders)."""
+    from paper_1812_02056_gb300 import binding
+    g = torch.Generator().manual_seed(M + N + K)
+    tt = torch.float64 if dt == "f64" else torch.float32
+    X = torch.randint(-4, 5, (M, K), generator=g).to(tt)
+    Y = torch.randint(-4, 5, (K, N) if kxn else (N, K), generator=g).to(tt)
+    C0 = torch.randint(-1000, 1000, (M, N), generator=g).to(tt)
+    exp, _ = _expected(C0, X, Y, kxn, dt)
+    h.set_option(binding.GB_OPT_STRASSEN, 1)
+    try:
+        C = _run(h, dt, 0, kxn, C0.to(DEV), X.to(DEV), Y.to(DEV)).cpu().double()
+    finally:
+        h.set_option(binding.GB_OPT_STRASSEN, 0)
+    assert torch.equal(C, exp)
+
+
+@pytest.mark.parametrize("kind", ["chol", "lu"])
+def test_factorizations_with_strassen_match_oracle(h, kind):
+    import oracle
+    from paper_1812_02056_gb300 import binding
+    from paper_1812_02056_gb300 import inputs as I
+    from tests.helpers import guarded_rel_err, lu_split
+    n, s = 2600, 1100
+    A = I.spd_gram(n, 3) if kind == "chol" else I.lu_diag_dominant(n, 3)
+    Ad = torch.from_numpy(A).to(DEV)
+    h.set_option(binding.GB_OPT_STRASSEN, 1)
+    try:
+        F, info = (h.chol_factor if kind == "chol" else h.lu_factor)(Ad, s, "f64")
+    finally:
+        h.set_option(binding.GB_OPT_STRASSEN, 0)
+    assert int(info.item()) == 0
+    Fg = F.cpu().numpy()
+    if kind == "chol":
+        Lo, _ = oracle.chol(A, s)
+        assert guarded_rel_err(Fg, Lo) <= 1e-10
+        assert h.backward_error(Ad, F, "f64") <= 1e-13
+    else:
+        Lo, Uo, _ = oracle.lu(A, s)
+        L, U = lu_split(Fg)
+        assert guarded_rel_err(L, Lo) <= 1e-10 and guarded_rel_err(U, Uo) <= 1e-10
+        assert h.backward_error(Ad, F, "f64", lu=True) <= 1e-13
