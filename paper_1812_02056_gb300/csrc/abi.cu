@@ -400,16 +400,80 @@ gb_status chol_blocked_on(gb_handle *h, int64_t n, int64_t s, T *W, int64_t ld, 
   return GB_OK;
 }
 
+// C -= X Y (LU's R_L R_U, full block), tensor cores for the mixed dtypes,
+// CUDA cores (optionally one Strassen level) otherwise.
+template <typename T>
+gb_status lu_update(gb_handle *h, gb_dtype dt, T *C, const T *X, const T *Y, int64_t ld,
+                    int64_t M, int64_t N, int64_t K, int *status, int pack_slot,
+                    cudaStream_t st) {
+  if (M <= 0 || N <= 0 || K <= 0) return GB_OK;
+  if constexpr (sizeof(T) == 4) {
+    if (is_mixed(dt) && h->tc_update) {
+      TcUpdateArgs a{};
+      a.C = reinterpret_cast<float *>(C);
+      a.ldc = ld;
+      a.X = reinterpret_cast<const float *>(X);
+      a.ldx = ld;
+      a.Y = reinterpret_cast<const float *>(Y);
+      a.ldy = ld;
+      a.M = M;
+      a.N = N;
+      a.K = K;
+      a.nn = true;
+      a.lower = false;
+      a.diag = 0;
+      a.f16 = (dt == GB_MIX_F16);
+      a.split = split_of(dt);
+      a.status = status;
+      a.err = h->d_err;
+      a.spin_limit = h->spin_limit;
+      gb_status ws = ws_reserve(h, pack_slot, tc_pack_bytes(M, N, K, true, a.split), st);
+      if (ws != GB_OK) return ws;
+      a.pack = h->ws[pack_slot].ptr;
+      a.pack_bytes = h->ws[pack_slot].bytes;
+      GB_CUDA_TRY(launch_update_tc(a, st));
+      return GB_OK;
+    }
+  }
+  return general_update<T>(h, C, ld, X, ld, Y, ld, M, N, K, true, status,
+                           pack_slot == WS_PANEL2 ? WS_STRAS2 : WS_STRAS, st);
+}
+
+template <typename T, typename Tc>
+gb_status lu_blocked_on(gb_handle *h, int64_t n, int64_t s, T *W, int64_t ld, int *status,
+                        gb_dtype dt, cudaStream_t st, bool la);
+
 template <typename T, typename Tc>
 gb_status lu_blocked(gb_handle *h, int64_t n, int64_t s, T *W, int64_t ld, int *status,
                      gb_dtype dt, cudaStream_t st) {
+  const bool la = h->lookahead && h->hi && h->aux && n > s + s;
+  if (!la) return lu_blocked_on<T, Tc>(h, n, s, W, ld, status, dt, st, false);
+  GB_CUDA_TRY(cudaEventRecord(h->ev_fork, st));
+  GB_CUDA_TRY(cudaStreamWaitEvent(h->hi, h->ev_fork, 0));
+  gb_status r = lu_blocked_on<T, Tc>(h, n, s, W, ld, status, dt, h->hi, true);
+  GB_CUDA_TRY(cudaEventRecord(h->ev_join, h->hi));
+  GB_CUDA_TRY(cudaStreamWaitEvent(st, h->ev_join, 0));
+  return r;
+}
+
+template <typename T, typename Tc>
+gb_status lu_blocked_on(gb_handle *h, int64_t n, int64_t s, T *W, int64_t ld, int *status,
+                        gb_dtype dt, cudaStream_t st, bool la) {
   const int64_t b = std::max(1, std::min(64, h->inner_step));
+  const size_t e = sizeof(T);
+  if (la && is_mixed(dt) && h->tc_update) {
+    const int64_t m0 = n - std::min(s, n);
+    const size_t pb = tc_pack_bytes(m0, m0, std::min(s, n), true, split_of(dt));
+    gb_status r = ws_reserve(h, WS_PANEL, pb, st);
+    if (r == GB_OK) r = ws_reserve(h, WS_PANEL2, pb, h->aux);
+    if (r != GB_OK) return r;
+  }
+  bool rest_pending = false;
   for (int64_t z = 0; z < n; z += s) {
     const int64_t sb = std::min(s, n - z);
     const int64_t pe = z + sb;
     for (int64_t j0 = z; j0 < pe; j0 += b) {
       const int bw = (int)std::min(b, pe - j0);
-      const size_t e = sizeof(T);
       {
         PhaseTimer t(h, st, GB_PHASE_DIAG, 2.0 * (double)bw * bw * bw / 3.0, 2.0 * bw * bw * e);
         GB_CUDA_TRY((launch_lu_diag<T, Tc>(W, ld, j0, bw, status, st)));
@@ -444,51 +508,45 @@ gb_status lu_blocked(gb_handle *h, int64_t n, int64_t s, T *W, int64_t ld, int *
         }
       }
     }
-    if (pe < n) {  // delayed rank-sb update A[pe.., pe..] -= R_L R_U
-      const int64_t m = n - pe;
-      T *C = W + pe * ld + pe;
-      const T *RL = W + pe * ld + z;
-      const T *RU = W + z * ld + pe;
-      bool done = false;
-      const bool tc = is_mixed(dt) && h->tc_update;
+    if (pe >= n) break;
+    // delayed rank-sb update A[pe.., pe..] -= R_L R_U
+    const int64_t m = n - pe;
+    const T *RL = W + pe * ld + z;  // rows pe.., columns z..pe
+    const T *RU = W + z * ld + pe;  // rows z..pe, columns pe..
+    if (!la) {
       PhaseTimer t(h, st, GB_PHASE_UPDATE, update_flops(m, m, sb, false),
-                   update_bytes(m, m, sb, false, sizeof(T)) -
-                       (tc ? 2.0 * (double)m * sb * (sizeof(T) - 2) : 0.0));
-      if constexpr (sizeof(T) == 4) {
-        if (is_mixed(dt) && h->tc_update) {
-          TcUpdateArgs a{};
-          a.C = reinterpret_cast<float *>(C);
-          a.ldc = ld;
-          a.X = reinterpret_cast<const float *>(RL);
-          a.ldx = ld;
-          a.Y = reinterpret_cast<const float *>(RU);
-          a.ldy = ld;
-          a.M = m;
-          a.N = m;
-          a.K = sb;
-          a.nn = true;
-          a.lower = false;
-          a.diag = 0;
-          a.f16 = (dt == GB_MIX_F16);
-          a.split = split_of(dt);
-          a.status = status;
-          a.err = h->d_err;
-          a.spin_limit = h->spin_limit;
-          const size_t pb = tc_pack_bytes(m, m, sb, true, split_of(dt));
-          gb_status ws = ws_reserve(h, WS_PANEL, pb, st);
-          if (ws != GB_OK) return ws;
-          a.pack = h->ws[WS_PANEL].ptr;
-          a.pack_bytes = h->ws[WS_PANEL].bytes;
-          GB_CUDA_TRY(launch_update_tc(a, st));
-          done = true;
-        }
-      }
-      if (!done) {
-        gb_status r = general_update<T>(h, C, ld, RL, ld, RU, ld, m, m, sb, true, status, WS_STRAS, st);
-        if (r != GB_OK) return r;
-      }
+                   update_bytes(m, m, sb, false, e));
+      gb_status r = lu_update<T>(h, dt, W + pe * ld + pe, RL, RU, ld, m, m, sb, status, WS_PANEL, st);
+      if (r != GB_OK) return r;
+      continue;
+    }
+    const int64_t nb = std::min(s, n - pe);
+    const int64_t q = pe + nb;
+    if (rest_pending) GB_CUDA_TRY(cudaStreamWaitEvent(st, h->ev_rest, 0));
+    {
+      // the next block's L columns (all rows) and U rows (all columns)
+      PhaseTimer t(h, st, GB_PHASE_UPDATE,
+                   update_flops(m, nb, sb, false) + update_flops(nb, n - q, sb, false),
+                   update_bytes(m, nb, sb, false, e) + update_bytes(nb, n - q, sb, false, e));
+      gb_status r = lu_update<T>(h, dt, W + pe * ld + pe, RL, RU, ld, m, nb, sb, status, WS_PANEL, st);
+      if (r == GB_OK && q < n)
+        r = lu_update<T>(h, dt, W + pe * ld + q, RL, RU + nb, ld, nb, n - q, sb, status, WS_PANEL,
+                         st);
+      if (r != GB_OK) return r;
+    }
+    if (q < n) {
+      GB_CUDA_TRY(cudaEventRecord(h->ev_next, st));
+      GB_CUDA_TRY(cudaStreamWaitEvent(h->aux, h->ev_next, 0));
+      PhaseTimer t(h, h->aux, GB_PHASE_UPDATE, update_flops(n - q, n - q, sb, false),
+                   update_bytes(n - q, n - q, sb, false, e));
+      gb_status r = lu_update<T>(h, dt, W + q * ld + q, RL + nb * ld, RU + nb, ld, n - q, n - q, sb,
+                                 status, WS_PANEL2, h->aux);
+      if (r != GB_OK) return r;
+      GB_CUDA_TRY(cudaEventRecord(h->ev_rest, h->aux));
+      rest_pending = true;
     }
   }
+  if (rest_pending) GB_CUDA_TRY(cudaStreamWaitEvent(st, h->ev_rest, 0));
   return GB_OK;
 }
 
