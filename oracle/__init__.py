@@ -1,4 +1,4 @@
-"""Plain FP64 CPU oracle for Algorithms 1 and 2 of arXiv:1812.02056.
+"""Plain FP64 CPU oracle for Algorithms 1, 2 and 3 of arXiv:1812.02056.
 
 TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the CPU
 baseline leg of ``bench.py`` use it to check and to time the CUDA library.
@@ -56,6 +56,12 @@ def _load():
         lib.orc_chol.restype = i64
         lib.orc_lu.argtypes = [i64, i64, P, i64, P, i64, P, i64, i32]
         lib.orc_lu.restype = i64
+        lib.orc_qr.argtypes = [i64, i64, P, i64, P, i64, P, i64, i32]
+        lib.orc_qr.restype = i64
+        lib.orc_qr_backward_error.argtypes = [i64, P, i64, P, i64, P, i64]
+        lib.orc_qr_backward_error.restype = dbl
+        lib.orc_orthogonality.argtypes = [i64, P, i64]
+        lib.orc_orthogonality.restype = dbl
         for name in ("orc_solve_lower", "orc_solve_lower_trans", "orc_solve_unit_upper",
                      "orc_chol_solve"):
             getattr(lib, name).argtypes = [i64, i64, P, i64, P, i64]
@@ -121,6 +127,34 @@ def lu(A, s: int, sequential: bool = False):
     if info < 0:
         raise ValueError(f"orc_lu failed ({info})")
     return L, U, int(info)
+
+
+def qr(A, s: int, full_r: bool = False):
+    """Algorithm 3 (fast QR, step ``s``, block Gram-Schmidt): ``A = Q R``.
+    Returns ``(Q, R, info)``; ``R`` is the upper triangle of ``Q^T A`` (all of
+    it with ``full_r``)."""
+    A = _f64(A)
+    n = A.shape[0]
+    Q = np.zeros((n, n))
+    R = np.zeros((n, n))
+    mode = FULL_SQUARE if full_r else 0
+    info = _load().orc_qr(n, int(s), _p(A), n, _p(Q), n, _p(R), n, mode)
+    if info < 0:
+        raise ValueError(f"orc_qr failed ({info})")
+    return Q, R, int(info)
+
+
+def qr_backward_error(A, Q, R) -> float:
+    """``||A - Q R||_F / ||A||_F`` in long double."""
+    A, Q, R = _f64(A), _f64(Q), _f64(R)
+    return float(_load().orc_qr_backward_error(A.shape[0], _p(A), A.shape[0], _p(Q), Q.shape[0],
+                                               _p(R), R.shape[0]))
+
+
+def orthogonality(Q) -> float:
+    """``||Q^T Q - I||_F`` in long double."""
+    Q = _f64(Q)
+    return float(_load().orc_orthogonality(Q.shape[0], _p(Q), Q.shape[0]))
 
 
 def _rhs(B):

@@ -1,6 +1,6 @@
 /*
- * oracle.c -- plain FP64 CPU oracle for the blocked Cholesky and pivot-free
- * LU of Camarero, "Simple, Fast and Practicable Algorithms for Cholesky, LU
+ * oracle.c -- plain FP64 CPU oracle for the blocked Cholesky, pivot-free
+ * LU and Gram-Schmidt QR of Camarero, "Simple, Fast and Practicable Algorithms for Cholesky, LU
  * and QR Decomposition Using Fast Rectangular Matrix Multiplication"
  * (arXiv:1812.02056).
  *
@@ -28,11 +28,12 @@
 #include <omp.h>
 #endif
 
-/* mode bits for orc_chol / orc_lu */
+/* mode bits for orc_chol / orc_lu / orc_qr */
 #define ORC_FULL_SQUARE 1 /* Cholesky: update the whole trailing square, as
                              Algorithm 1 writes it (default: lower triangle,
                              the only part the column step reads). LU always
-                             updates the full square. */
+                             updates the full square.  QR: R receives all of
+                             Q^T A (default: its upper triangle, zero below). */
 #define ORC_SEQUENTIAL 2  /* subtract each product L_ik*L_jk from A_ij in
                              turn instead of forming S = R R^T first */
 
@@ -217,6 +218,127 @@ int64_t orc_lu(int64_t n, int64_t s, const double *A, int64_t lda, double *L,
 }
 
 /*
+ * Algorithm 3 (fast QR with step s): A = Q R with Q orthogonal and R upper
+ * triangular.
+ *
+ * M starts as a copy of A.  Column c of Q is column c of M, made orthogonal
+ * to the columns of Q computed since the checkpoint z one after the other
+ * (v := v - u (u^T v) for u = Q[:, z], ..., Q[:, c-1]) and divided by its
+ * norm.  When c = z + s, the columns c..n-1 of M first lose their
+ * components along the block B_Q = Q[:, z..c-1] at once: C := B_Q^T B_M,
+ * S := B_Q C, M[:, c..] -= S, z := c.  Finally R := Q^T A.
+ *
+ * A, Q, R are n x n (lda, ldq, ldr).  R holds (Q^T A)_ij for j >= i and zero
+ * below the diagonal, or all of Q^T A with ORC_FULL_SQUARE.  Every sum runs
+ * over its index in ascending order, one product at a time (the loops walk
+ * rows of M and A for locality; each element still receives its products in
+ * that order).  Returns 0, or c+1 when the norm of the projected column c is
+ * zero or NaN (A singular): the paper assumes full rank; the oracle stops
+ * there and leaves Q's later columns and R zero.
+ */
+int64_t orc_qr(int64_t n, int64_t s, const double *A, int64_t lda, double *Q, int64_t ldq,
+               double *R, int64_t ldr, int mode) {
+  if (n < 0 || s < 1) return -1;
+  const int full = (mode & ORC_FULL_SQUARE) != 0;
+  const size_t nn = (size_t)(n > 0 ? n : 1);
+  const size_t sw = (size_t)(s < n ? s : (n > 0 ? n : 1));
+  double *M = (double *)malloc(nn * nn * sizeof(double));   /* working copy, row-major */
+  double *Qc = (double *)malloc(nn * nn * sizeof(double));  /* Q by columns: Qc[j*n+i] = Q_ij */
+  double *Cm = (double *)malloc(sw * nn * sizeof(double));  /* C = B_Q^T B_M, w x (n-c) */
+  double *v = (double *)malloc(nn * sizeof(double));
+  if (!M || !Qc || !Cm || !v) {
+    free(M);
+    free(Qc);
+    free(Cm);
+    free(v);
+    return -2;
+  }
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t j = 0; j < n; ++j) {
+      M[i * n + j] = A[i * lda + j];
+      Qc[j * n + i] = 0.0;
+      Q[i * ldq + j] = 0.0;
+      R[i * ldr + j] = 0.0;
+    }
+
+  int64_t z = 0, info = 0;
+  for (int64_t c = 0; c < n && info == 0; ++c) {
+    if (c == z + s) {
+      const int64_t w = c - z, m = n - c;
+      /* C := B_Q^T B_M:  C_kj = sum_i Q_{i,z+k} M_{i,c+j} */
+#pragma omp parallel for schedule(static)
+      for (int64_t k = 0; k < w; ++k) {
+        double *ck = Cm + k * m;
+        const double *qk = Qc + (z + k) * n;
+        for (int64_t j = 0; j < m; ++j) ck[j] = 0.0;
+        for (int64_t i = 0; i < n; ++i) {
+          const double q = qk[i];
+          const double *mi = M + i * n + c;
+          for (int64_t j = 0; j < m; ++j) ck[j] = ck[j] + q * mi[j];
+        }
+      }
+      /* S := B_Q C;  M[:, c..] -= S:  S_ij = sum_k Q_{i,z+k} C_kj */
+#pragma omp parallel
+      {
+        double *srow = (double *)malloc((size_t)(m > 0 ? m : 1) * sizeof(double));
+#pragma omp for schedule(static)
+        for (int64_t i = 0; i < n; ++i) {
+          for (int64_t j = 0; j < m; ++j) srow[j] = 0.0;
+          for (int64_t k = 0; k < w; ++k) {
+            const double q = Qc[(z + k) * n + i];
+            const double *ck = Cm + k * m;
+            for (int64_t j = 0; j < m; ++j) srow[j] = srow[j] + q * ck[j];
+          }
+          double *mi = M + i * n + c;
+          for (int64_t j = 0; j < m; ++j) mi[j] = mi[j] - srow[j];
+        }
+        free(srow);
+      }
+      z = c;
+    }
+    /* v := column c of M;  v := v - u (u^T v) for u = Q[:, z], ..., Q[:, c-1] */
+    for (int64_t i = 0; i < n; ++i) v[i] = M[i * n + c];
+    for (int64_t j = z; j < c; ++j) {
+      const double *u = Qc + j * n;
+      double d = 0.0;
+      for (int64_t i = 0; i < n; ++i) d = d + u[i] * v[i];
+      for (int64_t i = 0; i < n; ++i) v[i] = v[i] - u[i] * d;
+    }
+    /* Q[:, c] := v / ||v|| */
+    double nrm2 = 0.0;
+    for (int64_t i = 0; i < n; ++i) nrm2 = nrm2 + v[i] * v[i];
+    const double nrm = sqrt(nrm2);
+    if (!(nrm > 0.0)) {
+      info = c + 1;
+      break;
+    }
+    for (int64_t i = 0; i < n; ++i) Qc[c * n + i] = v[i] / nrm;
+  }
+  if (info == 0) {
+    for (int64_t i = 0; i < n; ++i)
+      for (int64_t j = 0; j < n; ++j) Q[i * ldq + j] = Qc[j * n + i];
+    /* R := Q^T A:  R_ij = sum_k Q_ki A_kj */
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t i = 0; i < n; ++i) {
+      const int64_t j0 = full ? 0 : i;
+      double *ri = R + i * ldr;
+      const double *qi = Qc + i * n;
+      for (int64_t j = j0; j < n; ++j) ri[j] = 0.0;
+      for (int64_t k = 0; k < n; ++k) {
+        const double q = qi[k];
+        const double *ak = A + k * lda;
+        for (int64_t j = j0; j < n; ++j) ri[j] = ri[j] + q * ak[j];
+      }
+    }
+  }
+  free(M);
+  free(Qc);
+  free(Cm);
+  free(v);
+  return info;
+}
+
+/*
  * Triangular solves, textbook forward and back substitution, B row-major
  * n x nrhs (ldb), overwritten with the solution.
  */
@@ -377,4 +499,36 @@ double orc_lu_backward_error(int64_t n, const double *A, int64_t lda, const doub
     }
   }
   return den > 0.0L ? (double)sqrtl(num / den) : 0.0;
+}
+
+/* ||A - Q R||_F / ||A||_F, accumulated in long double */
+double orc_qr_backward_error(int64_t n, const double *A, int64_t lda, const double *Q,
+                             int64_t ldq, const double *R, int64_t ldr) {
+  long double num = 0.0L, den = 0.0L;
+#pragma omp parallel for reduction(+ : num, den) schedule(static)
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t j = 0; j < n; ++j) {
+      long double acc = 0.0L;
+      for (int64_t k = 0; k < n; ++k)
+        acc += (long double)Q[i * ldq + k] * (long double)R[k * ldr + j];
+      const long double d = (long double)A[i * lda + j] - acc;
+      num += d * d;
+      den += (long double)A[i * lda + j] * (long double)A[i * lda + j];
+    }
+  return den > 0.0L ? (double)sqrtl(num / den) : 0.0;
+}
+
+/* ||Q^T Q - I||_F, accumulated in long double */
+double orc_orthogonality(int64_t n, const double *Q, int64_t ldq) {
+  long double num = 0.0L;
+#pragma omp parallel for reduction(+ : num) schedule(static)
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t j = 0; j < n; ++j) {
+      long double acc = 0.0L;
+      for (int64_t k = 0; k < n; ++k)
+        acc += (long double)Q[k * ldq + i] * (long double)Q[k * ldq + j];
+      const long double d = acc - (i == j ? 1.0L : 0.0L);
+      num += d * d;
+    }
+  return (double)sqrtl(num);
 }

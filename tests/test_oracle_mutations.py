@@ -43,6 +43,20 @@ MUTATIONS = {
     "lu_col_wrong_factor": ("ucol[k] = U[k * ldu + c];", "ucol[k] = U[c * ldu + k];"),
     "lu_row_sign": ("urow[i] = urow[i] - lck * U[k * ldu + i];",
                     "urow[i] = urow[i] + lck * U[k * ldu + i];"),
+    "qr_proj_sign": ("v[i] = v[i] - u[i] * d;", "v[i] = v[i] + u[i] * d;"),
+    "qr_proj_dropped": ("for (int64_t i = 0; i < n; ++i) v[i] = v[i] - u[i] * d;",
+                        "(void)d;"),
+    "qr_first_proj_skipped": ("for (int64_t j = z; j < c; ++j) {\n      const double *u",
+                              "for (int64_t j = z + 1; j < c; ++j) {\n      const double *u"),
+    "qr_no_normalise": ("Qc[c * n + i] = v[i] / nrm;", "Qc[c * n + i] = v[i];"),
+    "qr_update_sign": ("mi[j] = mi[j] - srow[j];", "mi[j] = mi[j] + srow[j];"),
+    "qr_update_c_transposed": ("const double *qk = Qc + (z + k) * n;",
+                               "const double *qk = Qc + (z + k);"),
+    "qr_update_skipped_column": ("const double *mi = M + i * n + c;",
+                                 "const double *mi = M + i * n + c + 1;"),
+    "qr_checkpoint_not_moved": ("      z = c;\n    }\n    /* v := column c",
+                                "    }\n    /* v := column c"),
+    "qr_r_transposed": ("const double *qi = Qc + i * n;", "const double *qi = Qc + i;"),
     "lu_update_first_term_dropped": ("for (int64_t k = z; k < c; ++k) {\n              const double lik = L[i * ldl + k];\n              for (int64_t j = c; j < n; ++j) srow[j]",
                                      "for (int64_t k = z + 1; k < c; ++k) {\n              const double lik = L[i * ldl + k];\n              for (int64_t j = c; j < n; ++j) srow[j]"),
 }
@@ -92,6 +106,31 @@ def _pins_pass() -> bool:
             L, U, info = oracle.lu(C, s)
             if info != 0 or oracle.lu_backward_error(C, L, U) > 1e-13:
                 return False
+        # Algorithm 3: permutation times triangular (exact) and LAPACK
+        g = I.rng(77)
+        n = 12
+        perm = g.permutation(n)
+        P = np.zeros((n, n))
+        P[perm, np.arange(n)] = 1.0
+        R0 = np.triu(g.integers(-5, 6, size=(n, n)).astype(np.float64), 1)
+        R0[np.diag_indices(n)] = g.integers(1, 9, size=n).astype(np.float64)
+        for s in (1, 3, 12):
+            Q, R, info = oracle.qr(P @ R0, s)
+            if info != 0 or not np.array_equal(Q, P) or not np.array_equal(R, R0):
+                return False
+        D = I.gaussian(40, 40, 5) + 6.0 * np.eye(40)
+        Qh, Rh = np.linalg.qr(D)
+        sg = np.sign(np.diag(Rh))
+        Qh, Rh = Qh * sg[None, :], Rh * sg[:, None]
+        for s in (1, 4, 40):
+            Q, R, info = oracle.qr(D, s)
+            if info != 0 or np.abs(Q - Qh).max() > 1e-12 or np.abs(R - Rh).max() > 1e-11:
+                return False
+        # s = 1 and s = n perform the same operations in the same order
+        Q1, R1, _ = oracle.qr(D, 1)
+        Qn, Rn, _ = oracle.qr(D, 40)
+        if not (np.array_equal(Q1, Qn) and np.array_equal(R1, Rn)):
+            return False
         return True
     except Exception:
         return False
