@@ -416,24 +416,28 @@ def run_update(args):
             binding.check(h.gb_rank_update(dt, 1, 0, m, m, K, C, m, R, K, R, K, stream),
                           "gb_rank_update")
 
-        for _ in range(args.warmup):
-            call()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        l0 = binding.kernel_launches()
-        e0.record(stream)
-        for _ in range(args.reps):
-            call()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / args.reps
-        flops = 2.0 * K * m * (m + 1) / 2.0
-        cbytes = 8.0 * m * (m + 1) / 2.0  # FP32 lower triangle read + written
-        tflops = flops / (ms * 1e-3) / 1e12
-        out["results"].append({
-            "K": K, "m": m, "ms": ms, "tflops": tflops,
-            "frac_of_bf16_peak": tflops / peaks["bf16_tflops"],
-            "hbm_bound_tflops": peaks["hbm_gbs"] * 1e9 * flops / cbytes / 1e12,
-            "launches_per_call": (binding.kernel_launches() - l0) / args.reps})
+        default_mode = h.get_option(binding.GB_OPT_TC_UPDATE)
+        for mode in [int(v) for v in args.tc_modes.split(",")]:
+            h.set_option(binding.GB_OPT_TC_UPDATE, mode)
+            for _ in range(args.warmup):
+                call()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            l0 = binding.kernel_launches()
+            e0.record(stream)
+            for _ in range(args.reps):
+                call()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.reps
+            flops = 2.0 * K * m * (m + 1) / 2.0
+            cbytes = 8.0 * m * (m + 1) / 2.0  # FP32 lower triangle read + written
+            tflops = flops / (ms * 1e-3) / 1e12
+            out["results"].append({
+                "K": K, "m": m, "tc_mode": mode, "ms": ms, "tflops": tflops,
+                "frac_of_bf16_peak": tflops / peaks["bf16_tflops"],
+                "hbm_bound_tflops": peaks["hbm_gbs"] * 1e9 * flops / cbytes / 1e12,
+                "launches_per_call": (binding.kernel_launches() - l0) / args.reps})
+        h.set_option(binding.GB_OPT_TC_UPDATE, default_mode)
         del C, R
         torch.cuda.empty_cache()
     out["peaks"] = {"bf16_tflops": peaks["bf16_tflops"], "hbm_gbs": peaks["hbm_gbs"], "source": src}
@@ -578,7 +582,38 @@ def run_batched(args):
             "breakdowns": bad, "tuned_steps_by_32": steps[:16].tolist(), "tune_s": tune_s,
             "sample_backward_error_max": max(errs), "graph_replays": args.steps,
             "bytes_in_out": 2 * int((sizes ** 2).sum()) * esz}
-        del buf, outb, g
+        # Algorithm 2 on the same matrices (SPD: every leading minor is positive)
+        binding.check(h.gb_lu_batched_plan(len(sizes), n_arr, a_arr, n_arr, l_arr, n_arr, dt, 0),
+                      "lu plan")
+        with torch.cuda.stream(st):
+            binding.check(h.gb_batched_run(info, st), "lu warm")
+        torch.cuda.synchronize()
+        g2 = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g2, stream=st):
+            binding.check(h.gb_batched_run(info, st), "lu capture")
+        for _ in range(args.warmup):
+            g2.replay()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(args.steps):
+            g2.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        ms_lu = e0.elapsed_time(e1) / args.steps
+        lu_errs = []
+        for i in rng.choice(len(sizes), 4, replace=False):
+            n = int(sizes[i])
+            A = buf[offs[i]:offs[i] + n * n].view(n, n).double().cpu().numpy()
+            F = outb[offs[i]:offs[i] + n * n].view(n, n).double().cpu().numpy()
+            Lf = np.tril(F)
+            Uf = np.triu(F, 1) + np.eye(n)
+            lu_errs.append(oracle.lu_backward_error(A, Lf, Uf))
+        gf_lu = 2.0 * flops / (ms_lu * 1e-3) / 1e9
+        out["results"][dtype + "_lu"] = {
+            "ms_per_batch": ms_lu, "gflops": gf_lu, "frac_of_alu_peak": gf_lu / alu,
+            "breakdowns": int((info != 0).sum().item()), "step": "min(n, 32)",
+            "sample_backward_error_max": max(lu_errs), "graph_replays": args.steps}
+        del buf, outb, g, g2
         torch.cuda.empty_cache()
     # CPU oracle on a bounded sample of the same workload
     idx = np.random.default_rng(2).choice(len(sizes), args.batch_cpu_sample, replace=False)
@@ -725,6 +760,74 @@ def run_strassen(args):
     return 0
 
 
+def run_qr(args):
+    """Algorithm 3 (fast QR): FP64 and FP32 at n for each step s; GFLOP/s
+    counted as 3 n^3 (Gram-Schmidt Q: 2 n^3, R = Q^T A upper triangle: n^3),
+    per-phase device time, orthogonality ||Q^T Q - I||_F and backward error
+    ||A - Q R||_F / ||A||_F (checked with torch matmuls outside the timing),
+    and the oracle on a bounded sample."""
+    import time
+
+    import numpy as np
+    import torch
+
+    from paper_1812_02056_gb300 import _build, binding, inputs
+    _build.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    h = binding.Handle(0)
+    n = args.n
+    G = torch.from_numpy(inputs.gaussian(n, n, inputs.seed_for(inputs.W_N8192, 70))).to(dev)
+    A64 = G + 2.0 * np.sqrt(n) * torch.eye(n, dtype=torch.float64, device=dev)
+    out = {"mode": "qr", "n": n, "flop_count": "3 n^3", "results": {}}
+    for dtype in ("f64", "f32"):
+        A = A64 if dtype == "f64" else A64.float()
+        Q = torch.empty_like(A)
+        R = torch.empty_like(A)
+        info = torch.zeros(1, dtype=torch.int32, device=dev)
+        dt = binding.DTYPES[dtype]
+        for s, b in [(int(v), int(w)) for v in args.qr_steps.split(",")
+                     for w in args.qr_inner.split(",")]:
+            if b > s:
+                continue
+            h.set_option(binding.GB_OPT_QR_INNER_STEP, b)
+            binding.check(h.gb_qr_factor(n, s, dt, A, n, Q, n, R, n, info), "qr warm-up")
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(args.reps):
+                h.gb_qr_factor(n, s, dt, A, n, Q, n, R, n, info)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.reps
+            h.set_option(binding.GB_OPT_PROFILE, 1)
+            h.profile_read()
+            h.gb_qr_factor(n, s, dt, A, n, Q, n, R, n, info)
+            prof = h.profile_read()
+            h.set_option(binding.GB_OPT_PROFILE, 0)
+            Qd, Rd, Ad = Q.double(), R.double(), A.double()
+            orth = torch.linalg.norm(Qd.T @ Qd - torch.eye(n, dtype=torch.float64, device=dev)).item()
+            berr = (torch.linalg.norm(Ad - Qd @ Rd) / torch.linalg.norm(Ad)).item()
+            out["results"][f"{dtype}_s{s}_b{b}"] = {
+                "ms": ms, "gflops": 3.0 * n ** 3 / (ms * 1e-3) / 1e9, "info": int(info.item()),
+                "orthogonality": orth, "backward_error": berr,
+                "phase_ms": {"panel": prof.ms[2], "inner": prof.ms[3], "update_and_r": prof.ms[4]}}
+        h.set_option(binding.GB_OPT_QR_INNER_STEP, 16)
+    if not args.no_cpu:
+        import oracle
+        cn = min(2048, n)  # a bounded sample of the same input (seconds of CPU work)
+        Ah = A64[:cn, :cn].cpu().numpy()
+        t0 = time.perf_counter()
+        oracle.qr(Ah, min(64, cn))
+        dt_s = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": 3.0 * cn ** 3 / dt_s / 1e9, "unit": "GFLOP/s",
+                               "cores": oracle.num_threads(), "kind": "oracle",
+                               "sample": f"FP64 QR n={cn}, s=64, leading block of the input"}
+    print(json.dumps(out))
+    h.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -740,12 +843,18 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip sweeps and accuracy figures")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--mode", choices=["chol", "update", "mixed", "batched", "served", "strassen"],
+    ap.add_argument("--mode", choices=["chol", "update", "mixed", "batched", "served", "strassen",
+                                       "qr"],
                     default="chol",
                     help="chol: the benchmark line; update: the tensor-core rank-s update "
                          "alone; mixed: FP64 vs mixed-precision time to solution")
     ap.add_argument("--ks", default="256,512,1024,2048")
+    ap.add_argument("--qr-steps", default="32,64,128,256")
+    ap.add_argument("--qr-inner", default="8,16,32")
     ap.add_argument("--update-dtype", default="mix_bf16")
+    ap.add_argument("--tc-modes", default="1,2",
+                    help="update mode: tensor-core kernel variants to time (1 one CTA per tile, "
+                         "2 CTA pairs with pair MMAs)")
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--s-f64", type=int, default=256)
     ap.add_argument("--s-mixed", type=int, default=1024)
@@ -766,6 +875,8 @@ def main():
         return run_batched(args)
     if args.mode == "served":
         return run_served(args)
+    if args.mode == "qr":
+        return run_qr(args)
     if args.mode == "strassen":
         return run_strassen(args)
     return run_ours(args)

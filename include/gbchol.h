@@ -120,8 +120,12 @@ typedef enum gb_option {
   GB_OPT_USE_GRAPHS = 2,    /* 1: replay a captured CUDA graph of the whole
                                block loop for repeated (n, s, dtype, ld)
                                calls on device buffers (default 1).          */
-  GB_OPT_TC_UPDATE = 3,     /* 1: mixed dtypes use the tcgen05 tensor-core
-                               update (default); 0: the SIMT FP32 update.   */
+  GB_OPT_TC_UPDATE = 3,     /* mixed dtypes' update: 2 (default) the
+                               tcgen05 tensor-core kernel on CTA pairs (two
+                               SMs) computing 256 x 256 tiles with pair MMAs;
+                               1 the same kernel with one CTA per 128 x 256
+                               tile; 0 the SIMT FP32 update.  Other values:
+                               error -3.                                     */
   GB_OPT_SPIN_LIMIT = 4,    /* limit of bounded device waits, in units of
                                100 ns of %globaltimer (default 2^26, ~6.7 s). */
   GB_OPT_PROFILE = 5,       /* 1: record CUDA events around every launch of
@@ -134,7 +138,7 @@ typedef enum gb_option {
                                the next s-block's columns, and the rest of it
                                runs on a second stream while the next block's
                                column steps proceed; 0: one stream.          */
-  GB_OPT_STRASSEN = 8       /* 1: the FP64/FP32 delayed updates use one level
+  GB_OPT_STRASSEN = 8,      /* 1: the FP64/FP32 delayed updates use one level
                                of Strassen's multiplication (7 half-size
                                products; the paper's practical variant, Sec. 2
                                timing paragraph): LU's update, and the
@@ -142,6 +146,11 @@ typedef enum gb_option {
                                (its diagonal halves stay classical); also
                                gb_rank_update without the lower mask.
                                Default 0.                                    */
+  GB_OPT_QR_INNER_STEP = 9  /* gb_qr_factor: columns per panel launch, each
+                               orthogonalised against the earlier ones of its
+                               inner block one at a time (default 16, range
+                               1..256; capped by s and by the panel's shared
+                               memory, 200 KiB per CTA for ceil(n/8) rows).  */
 } gb_option;
 
 gb_status gb_set_option(gb_handle *h, gb_option opt, int64_t value);
@@ -185,6 +194,37 @@ gb_status gb_chol_factor(gb_handle *h, int64_t n, int64_t s, gb_dtype dt, const 
  */
 gb_status gb_lu_factor(gb_handle *h, int64_t n, int64_t s, gb_dtype dt, const void *A,
                        int64_t lda, void *LU, int64_t ldlu, int *info, void *stream);
+
+/* ---------------------------------------------------------------------- QR */
+/*
+ * gb_qr_factor -- Algorithm 3 (fast QR with step s), arXiv:1812.02056
+ * Sec. 2: A = Q R with Q orthogonal and R upper triangular with a positive
+ * diagonal.  Column c of Q is column c of the working matrix made
+ * orthogonal to the columns of Q since the last checkpoint, one after the
+ * other, and normalised; every s columns the trailing columns lose their
+ * components along the last s columns of Q at once (C = B_Q^T B_M,
+ * M -= B_Q C); at the end R = Q^T A.  Inside a block of s columns the
+ * column steps run in inner blocks of b = min(s, GB_OPT_QR_INNER_STEP, the
+ * shared-memory limit of the panel kernel) columns (the paper's remark that
+ * s may vary, Sec. 2).
+ *
+ *  dt    GB_F64 (A, Q, R double) or GB_F32 (float); other dtypes:
+ *        GB_ERR_UNSUPPORTED.
+ *  A     n x n, leading dimension lda, read in full; must have full rank.
+ *  Q     n x n output, leading dimension ldq: the orthonormal columns.
+ *  R     n x n output, leading dimension ldr: Q^T A on and above the
+ *        diagonal, zeros below.
+ *  Q and R must not overlap A or each other (error -7 / -9): A is read
+ *  again for R after Q is complete.  Host or device pointers, as for
+ *  gb_chol_factor.
+ *  s     step (s >= 1; s >= n: no delayed projection; s = 0: 64).
+ *  info  0, or c + 1 (1-based) when the projected column c has zero (or
+ *        NaN) norm, i.e. A is rank deficient there; Q and R are then
+ *        unspecified from that column on.
+ */
+gb_status gb_qr_factor(gb_handle *h, int64_t n, int64_t s, gb_dtype dt, const void *A,
+                       int64_t lda, void *Q, int64_t ldq, void *R, int64_t ldr, int *info,
+                       void *stream);
 
 /* ------------------------------------------------------------------ solves */
 typedef struct gb_refine_opts {
@@ -449,6 +489,37 @@ gb_status gb_batched_plan(gb_handle *h, int64_t count, const int64_t *n, void *c
                           const int64_t *lda, void *const *L, const int64_t *ldl, gb_dtype dt,
                           int64_t s, void *stream);
 gb_status gb_batched_run(gb_handle *h, int *info, void *stream);
+
+/*
+ * gb_lu_factor_batched -- Algorithm 2 (pivot-free Crout LU with step s,
+ * arXiv:1812.02056 Sec. 2) applied independently to `count` matrices of
+ * possibly different orders, in ONE persistent launch, like
+ * gb_chol_factor_batched.  A matrix held whole in shared memory
+ * (n * ld <= S, ld = n rounded up to odd; S as above: FP64 n <= 118, FP32
+ * n <= 167) runs all of Algorithm 2 there; a larger one is first copied to
+ * LU and keeps an L panel (rows z..n-1) and a U panel (columns z..n-1) of the
+ * block in shared memory -- so its step is min(s, floor(S / (2 n))) -- and
+ * receives the delayed update of the trailing square in place in LU.
+ *
+ *  A[count]     device pointers to the inputs, read in full; each must have
+ *               nonzero leading principal minors.
+ *  LU[count]    device pointers to the outputs (LU[i] may equal A[i]), in
+ *               the compact form of gb_lu_factor.
+ *  ldlu[count]  leading dimensions of the outputs.
+ *  n, lda, dt, info, stream as for gb_chol_factor_batched; s >= 1, or 0 for
+ *  min(n, 32).  info[i] = c + 1 when L_cc of matrix i is zero or NaN.
+ */
+gb_status gb_lu_factor_batched(gb_handle *h, int64_t count, const int64_t *n, void *const *A,
+                               const int64_t *lda, void *const *LU, const int64_t *ldlu,
+                               gb_dtype dt, int64_t s, int *info, void *stream);
+
+/*
+ * gb_lu_batched_plan -- gb_batched_plan for Algorithm 2: the plan that the
+ * next gb_batched_run launches is the batched LU of gb_lu_factor_batched.
+ */
+gb_status gb_lu_batched_plan(gb_handle *h, int64_t count, const int64_t *n, void *const *A,
+                             const int64_t *lda, void *const *LU, const int64_t *ldlu,
+                             gb_dtype dt, int64_t s, void *stream);
 
 /*
  * gb_batched_tune -- the autotuner of the batched call: for every bucket of

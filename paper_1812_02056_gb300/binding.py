@@ -37,6 +37,7 @@ GB_OPT_PROFILE = 5
 GB_OPT_BATCHED_EXACT = 6
 GB_OPT_LOOKAHEAD = 7
 GB_OPT_STRASSEN = 8
+GB_OPT_QR_INNER_STEP = 9
 
 
 class GbError(RuntimeError):
@@ -87,6 +88,7 @@ SIGNATURES = {
     "gb_get_option": (_I32, [_P, _I32, ctypes.POINTER(_I64)]),
     "gb_chol_factor": (_I32, [_P, _I64, _I64, _I32, _P, _I64, _P, _I64, _P, _P]),
     "gb_lu_factor": (_I32, [_P, _I64, _I64, _I32, _P, _I64, _P, _I64, _P, _P]),
+    "gb_qr_factor": (_I32, [_P, _I64, _I64, _I32, _P, _I64, _P, _I64, _P, _I64, _P, _P]),
     "gb_chol_solve": (_I32, [_P, _I64, _I64, _I32, _P, _I64, _P, _I64, _P, _I64, _P, _I64,
                              ctypes.POINTER(RefineOpts), ctypes.POINTER(SolveStats), _P]),
     "gb_lu_solve": (_I32, [_P, _I64, _I64, _I32, _P, _I64, _P, _I64, _P, _I64, _P, _I64,
@@ -95,6 +97,8 @@ SIGNATURES = {
                                  ctypes.POINTER(_D), _P]),
     "gb_chol_factor_batched": (_I32, [_P, _I64, _P, _P, _P, _P, _P, _I32, _I64, _P, _P]),
     "gb_batched_plan": (_I32, [_P, _I64, _P, _P, _P, _P, _P, _I32, _I64, _P]),
+    "gb_lu_factor_batched": (_I32, [_P, _I64, _P, _P, _P, _P, _P, _I32, _I64, _P, _P]),
+    "gb_lu_batched_plan": (_I32, [_P, _I64, _P, _P, _P, _P, _P, _I32, _I64, _P]),
     "gb_batched_run": (_I32, [_P, _P, _P]),
     "gb_chol_solve_noalloc": (_I32, [_I64, _I64, _I32, _P, _I64, _P, _I64, _P, _I64, _P]),
     "gb_rank_update": (_I32, [_P, _I32, _I32, _I32, _I64, _I64, _I64, _P, _I64, _P, _I64, _P,
@@ -253,6 +257,10 @@ class Handle:
         return self.lib.gb_lu_factor(self.h, n, s, dt, _ptr(A), lda, _ptr(LU), ldlu, _ptr(info),
                                      _stream_ptr(stream))
 
+    def gb_qr_factor(self, n, s, dt, A, lda, Q, ldq, R, ldr, info, stream=None) -> int:
+        return self.lib.gb_qr_factor(self.h, n, s, dt, _ptr(A), lda, _ptr(Q), ldq, _ptr(R), ldr,
+                                     _ptr(info), _stream_ptr(stream))
+
     def _solve(self, fn, n, nrhs, dt, F, ldf, A, lda, B, ldb, X, ldx, tol, max_iter, stream):
         opts = RefineOpts(tol, max_iter)
         stats = SolveStats()
@@ -287,6 +295,18 @@ class Handle:
         return self.lib.gb_batched_plan(self.h, count, _ptr(n_arr), _ptr(a_arr), _ptr(lda_arr),
                                         _ptr(l_arr), _ptr(ldl_arr), dt, s, _stream_ptr(stream))
 
+    def gb_lu_factor_batched(self, count, n_arr, a_arr, lda_arr, lu_arr, ldlu_arr, dt, s, info,
+                             stream=None):
+        return self.lib.gb_lu_factor_batched(self.h, count, _ptr(n_arr), _ptr(a_arr),
+                                             _ptr(lda_arr), _ptr(lu_arr), _ptr(ldlu_arr), dt, s,
+                                             _ptr(info), _stream_ptr(stream))
+
+    def gb_lu_batched_plan(self, count, n_arr, a_arr, lda_arr, lu_arr, ldlu_arr, dt, s,
+                           stream=None):
+        return self.lib.gb_lu_batched_plan(self.h, count, _ptr(n_arr), _ptr(a_arr), _ptr(lda_arr),
+                                           _ptr(lu_arr), _ptr(ldlu_arr), dt, s,
+                                           _stream_ptr(stream))
+
     def gb_batched_run(self, info, stream=None):
         return self.lib.gb_batched_run(self.h, _ptr(info), _stream_ptr(stream))
 
@@ -296,6 +316,16 @@ class Handle:
     def chol_factor_batched(self, mats, s: int = 0, dtype: str = "f64", outs=None, stream=None):
         """Factor a list of square CUDA tensors (in place unless `outs` is
         given) in one launch; returns the per-matrix info as a numpy array."""
+        return self._factor_batched(self.gb_chol_factor_batched, "gb_chol_factor_batched", mats,
+                                    s, dtype, outs, stream)
+
+    def lu_factor_batched(self, mats, s: int = 0, dtype: str = "f64", outs=None, stream=None):
+        """Batched Algorithm 2: compact LU of each square CUDA tensor (in place
+        unless `outs` is given); returns the per-matrix info."""
+        return self._factor_batched(self.gb_lu_factor_batched, "gb_lu_factor_batched", mats, s,
+                                    dtype, outs, stream)
+
+    def _factor_batched(self, fn, name, mats, s, dtype, outs, stream):
         import numpy as np
         import torch
         cnt = len(mats)
@@ -306,8 +336,7 @@ class Handle:
         l_arr = np.array([m.data_ptr() for m in outs], dtype=np.uint64)
         ldl = np.array([max(1, m.stride(0)) for m in outs], dtype=np.int64)
         info = torch.zeros(max(cnt, 1), dtype=torch.int32, device=mats[0].device if mats else "cuda")
-        check(self.gb_chol_factor_batched(cnt, n_arr, a_arr, lda, l_arr, ldl, DTYPES[dtype], s,
-                                          info, stream), "gb_chol_factor_batched")
+        check(fn(cnt, n_arr, a_arr, lda, l_arr, ldl, DTYPES[dtype], s, info, stream), name)
         torch.cuda.synchronize()
         return info[:cnt].cpu().numpy()
 
@@ -339,6 +368,19 @@ class Handle:
         check(self.gb_lu_factor(n, s, dt, A, _ld(A) if n else 1, LU, _ld(LU) if n else 1, info,
                                 stream), "gb_lu_factor")
         return LU, info
+
+    def qr_factor(self, A, s: int, dtype: str = "f64", stream=None):
+        """Algorithm 3: ``A = Q R``; returns ``(Q, R, info)``."""
+        import torch
+        n = A.shape[0]
+        dt = DTYPES[dtype]
+        ttype = torch.float64 if dt == GB_F64 else torch.float32
+        Q = torch.empty((n, n), dtype=ttype, device=A.device)
+        R = torch.empty((n, n), dtype=ttype, device=A.device)
+        info = torch.zeros(1, dtype=torch.int32, device=A.device)
+        check(self.gb_qr_factor(n, s, dt, A, _ld(A) if n else 1, Q, _ld(Q) if n else 1, R,
+                                _ld(R) if n else 1, info, stream), "gb_qr_factor")
+        return Q, R, info
 
     def chol_solve(self, L, B, dtype: str = "f64", A=None, tol=1e-14, max_iter=30, stream=None,
                    allow_not_converged=False):

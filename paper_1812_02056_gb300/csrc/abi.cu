@@ -276,6 +276,7 @@ gb_status chol_update(gb_handle *h, gb_dtype dt, T *C, const T *X, const T *Y, i
       a.status = status;
       a.err = h->d_err;
       a.spin_limit = h->spin_limit;
+      a.cluster = h->tc_update;
       gb_status ws = ws_reserve(h, pack_slot, tc_pack_bytes(M, N, K, false, a.split), st);
       if (ws != GB_OK) return ws;
       a.pack = h->ws[pack_slot].ptr;
@@ -427,6 +428,7 @@ gb_status lu_update(gb_handle *h, gb_dtype dt, T *C, const T *X, const T *Y, int
       a.status = status;
       a.err = h->d_err;
       a.spin_limit = h->spin_limit;
+      a.cluster = h->tc_update;
       gb_status ws = ws_reserve(h, pack_slot, tc_pack_bytes(M, N, K, true, a.split), st);
       if (ws != GB_OK) return ws;
       a.pack = h->ws[pack_slot].ptr;
@@ -551,6 +553,120 @@ gb_status lu_blocked_on(gb_handle *h, int64_t n, int64_t s, T *W, int64_t ld, in
 }
 
 // Common driver of gb_chol_factor / gb_lu_factor.
+// ------------------------------------------------------------- Algorithm 3
+// Fast QR with step s: Q (n x n, ldq) holds the working matrix M and ends
+// as Q; every s columns the trailing columns lose their components along
+// the block just finished (C := B_Q^T B_M, M -= B_Q C).  Inside a block the
+// column steps run in inner blocks of b columns (the paper's remark that s
+// may vary, Sec. 2): the panel kernel orthogonalises b columns one after
+// the other, and the rest of the block's columns receive the same two-GEMM
+// projection for those b columns.  Finally R := Q^T A (upper triangle).
+template <typename T>
+gb_status qr_blocked(gb_handle *h, int64_t n, int64_t s, const T *A, int64_t lda, T *Q,
+                     int64_t ldq, T *R, int64_t ldr, int *status, cudaStream_t st) {
+  const int64_t bmax = qr_panel_max_cols(n, sizeof(T));
+  if (bmax < 1) return GB_ERR_UNSUPPORTED;
+  const int64_t b =
+      std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(s, (int64_t)h->qr_inner), bmax));
+  const size_t esz = sizeof(T);
+  const int64_t sw = std::min(s, n);
+  gb_status r = ws_reserve(h, WS_QR, (size_t)sw * (size_t)n * esz + 256, st);
+  if (r != GB_OK) return r;
+  const size_t wbytes = gemm_tn_work_bytes(esz, h->sm_count);
+  if ((r = ws_reserve(h, WS_PANEL2, wbytes, st)) != GB_OK) return r;
+  T *Cw = reinterpret_cast<T *>(h->ws[WS_QR].ptr);
+  void *work = h->ws[WS_PANEL2].ptr;
+  for (int64_t z = 0; z < n; z += s) {
+    const int64_t sb = std::min(s, n - z);
+    for (int64_t z2 = z; z2 < z + sb; z2 += b) {
+      const int64_t bb = std::min(b, z + sb - z2);
+      {
+        PhaseTimer tp(h, st, GB_PHASE_PANEL, 4.0 * (double)n * (double)bb * (double)bb, 0.0);
+        GB_CUDA_TRY(launch_qr_panel<T>(Q, ldq, n, z2, (int)bb, status, st));
+      }
+      const int64_t rest = z + sb - (z2 + bb);
+      if (rest > 0) {
+        PhaseTimer ti(h, st, GB_PHASE_INNER, 4.0 * (double)n * (double)bb * (double)rest,
+                      3.0 * (double)n * (double)rest * (double)esz);
+        GB_CUDA_TRY(launch_gemm_tn<T>(Cw, rest, Q + z2, ldq, Q + z2 + bb, ldq, bb, rest, n, false,
+                                      status, work, h->ws[WS_PANEL2].bytes, h->sm_count, st));
+        GB_CUDA_TRY(launch_update_simt<T>(Q + z2 + bb, ldq, Q + z2, ldq, Cw, rest, n, rest, bb,
+                                          true, false, 0, status, st));
+      }
+    }
+    const int64_t m = n - z - sb;
+    if (m > 0) {
+      PhaseTimer tu(h, st, GB_PHASE_UPDATE, 4.0 * (double)n * (double)sb * (double)m,
+                    3.0 * (double)n * (double)m * (double)esz);
+      GB_CUDA_TRY(launch_gemm_tn<T>(Cw, m, Q + z, ldq, Q + z + sb, ldq, sb, m, n, false, status,
+                                    work, h->ws[WS_PANEL2].bytes, h->sm_count, st));
+      GB_CUDA_TRY(launch_update_simt<T>(Q + z + sb, ldq, Q + z, ldq, Cw, m, n, m, sb, true, false,
+                                        0, status, st));
+    }
+  }
+  PhaseTimer tr(h, st, GB_PHASE_UPDATE, (double)n * (double)n * (double)(n + 1),
+                2.0 * (double)n * (double)n * (double)esz);
+  GB_CUDA_TRY(launch_gemm_tn<T>(R, ldr, Q, ldq, A, lda, n, n, n, true, status, nullptr, 0,
+                                h->sm_count, st));
+  return GB_OK;
+}
+
+gb_status qr_common(gb_handle *h, int64_t n, int64_t s, gb_dtype dt, const void *A, int64_t lda,
+                    void *Q, int64_t ldq, void *R, int64_t ldr, int *info, void *stream) {
+  if (!h) return -1;
+  if (n < 0 || n > (int64_t)1 << 30) return -2;
+  if (s < 0) return -3;
+  if (!valid_dtype(dt)) return -4;
+  if (dt != GB_F64 && dt != GB_F32) return GB_ERR_UNSUPPORTED;
+  if (n > 0 && !A) return -5;
+  if (lda < std::max<int64_t>(1, n)) return -6;
+  if (n > 0 && !Q) return -7;
+  if (ldq < std::max<int64_t>(1, n)) return -8;
+  if (n > 0 && !R) return -9;
+  if (ldr < std::max<int64_t>(1, n)) return -10;
+  if (!info) return -11;
+  const size_t esz = elem_size_input(dt);
+  auto span = [&](const void *p, int64_t ld) {
+    const char *b = (const char *)p;
+    return std::make_pair(b, b + ((size_t)std::max<int64_t>(n - 1, 0) * ld + n) * esz);
+  };
+  if (n > 0) {  // Q and R are written while A is still read
+    auto a = span(A, lda), q = span(Q, ldq), rr = span(R, ldr);
+    if (q.first < a.second && a.first < q.second) return -7;
+    if (rr.first < a.second && a.first < rr.second) return -9;
+    if (rr.first < q.second && q.first < rr.second) return -9;
+  }
+  DeviceGuard g(h->device);
+  std::lock_guard<std::mutex> lk(h->mu);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (s == 0) s = 64;
+  InfoWord iw;
+  gb_status r = iw.init(h, info, st);
+  if (r != GB_OK) return r;
+  if (n == 0) return iw.finish(st);
+  Staged sa, sq, sr;
+  if ((r = sa.take(A, n, n, lda, esz, true, false, st)) != GB_OK) return r;
+  if ((r = sq.take(Q, n, n, ldq, esz, false, true, st)) != GB_OK) return r;
+  if ((r = sr.take(R, n, n, ldr, esz, false, true, st)) != GB_OK) return r;
+  if (dt == GB_F64) {
+    GB_CUDA_TRY((launch_copy_matrix<double, double>((const double *)sa.dev, sa.ldd,
+                                                    (double *)sq.dev, sq.ldd, n, false, st)));
+    r = qr_blocked<double>(h, n, s, (const double *)sa.dev, sa.ldd, (double *)sq.dev, sq.ldd,
+                           (double *)sr.dev, sr.ldd, iw.dev, st);
+  } else {
+    GB_CUDA_TRY((launch_copy_matrix<float, float>((const float *)sa.dev, sa.ldd, (float *)sq.dev,
+                                                  sq.ldd, n, false, st)));
+    r = qr_blocked<float>(h, n, s, (const float *)sa.dev, sa.ldd, (float *)sq.dev, sq.ldd,
+                          (float *)sr.dev, sr.ldd, iw.dev, st);
+  }
+  if (r != GB_OK) return r;
+  if ((r = sq.finish()) != GB_OK) return r;
+  if ((r = sr.finish()) != GB_OK) return r;
+  if ((r = iw.finish(st)) != GB_OK) return r;
+  if (sa.on_host() || sq.on_host() || sr.on_host()) GB_CUDA_TRY(cudaStreamSynchronize(st));
+  return GB_OK;
+}
+
 gb_status factor_common(bool is_lu, gb_handle *h, int64_t n, int64_t s, gb_dtype dt,
                         const void *A, int64_t lda, void *L, int64_t ldl, int *info,
                         void *stream) {
@@ -901,7 +1017,10 @@ gb_status gb_set_option(gb_handle *h, gb_option opt, int64_t v) {
       h->inner_step = (int)v;
       return GB_OK;
     case GB_OPT_USE_GRAPHS: h->use_graphs = v ? 1 : 0; return GB_OK;
-    case GB_OPT_TC_UPDATE: h->tc_update = v ? 1 : 0; return GB_OK;
+    case GB_OPT_TC_UPDATE:
+      if (v < 0 || v > 2) return -3;
+      h->tc_update = (int)v;
+      return GB_OK;
     case GB_OPT_SPIN_LIMIT:
       if (v < 1) return -3;
       h->spin_limit = v;
@@ -910,6 +1029,10 @@ gb_status gb_set_option(gb_handle *h, gb_option opt, int64_t v) {
     case GB_OPT_BATCHED_EXACT: h->batched_exact = v ? 1 : 0; return GB_OK;
     case GB_OPT_LOOKAHEAD: h->lookahead = v ? 1 : 0; return GB_OK;
     case GB_OPT_STRASSEN: h->strassen = v ? 1 : 0; return GB_OK;
+    case GB_OPT_QR_INNER_STEP:
+      if (v < 1 || v > 256) return -3;
+      h->qr_inner = (int)v;
+      return GB_OK;
     default: return -2;
   }
 }
@@ -926,6 +1049,7 @@ gb_status gb_get_option(gb_handle *h, gb_option opt, int64_t *v) {
     case GB_OPT_BATCHED_EXACT: *v = h->batched_exact; return GB_OK;
     case GB_OPT_LOOKAHEAD: *v = h->lookahead; return GB_OK;
     case GB_OPT_STRASSEN: *v = h->strassen; return GB_OK;
+    case GB_OPT_QR_INNER_STEP: *v = h->qr_inner; return GB_OK;
     default: return -2;
   }
 }
@@ -938,6 +1062,12 @@ gb_status gb_chol_factor(gb_handle *h, int64_t n, int64_t s, gb_dtype dt, const 
 gb_status gb_lu_factor(gb_handle *h, int64_t n, int64_t s, gb_dtype dt, const void *A,
                        int64_t lda, void *LU, int64_t ldlu, int *info, void *stream) {
   return factor_common(true, h, n, s, dt, A, lda, LU, ldlu, info, stream);
+}
+
+gb_status gb_qr_factor(gb_handle *h, int64_t n, int64_t s, gb_dtype dt, const void *A,
+                       int64_t lda, void *Q, int64_t ldq, void *R, int64_t ldr, int *info,
+                       void *stream) {
+  return qr_common(h, n, s, dt, A, lda, Q, ldq, R, ldr, info, stream);
 }
 
 gb_status gb_chol_solve(gb_handle *h, int64_t n, int64_t nrhs, gb_dtype factor_dt, const void *L,
@@ -1006,13 +1136,14 @@ int batched_default_step(const gb_handle *h, int dtype_index, int n) {
 // handle's batched workspace; remembered in h->plan.
 gb_status batched_upload(gb_handle *h, int64_t count, const int64_t *n, void *const *A,
                          const int64_t *lda, void *const *L, const int64_t *ldl, gb_dtype dt,
-                         const int *steps, cudaStream_t st) {
+                         const int *steps, cudaStream_t st, int lu = 0) {
   const int di = dt == GB_F64 ? 0 : 1;
   std::vector<int> order((size_t)count), nn((size_t)count), ss((size_t)count);
   for (int64_t i = 0; i < count; ++i) {
     order[i] = (int)i;
     nn[i] = (int)n[i];
-    ss[i] = steps ? steps[i] : batched_default_step(h, di, (int)n[i]);
+    // the tuned table is Cholesky's; LU takes the default rule
+    ss[i] = steps ? steps[i] : lu ? std::min((int)n[i], 32) : batched_default_step(h, di, (int)n[i]);
   }
   // longest processing time first: orders by n^3, descending
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return nn[a] > nn[b]; });
@@ -1044,6 +1175,7 @@ gb_status batched_upload(gb_handle *h, int64_t count, const int64_t *n, void *co
   p.L = (void *const *)(d + off_l);
   p.ldl = (const int64_t *)(d + off_ll);
   p.ticket = (int *)(d + off_t);
+  p.lu = lu;
   return GB_OK;
 }
 
@@ -1051,6 +1183,17 @@ gb_status batched_upload(gb_handle *h, int64_t count, const int64_t *n, void *co
 gb_status batched_launch(gb_handle *h, int *info_dev, cudaStream_t st) {
   const auto &p = h->plan;
   if (p.count <= 0) return GB_OK;
+  if (p.lu) {
+    if (p.dt == GB_F64)
+      GB_CUDA_TRY(launch_lu_batched_plan<double>(p.count, p.order, p.n, p.step, p.A, p.lda, p.L,
+                                                 p.ldl, info_dev, p.ticket, h->sm_count,
+                                                 h->batched_exact, st));
+    else
+      GB_CUDA_TRY(launch_lu_batched_plan<float>(p.count, p.order, p.n, p.step, p.A, p.lda, p.L,
+                                                p.ldl, info_dev, p.ticket, h->sm_count,
+                                                h->batched_exact, st));
+    return GB_OK;
+  }
   if (p.dt == GB_F64)
     GB_CUDA_TRY(launch_chol_batched_plan<double>(p.count, p.order, p.n, p.step, p.A, p.lda, p.L,
                                                  p.ldl, info_dev, p.ticket, h->sm_count,
@@ -1087,9 +1230,12 @@ gb_status batched_check(gb_handle *h, int64_t count, const int64_t *n, void *con
 }  // namespace
 }  // namespace gb
 
-extern "C" gb_status gb_batched_plan(gb_handle *h, int64_t count, const int64_t *n,
-                                     void *const *A, const int64_t *lda, void *const *L,
-                                     const int64_t *ldl, gb_dtype dt, int64_t s, void *stream) {
+namespace gb {
+namespace {
+
+gb_status batched_plan_common(gb_handle *h, int64_t count, const int64_t *n, void *const *A,
+                              const int64_t *lda, void *const *L, const int64_t *ldl, gb_dtype dt,
+                              int64_t s, void *stream, int lu) {
   gb_status r = batched_check(h, count, n, A, lda, L, ldl, dt, s);
   if (r != GB_OK) return r;
   DeviceGuard g(h->device);
@@ -1101,22 +1247,12 @@ extern "C" gb_status gb_batched_plan(gb_handle *h, int64_t count, const int64_t 
     return GB_OK;
   }
   return batched_upload(h, count, n, A, lda, L, ldl, dt, s > 0 ? steps.data() : nullptr,
-                        (cudaStream_t)stream);
+                        (cudaStream_t)stream, lu);
 }
 
-extern "C" gb_status gb_batched_run(gb_handle *h, int *info, void *stream) {
-  if (!h) return -1;
-  if (h->plan.count > 0 && !info) return -2;
-  if (h->plan.count > 0 && !is_device_ptr(info)) return -2;
-  DeviceGuard g(h->device);
-  std::lock_guard<std::mutex> lk(h->mu);
-  return batched_launch(h, info, (cudaStream_t)stream);
-}
-
-extern "C" gb_status gb_chol_factor_batched(gb_handle *h, int64_t count, const int64_t *n,
-                                            void *const *A, const int64_t *lda, void *const *L,
-                                            const int64_t *ldl, gb_dtype dt, int64_t s, int *info,
-                                            void *stream) {
+gb_status factor_batched_common(gb_handle *h, int64_t count, const int64_t *n, void *const *A,
+                                const int64_t *lda, void *const *L, const int64_t *ldl,
+                                gb_dtype dt, int64_t s, int *info, void *stream, int lu) {
   gb_status r = batched_check(h, count, n, A, lda, L, ldl, dt, s);
   if (r != GB_OK) return r;
   if (count > 0 && !info) return -10;
@@ -1126,8 +1262,8 @@ extern "C" gb_status gb_chol_factor_batched(gb_handle *h, int64_t count, const i
   cudaStream_t st = (cudaStream_t)stream;
   std::vector<int> steps;
   if (s > 0) steps.assign((size_t)count, (int)std::min<int64_t>(s, 1 << 20));
-  if ((r = batched_upload(h, count, n, A, lda, L, ldl, dt, s > 0 ? steps.data() : nullptr, st)) !=
-      GB_OK)
+  if ((r = batched_upload(h, count, n, A, lda, L, ldl, dt, s > 0 ? steps.data() : nullptr, st,
+                          lu)) != GB_OK)
     return r;
   int *info_dev = info;
   int *info_scratch = nullptr;
@@ -1148,6 +1284,45 @@ extern "C" gb_status gb_chol_factor_batched(gb_handle *h, int64_t count, const i
   }
   if (info_scratch) cudaFreeAsync(info_scratch, st);
   return r;
+}
+
+}  // namespace
+}  // namespace gb
+
+extern "C" gb_status gb_batched_plan(gb_handle *h, int64_t count, const int64_t *n,
+                                     void *const *A, const int64_t *lda, void *const *L,
+                                     const int64_t *ldl, gb_dtype dt, int64_t s, void *stream) {
+  return batched_plan_common(h, count, n, A, lda, L, ldl, dt, s, stream, 0);
+}
+
+extern "C" gb_status gb_lu_batched_plan(gb_handle *h, int64_t count, const int64_t *n,
+                                        void *const *A, const int64_t *lda, void *const *LU,
+                                        const int64_t *ldlu, gb_dtype dt, int64_t s,
+                                        void *stream) {
+  return batched_plan_common(h, count, n, A, lda, LU, ldlu, dt, s, stream, 1);
+}
+
+extern "C" gb_status gb_batched_run(gb_handle *h, int *info, void *stream) {
+  if (!h) return -1;
+  if (h->plan.count > 0 && !info) return -2;
+  if (h->plan.count > 0 && !is_device_ptr(info)) return -2;
+  DeviceGuard g(h->device);
+  std::lock_guard<std::mutex> lk(h->mu);
+  return batched_launch(h, info, (cudaStream_t)stream);
+}
+
+extern "C" gb_status gb_chol_factor_batched(gb_handle *h, int64_t count, const int64_t *n,
+                                            void *const *A, const int64_t *lda, void *const *L,
+                                            const int64_t *ldl, gb_dtype dt, int64_t s, int *info,
+                                            void *stream) {
+  return factor_batched_common(h, count, n, A, lda, L, ldl, dt, s, info, stream, 0);
+}
+
+extern "C" gb_status gb_lu_factor_batched(gb_handle *h, int64_t count, const int64_t *n,
+                                          void *const *A, const int64_t *lda, void *const *LU,
+                                          const int64_t *ldlu, gb_dtype dt, int64_t s, int *info,
+                                          void *stream) {
+  return factor_batched_common(h, count, n, A, lda, LU, ldlu, dt, s, info, stream, 1);
 }
 
 extern "C" gb_status gb_batched_tune(gb_handle *h, gb_dtype dt, int64_t n_max, int *steps_out,
@@ -1315,6 +1490,7 @@ extern "C" gb_status gb_rank_update(gb_handle *h, gb_dtype dt, int lower, int y_
     a.status = status;
     a.err = h->d_err;
     a.spin_limit = h->spin_limit;
+    a.cluster = h->tc_update;
     gb_status r = ws_reserve(h, WS_PANEL, tc_pack_bytes(M, N, K, nn, split_of(dt)), st);
     if (r != GB_OK) return r;
     a.pack = h->ws[WS_PANEL].ptr;

@@ -14,6 +14,12 @@
 // Every sum runs in ascending k, one product at a time.  With `exact` set the
 // kernel uses separately rounded multiply and subtract (no FMA), so its FP64
 // result is the same bits as the oracle's literal mode.
+//
+// Batched Algorithm 2 (pivot-free Crout LU, L lower, U unit upper, stored
+// compactly) follows the same plan: the whole matrix in shared memory when
+// it fits, else an L panel (rows [z, n) x the block's columns) and a U panel
+// (the block's rows x columns [z, n)) in shared memory and the delayed
+// update of the trailing square in place in the output.
 #include <math.h>
 
 #include <algorithm>
@@ -163,6 +169,123 @@ __device__ int chol_panel_path(T *A, int64_t lda, int n, int s, T *P, T *red) {
   return 0;
 }
 
+
+// ------------------------------------------------- Algorithm 2, whole matrix in shared memory
+// W: n x n working matrix, leading dimension ld.  L_ic (i >= c) overwrites
+// W[i][c], U_ci (i > c) overwrites W[c][i]; U's unit diagonal is implied.
+template <typename T, bool EXACT>
+__device__ int lu_in_smem(T *W, int n, int ld, int s) {
+  constexpr bool exact = EXACT;
+  const int tid = threadIdx.x;
+  int z = 0;
+  for (int c = 0; c < n; ++c) {
+    if (c == z + s) {
+      // delayed update of the trailing square: W_ij -= S_ij, S_ij = sum_k L_ik U_kj
+      for (int i = c + (tid >> 5); i < n; i += BT / 32) {
+        const T *Li = W + (int64_t)i * ld;
+        for (int j = c + (tid & 31); j < n; j += 32) {
+          T sij = T(0);
+#pragma unroll 4
+          for (int k = z; k < c; ++k) sij = madd(sij, Li[k], W[(int64_t)k * ld + j], exact);
+          W[(int64_t)i * ld + j] = W[(int64_t)i * ld + j] - sij;
+        }
+      }
+      z = c;
+      __syncthreads();
+    }
+    // column c of L (rows i >= c) and the numerators of row c of U (j > c)
+    const int m = n - c;
+    for (int t = tid; t < 2 * m - 1; t += BT) {
+      if (t < m) {
+        const int i = c + t;
+        const T *Li = W + (int64_t)i * ld;
+        T v = Li[c];
+#pragma unroll 4
+        for (int k = z; k < c; ++k) v = msub(v, Li[k], W[(int64_t)k * ld + c], exact);
+        W[(int64_t)i * ld + c] = v;
+      } else {
+        const int j = c + 1 + (t - m);
+        const T *Lc = W + (int64_t)c * ld;
+        T u = Lc[j];
+#pragma unroll 4
+        for (int k = z; k < c; ++k) u = msub(u, Lc[k], W[(int64_t)k * ld + j], exact);
+        W[(int64_t)c * ld + j] = u;
+      }
+    }
+    __syncthreads();
+    const T lcc = W[(int64_t)c * ld + c];
+    if (lcc == T(0) || lcc != lcc) return c + 1;  // uniform: every thread read the same lcc
+    for (int j = c + 1 + tid; j < n; j += BT) W[(int64_t)c * ld + j] = ddiv(W[(int64_t)c * ld + j], lcc);
+    __syncthreads();
+  }
+  return 0;
+}
+
+// ------------------------------------------------- Algorithm 2, panels in shared memory
+// A: the n x n working matrix in global memory (the output), in place.
+// PL: rows [z, n) x columns [z, z + sb), leading dimension s (L panel);
+// PU: rows [z, z + sb) x columns [z, n), leading dimension n (U panel).
+// Inside the diagonal block, L is read from PL (on and below the diagonal)
+// and U from PU (above it).
+template <typename T, bool EXACT>
+__device__ int lu_panel_path(T *A, int64_t lda, int n, int s, T *PL, T *PU) {
+  constexpr bool exact = EXACT;
+  const int tid = threadIdx.x;
+  for (int z = 0; z < n; z += s) {
+    const int sb = min(s, n - z);
+    const int rows = n - z;
+    for (int r = tid >> 5; r < rows; r += BT / 32)
+      for (int q = tid & 31; q < sb; q += 32) PL[(int64_t)r * s + q] = A[(int64_t)(z + r) * lda + z + q];
+    for (int r = tid >> 5; r < sb; r += BT / 32)
+      for (int q = tid & 31; q < rows; q += 32) PU[(int64_t)r * n + q] = A[(int64_t)(z + r) * lda + z + q];
+    __syncthreads();
+    for (int c = 0; c < sb; ++c) {  // column z + c, local index c
+      const int m = rows - c;
+      for (int t = tid; t < 2 * m - 1; t += BT) {
+        if (t < m) {
+          const int r = c + t;
+          T *Pr = PL + (int64_t)r * s;
+          T v = Pr[c];
+#pragma unroll 4
+          for (int k = 0; k < c; ++k) v = msub(v, Pr[k], PU[(int64_t)k * n + c], exact);
+          Pr[c] = v;
+        } else {
+          const int q = c + 1 + (t - m);
+          const T *Pc = PL + (int64_t)c * s;
+          T u = PU[(int64_t)c * n + q];
+#pragma unroll 4
+          for (int k = 0; k < c; ++k) u = msub(u, Pc[k], PU[(int64_t)k * n + q], exact);
+          PU[(int64_t)c * n + q] = u;
+        }
+      }
+      __syncthreads();
+      const T lcc = PL[(int64_t)c * s + c];
+      if (lcc == T(0) || lcc != lcc) return z + c + 1;
+      for (int q = c + 1 + tid; q < rows; q += BT) PU[(int64_t)c * n + q] = ddiv(PU[(int64_t)c * n + q], lcc);
+      __syncthreads();
+    }
+    for (int r = tid >> 5; r < rows; r += BT / 32)
+      for (int q = tid & 31; q < sb; q += 32)
+        if (q <= r) A[(int64_t)(z + r) * lda + z + q] = PL[(int64_t)r * s + q];
+    for (int r = tid >> 5; r < sb; r += BT / 32)
+      for (int q = r + 1 + (tid & 31); q < rows; q += 32) A[(int64_t)(z + r) * lda + z + q] = PU[(int64_t)r * n + q];
+    // delayed update of the trailing square: rows/cols [z+sb, n)
+    const int mt = n - z - sb;
+    for (int r = tid >> 5; r < mt; r += BT / 32) {
+      const T *Pi = PL + (int64_t)(sb + r) * s;
+      for (int q = tid & 31; q < mt; q += 32) {
+        T sij = T(0);
+#pragma unroll 4
+        for (int k = 0; k < sb; ++k) sij = madd(sij, Pi[k], PU[(int64_t)k * n + sb + q], exact);
+        T *a = A + (int64_t)(z + sb + r) * lda + z + sb + q;
+        *a = *a - sij;
+      }
+    }
+    __syncthreads();
+  }
+  return 0;
+}
+
 struct Plan {
   int count;
   const int *order;
@@ -215,6 +338,59 @@ __global__ void __launch_bounds__(BT, 2) batched_chol_kernel(Plan plan, int64_t 
         __syncthreads();
         const int sp = (int)min64(s, smem_elems / n);  // panel width that fits
         info = chol_panel_path<T, EXACT>(L, ldl, n, max(1, sp), buf, red);
+        __syncthreads();
+      }
+    }
+    if (threadIdx.x == 0) plan.info[idx] = info;
+    __syncthreads();  // s_idx is rewritten next iteration
+  }
+}
+
+
+// Leading dimension of a matrix held whole in shared memory: odd, so that
+// threads walking down a column hit different banks.
+__device__ __host__ inline int64_t lu_smem_ld(int n) { return (n & 1) ? n : n + 1; }
+
+template <typename T, bool EXACT>
+__global__ void __launch_bounds__(BT, 2) batched_lu_kernel(Plan plan, int64_t smem_elems) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *buf = reinterpret_cast<T *>(smem_raw);
+  __shared__ int s_idx;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const int t = atomicAdd(plan.ticket, 1);
+      s_idx = t < plan.count ? plan.order[t] : -1;
+    }
+    __syncthreads();
+    const int idx = s_idx;
+    if (idx < 0) break;
+    const int n = plan.n[idx];
+    const int s = max(1, plan.step[idx]);
+    const T *A = reinterpret_cast<const T *>(plan.A[idx]);
+    const int64_t lda = plan.lda[idx];
+    T *LU = reinterpret_cast<T *>(plan.L[idx]);
+    const int64_t ldo = plan.ldl[idx];
+    int info = 0;
+    if (n > 0) {
+      const int64_t ld = lu_smem_ld(n);
+      if ((int64_t)n * ld <= smem_elems) {
+        for (int r = threadIdx.x >> 5; r < n; r += BT / 32)
+          for (int q = threadIdx.x & 31; q < n; q += 32) buf[r * ld + q] = A[(int64_t)r * lda + q];
+        __syncthreads();
+        info = lu_in_smem<T, EXACT>(buf, n, (int)ld, min(s, n));
+        __syncthreads();
+        for (int r = threadIdx.x >> 5; r < n; r += BT / 32)
+          for (int q = threadIdx.x & 31; q < n; q += 32) LU[(int64_t)r * ldo + q] = buf[r * ld + q];
+      } else {
+        // the panel path works in place in the output: copy A first
+        if (LU != A)
+          for (int r = threadIdx.x >> 5; r < n; r += BT / 32)
+            for (int q = threadIdx.x & 31; q < n; q += 32) LU[(int64_t)r * ldo + q] = A[(int64_t)r * lda + q];
+        __syncthreads();
+        const int sp = (int)min64(s, smem_elems / (2 * (int64_t)n));  // both panels fit
+        T *PL = buf;
+        T *PU = buf + (int64_t)n * max(1, sp);
+        info = lu_panel_path<T, EXACT>(LU, ldo, n, max(1, sp), PL, PU);
         __syncthreads();
       }
     }
@@ -280,5 +456,39 @@ template cudaError_t launch_chol_batched_plan<float>(int, const int *, const int
                                                      void *const *, const int64_t *, void *const *,
                                                      const int64_t *, int *, int *, int, int,
                                                      cudaStream_t);
+
+template <typename T>
+cudaError_t launch_lu_batched_plan(int count, const int *order, const int *n, const int *step,
+                                   void *const *A, const int64_t *lda, void *const *LU,
+                                   const int64_t *ldlu, int *info, int *ticket, int sm_count,
+                                   int exact, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  const size_t smem = batched_smem_bytes();
+  static cudaError_t attr0 = cudaFuncSetAttribute(
+      batched_lu_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  static cudaError_t attr1 = cudaFuncSetAttribute(
+      batched_lu_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (attr0 != cudaSuccess) return attr0;
+  if (attr1 != cudaSuccess) return attr1;
+  cudaError_t e = cudaMemsetAsync(ticket, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  Plan p{count, order, n, step, A, lda, LU, ldlu, info, ticket};
+  const int grid = std::min(count, 2 * sm_count);
+  if (exact)
+    batched_lu_kernel<T, true><<<grid, BT, smem, st>>>(p, (int64_t)(smem / sizeof(T)));
+  else
+    batched_lu_kernel<T, false><<<grid, BT, smem, st>>>(p, (int64_t)(smem / sizeof(T)));
+  count_launch();
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_lu_batched_plan<double>(int, const int *, const int *, const int *,
+                                                    void *const *, const int64_t *, void *const *,
+                                                    const int64_t *, int *, int *, int, int,
+                                                    cudaStream_t);
+template cudaError_t launch_lu_batched_plan<float>(int, const int *, const int *, const int *,
+                                                   void *const *, const int64_t *, void *const *,
+                                                   const int64_t *, int *, int *, int, int,
+                                                   cudaStream_t);
 
 }  // namespace gb

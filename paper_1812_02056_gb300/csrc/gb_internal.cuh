@@ -53,7 +53,8 @@ struct gb_handle {
   int sm_count = 0;
   int inner_step = 64;
   int use_graphs = 1;
-  int tc_update = 1;
+  int tc_update = 2;
+  int qr_inner = 16;          // inner step of the QR panel (GB_OPT_QR_INNER_STEP)
   int64_t spin_limit = 1 << 26;
   int *d_status = nullptr;   // scratch status word for host `info` pointers
   int *d_err = nullptr;      // device error word (DEV_ERR_*)
@@ -61,7 +62,7 @@ struct gb_handle {
   unsigned long long *d_arrivals = nullptr;  // arrival counter of the fused panel kernel
   double *d_scalars = nullptr;  // small FP64 reduction outputs
   unsigned sync_epoch = 0;
-  gb::Workspace ws[8];       // named workspaces, see WS_* below
+  gb::Workspace ws[9];       // named workspaces, see WS_* below
   std::mutex mu;
   // GB_OPT_PROFILE: event pairs recorded around launches, read later
   int profile = 0;
@@ -91,13 +92,14 @@ struct gb_handle {
     void *const *L = nullptr;
     const int64_t *lda = nullptr, *ldl = nullptr;
     int *ticket = nullptr;
+    int lu = 0;  // 1: Algorithm 2 (LU), 0: Algorithm 1 (Cholesky)
   } plan;
 };
 
 namespace gb {
 
 enum { WS_STAGE = 0, WS_PANEL = 1, WS_SOLVE = 2, WS_MISC = 3, WS_DINV = 4, WS_PANEL2 = 5,
-       WS_STRAS = 6, WS_STRAS2 = 7 };
+       WS_STRAS = 6, WS_STRAS2 = 7, WS_QR = 8 };
 constexpr int SYNC_WORDS = 1 << 16;
 
 // Make sure workspace `slot` holds >= bytes; waits for `stream` before
@@ -176,6 +178,7 @@ struct TcUpdateArgs {
   int64_t spin_limit;
   void *pack;        // workspace for the packed operands
   size_t pack_bytes;
+  int cluster;       // 2: CTA pairs with pair MMAs (256 x 256 tiles); else 1
 };
 size_t tc_pack_bytes(int64_t M, int64_t N, int64_t K, bool nn, int split);
 cudaError_t launch_update_tc(const TcUpdateArgs &a, cudaStream_t st);
@@ -221,6 +224,26 @@ cudaError_t launch_chol_batched_plan(int count, const int *order, const int *n, 
                                      void *const *A, const int64_t *lda, void *const *L,
                                      const int64_t *ldl, int *info, int *ticket, int sm_count,
                                      int exact, cudaStream_t st);
+// The same for Algorithm 2 (compact LU written to L[i] with ldl[i]).
+template <typename T>
+cudaError_t launch_lu_batched_plan(int count, const int *order, const int *n, const int *step,
+                                   void *const *A, const int64_t *lda, void *const *LU,
+                                   const int64_t *ldlu, int *info, int *ticket, int sm_count,
+                                   int exact, cudaStream_t st);
+// Algorithm 3 (qr.cu).  Column steps of columns [col0, col0 + bb) of the
+// n x n working matrix Qm on one cluster of 8 CTAs (bb <= qr_panel_max_cols).
+int64_t qr_panel_max_cols(int64_t n, size_t esz);
+template <typename T>
+cudaError_t launch_qr_panel(T *Qm, int64_t ldq, int64_t n, int64_t col0, int bb, int *status,
+                            cudaStream_t st);
+// C := X^T Y (X: K x M, Y: K x N, row-major); upper: C's upper triangle,
+// zeros below.  Skinny results split K into `work` when it is large enough
+// (gemm_tn_work_bytes).
+size_t gemm_tn_work_bytes(size_t esz, int sm_count);
+template <typename T>
+cudaError_t launch_gemm_tn(T *C, int64_t ldc, const T *X, int64_t ldx, const T *Y, int64_t ldy,
+                           int64_t M, int64_t N, int64_t K, bool upper, const int *status,
+                           void *work, size_t work_bytes, int sm_count, cudaStream_t st);
 template <typename T>
 cudaError_t launch_fill_spd(T *base, int64_t stride, int count, int n, cudaStream_t st);
 

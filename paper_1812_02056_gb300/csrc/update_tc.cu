@@ -20,6 +20,19 @@
 //    Every mbarrier wait is bounded by a %globaltimer deadline; on expiry the
 //    CTA raises DEV_ERR_TIMEOUT, skips its stores, frees its tensor memory and
 //    returns.
+// 3. pair variant (CL = 2): clusters of two CTAs on two SMs compute a
+//    256 x 256 tile with tcgen05.mma.cta_group::2 (M = 256): each CTA stages
+//    its own 128 rows of A and one 128-row half of B, and the MMA issued by
+//    the even CTA reads both CTAs' shared memory and accumulates each CTA's
+//    128 x 256 half in that CTA's tensor memory.  Per SM and k-block this
+//    moves 32 KiB through shared memory instead of 48 KiB (TMA writes plus
+//    MMA reads), which frees shared-memory bandwidth and room for 6 stages.
+//    TMA loads of both CTAs complete on the even CTA's stage barrier; the
+//    MMA issuer's commits arrive on both CTAs' barriers (multicast); the odd
+//    CTA's epilogue releases the accumulator on the even CTA's barrier.
+//    Before leaving, each producer waits for the last stage releases and
+//    the MMA issuer for its last MMAs, so no copy, MMA or arrival targets a
+//    CTA that has exited.
 #include <cuda.h>  // CUtensorMap and its enums (types only; the encoder is
                    // fetched through the runtime's driver entry point)
 #include <cuda_bf16.h>
@@ -35,16 +48,24 @@
 namespace gb {
 namespace {
 
-constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
-constexpr int EPI_WARPS = 4;
-constexpr int THREADS = 64 + EPI_WARPS * 32;  // producer, MMA, 4 epilogue warps
+constexpr int BM = 128, BN = 256, BK = 64;
 constexpr uint32_t TMEM_COLS = 512;           // two 128 x 256 FP32 accumulators
 constexpr uint32_t A_STAGE = BM * BK * 2;     // 16 KiB
-constexpr uint32_t B_STAGE = BN * BK * 2;     // 32 KiB
 constexpr uint32_t STAGING = 32 * 32 * 4;     // one 32 x 32 FP32 reduce box
-constexpr size_t SMEM_BYTES =
-    (size_t)STAGES * (A_STAGE + B_STAGE) + EPI_WARPS * 2 * STAGING + 1024 + 256;
-static_assert(SMEM_BYTES <= 232448, "shared memory per CTA");
+// per CTA: CL = 1 stages all 256 rows of B, CL = 2 one half of them, which
+// leaves room for 6 stages.  (Eight epilogue warps with 5 stages measured
+// slower than four with 6: the main loop wants the deeper ring.)
+template <int CL>
+struct Cfg {
+  static constexpr uint32_t B_STAGE = BN / CL * BK * 2;  // 32 / 16 KiB
+  static constexpr int STAGES = CL == 1 ? 4 : 6;
+  static constexpr int EPI_WARPS = 4;
+  static constexpr int THREADS = 64 + EPI_WARPS * 32;  // producer, MMA, epilogue warps
+  static constexpr size_t SMEM =
+      (size_t)STAGES * (A_STAGE + B_STAGE) + EPI_WARPS * 2 * STAGING + 1024 + 256;
+};
+constexpr int MAX_STAGES = 6;
+static_assert(Cfg<1>::SMEM <= 232448 && Cfg<2>::SMEM <= 232448, "shared memory per CTA");
 
 // ------------------------------------------------------------ PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -105,17 +126,82 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, u
       : "memory");
 }
 
-__device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                   smem_u32(slot)),
-               "r"(ncols)
-               : "memory");
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+// The same load for a CTA pair: the box lands in this CTA's shared memory
+// and its bytes complete on `bar`, a shared::cluster address that may lie in
+// the peer CTA (the even CTA's stage barrier).
+__device__ __forceinline__ void tma_load_2d_pair(void *dst, const CUtensorMap *map, uint32_t bar,
+                                                 int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.cta_group::2"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
+      : "memory");
 }
 
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_id_x() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t num_clusters_x() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+  return r;
+}
+// All threads of all CTAs of the cluster; release/acquire orders shared
+// memory (and barrier initialisation) across the cluster.
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// shared::cluster address of the variable at `p` in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t cluster_addr(const void *p, uint32_t rank) {
+  uint32_t remote;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(smem_u32(p)), "r"(rank));
+  return remote;
+}
+// 32-bit store into CTA `rank`'s copy of the shared variable at `p`.
+__device__ __forceinline__ void st_cluster_u32(void *p, uint32_t rank, uint32_t v) {
+  asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(cluster_addr(p, rank)), "r"(v) : "memory");
+}
+// Arrive on a barrier given by its shared::cluster address (possibly remote).
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar)
                : "memory");
+}
+
+// Tensor-memory allocation: one warp per CTA; for a pair (CL = 2) one warp
+// of each of the two CTAs takes part in the same allocation.
+template <int CL>
+__device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols) {
+  if (CL == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  } else {
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+  }
+}
+
+template <int CL>
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  if (CL == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+                 : "memory");
+  else
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+                 : "memory");
 }
 
 __device__ __forceinline__ void tc_fence_before() {
@@ -126,14 +212,26 @@ __device__ __forceinline__ void tc_fence_after() {
 }
 
 // D[tmem] (+)= A[smem] * B[smem]^T, both K-major, 16-bit inputs, FP32 accumulate.
+// CL = 2: M = 256 over the CTA pair (A rows and B halves read from both CTAs'
+// shared memory at the descriptors' offsets, D split over both CTAs' tensor
+// memory at `tmem_d`).
+template <int CL>
 __device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc,
                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-      "l"(da), "l"(db), "r"(idesc), "r"(accumulate)
-      : "memory");
+  if (CL == 1)
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(da), "l"(db), "r"(idesc), "r"(accumulate)
+        : "memory");
+  else
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(da), "l"(db), "r"(idesc), "r"(accumulate)
+        : "memory");
 }
 
 // Arrive on `bar` once every tcgen05 operation this thread issued so far is done.
@@ -141,6 +239,21 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
   asm volatile(
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
           smem_u32(bar))
+      : "memory");
+}
+// Pair forms: arrive on `bar` in this CTA, or on the barrier at `bar`'s offset
+// in every CTA of `mask`, once the pair MMAs this thread issued are done.
+__device__ __forceinline__ void mma_commit_pair(uint64_t *bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit_pair_mc(uint64_t *bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+      " [%0], %1;" ::"r"(smem_u32(bar)),
+      "h"(mask)
       : "memory");
 }
 
@@ -197,98 +310,155 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// Valid output tiles in row-major tile order, strided over the persistent CTAs.
+// The valid output tiles, counted in row-major order of groups of `cl`
+// vertically adjacent tiles and dealt out round-robin: index v goes to the
+// persistent CTA (cl = 1) or cluster (cl = 2) v mod stride, so every CTA
+// gets the same number of tiles to within one.  A group row holds a prefix
+// of valid tiles (lower mode: up to the diagonal of its lowest tile); `rank`
+// picks the tile of the group.
 struct TileIter {
-  int64_t t, total, nbj, stride, diag;
+  int64_t v, total, stride;  // next index, number of valid groups, stride
+  int64_t row, row_start;    // group row of index v and the index of its first tile
+  int64_t nbj, diag;
+  int rank, cl;
   bool lower;
+  __device__ int64_t row_count(int64_t bg) const {
+    if (!lower) return nbj;
+    const int64_t last = bg * cl * BM + cl * BM - 1 + diag;  // last column on/below the diagonal
+    return last < 0 ? 0 : min64(nbj, last / BN + 1);
+  }
   __device__ bool next(int64_t &m0, int64_t &n0) {
-    while (t < total) {
-      const int64_t bi = t / nbj, bj = t % nbj;
-      t += stride;
-      m0 = bi * BM;
-      n0 = bj * BN;
-      if (!lower || m0 + BM - 1 + diag >= n0) return true;  // skip tiles above the diagonal
+    if (v >= total) return false;
+    for (int64_t c = row_count(row); v >= row_start + c; c = row_count(row)) {
+      row_start += c;
+      ++row;
     }
-    return false;
+    m0 = row * cl * BM + rank * BM;
+    n0 = (v - row_start) * BN;
+    v += stride;
+    return true;
   }
 };
 
 // ---------------------------------------------------------------- kernel
-// Persistent: one CTA per SM walks the tile list.  Warp 0 = TMA producer,
-// warp 1 = MMA issuer (and tensor-memory owner), warps 2..5 = epilogue.
-// Two 256-column accumulators let the epilogue of one tile run while the
-// MMAs of the next accumulate.
-template <bool LOWER>
-__global__ void __launch_bounds__(THREADS, 1)
+// Persistent: one CTA per SM (CL = 1) or one CTA pair per two SMs (CL = 2)
+// walks the tile list.  Warp 0 = TMA producer, warp 1 = MMA issuer (even CTA
+// only for a pair) and tensor-memory owner, warps 2..5 = epilogue.  Two
+// 256-column accumulators let the epilogue of one tile run while the MMAs of
+// the next accumulate.
+template <bool LOWER, int CL>
+__global__ void __launch_bounds__(Cfg<CL>::THREADS, 1)
     tc_update_kernel(const __grid_constant__ CUtensorMap map_a,
                      const __grid_constant__ CUtensorMap map_b,
                      const __grid_constant__ CUtensorMap map_c, float *__restrict__ C, int64_t ldc,
-                     int64_t M, int64_t N, int nk, int64_t diag, uint32_t idesc, const int *status,
-                     int *err, long long wait_ns, int use_tma_store, int vec_ok) {
+                     int64_t M, int64_t N, int nk, int64_t diag, int64_t total, uint32_t idesc,
+                     const int *status, int *err, long long wait_ns, int use_tma_store,
+                     int vec_ok) {
+  static_assert(CL == 1 || CL == 2, "one CTA or a CTA pair");
+  constexpr int STAGES = Cfg<CL>::STAGES;
+  constexpr uint32_t B_STAGE = Cfg<CL>::B_STAGE;
+  constexpr int EPI_WARPS = Cfg<CL>::EPI_WARPS;
+  static_assert(EPI_WARPS % 4 == 0 && STAGES <= MAX_STAGES, "epilogue warps per lane quarter");
   extern __shared__ uint8_t smem_raw[];
-  if (*reinterpret_cast<const volatile int *>(status) != 0) return;
-  // a CTA whose wait expired has already raised the error word: later CTAs
-  // leave at once instead of waiting out their own deadlines
-  if (*reinterpret_cast<const volatile int *>(err) & DEV_ERR_TIMEOUT) return;
-
   uint8_t *smem = reinterpret_cast<uint8_t *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   uint8_t *sA = smem;
   uint8_t *sB = sA + STAGES * A_STAGE;
   uint8_t *sStage = sB + STAGES * B_STAGE;  // EPI_WARPS x 2 x 4 KiB, 1 KiB aligned
   uint64_t *full = reinterpret_cast<uint64_t *>(sStage + EPI_WARPS * 2 * STAGING);
-  uint64_t *empty = full + STAGES;
-  uint64_t *acc_full = empty + STAGES;
+  uint64_t *empty = full + MAX_STAGES;
+  uint64_t *acc_full = empty + MAX_STAGES;
   uint64_t *acc_empty = acc_full + 2;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 2);
+  uint64_t *drain = acc_empty + 2;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+  volatile uint32_t *skip = reinterpret_cast<volatile uint32_t *>(tmem_slot + 2);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = CL > 1 ? cluster_ctarank() : 0u;
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
+      mbar_init(&full[s], 1);   // the even CTA's producer arrives (with the byte count)
+      mbar_init(&empty[s], 1);  // one commit of the MMA issuer
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&acc_full[b], 1);
-      mbar_init(&acc_empty[b], EPI_WARPS);
+      mbar_init(&acc_empty[b], CL * EPI_WARPS);  // every epilogue warp of the pair
     }
+    mbar_init(drain, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    // Skip the work after a failed column step, or when a CTA whose wait
+    // expired has already raised the error word.  Rank 0 decides for the
+    // whole cluster, so that both CTAs of a pair skip or both work.
+    if (rank == 0) {
+      const uint32_t v = (*reinterpret_cast<const volatile int *>(status) != 0 ||
+                          (*reinterpret_cast<const volatile int *>(err) & DEV_ERR_TIMEOUT))
+                             ? 1u
+                             : 0u;
+      if (CL > 1) {
+        for (uint32_t r = 0; r < (uint32_t)CL; ++r) st_cluster_u32((void *)skip, r, v);
+      } else {
+        *skip = v;
+      }
+    }
   }
-  if (warp == 1) tmem_alloc(tmem_slot, TMEM_COLS);
+  if (warp == 1) tmem_alloc<CL>(tmem_slot, TMEM_COLS);
   tc_fence_before();
-  __syncthreads();
+  if (CL > 1) cluster_sync();  // barriers initialised and tensor memory allocated in both CTAs
+  else __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   const unsigned long long deadline = (unsigned long long)wait_ns;  // per wait
 
-  const int64_t nbi = (M + BM - 1) / BM, nbj = (N + BN - 1) / BN;
-  TileIter it{(int64_t)blockIdx.x, nbi * nbj, nbj, (int64_t)gridDim.x, diag, LOWER};
+  const int64_t nbj = (N + BN - 1) / BN;
+  const int64_t group = CL > 1 ? (int64_t)cluster_id_x() : (int64_t)blockIdx.x;
+  const int64_t ngroups = CL > 1 ? (int64_t)num_clusters_x() : (int64_t)gridDim.x;
+  TileIter it{group, total, ngroups, 0, 0, nbj, diag, (int)rank, CL, LOWER};
   int64_t m0 = 0, n0 = 0;
 
-  if (warp == 0) {
+  if (*skip) {
+    // nothing issued: straight to the teardown
+  } else if (warp == 0) {
     // ------------------------------------------------ TMA producer
     if (lane == 0) {
       uint32_t g = 0;
       bool ok = true;
+      // stage barrier the copies complete on: this CTA's, or the even CTA's
+      const uint32_t full0 = CL > 1 ? cluster_addr(full, 0) : smem_u32(full);
       while (ok && it.next(m0, n0)) {
         for (int kb = 0; kb < nk; ++kb, ++g) {
           const uint32_t s = g % STAGES, ph = (g / STAGES) & 1u;
-          if (g >= STAGES && !mbar_wait(&empty[s], ph ^ 1u, deadline, err, abort_flag)) {
+          if (g >= (uint32_t)STAGES && !mbar_wait(&empty[s], ph ^ 1u, deadline, err, abort_flag)) {
             ok = false;
             break;
           }
-          mbar_expect_tx(&full[s], A_STAGE + B_STAGE);
-          tma_load_2d(sA + s * A_STAGE, &map_a, &full[s], kb * BK, (int)m0);
-          tma_load_2d(sB + s * B_STAGE, &map_b, &full[s], kb * BK, (int)n0);
+          if (CL == 1) {
+            mbar_expect_tx(&full[s], A_STAGE + B_STAGE);
+            tma_load_2d(sA + s * A_STAGE, &map_a, &full[s], kb * BK, (int)m0);
+            tma_load_2d(sB + s * B_STAGE, &map_b, &full[s], kb * BK, (int)n0);
+          } else {
+            // the even CTA's barrier counts the bytes of both CTAs
+            if (rank == 0) mbar_expect_tx(&full[s], CL * (A_STAGE + B_STAGE));
+            const uint32_t bar = full0 + s * 8u;
+            tma_load_2d_pair(sA + s * A_STAGE, &map_a, bar, kb * BK, (int)m0);
+            tma_load_2d_pair(sB + s * B_STAGE, &map_b, bar, kb * BK,
+                             (int)(n0 + rank * (BN / 2)));
+          }
         }
+      }
+      // Pair: wait for the last stage releases, so that no commit arrives on
+      // this CTA's barriers after it exits (every copy into this CTA was
+      // waited for by the MMA issuer before it released the stage).
+      if (CL > 1 && ok) {
+        for (uint32_t j = g > (uint32_t)STAGES ? g - STAGES : 0u; j < g; ++j)
+          if (!mbar_wait(&empty[j % STAGES], (j / STAGES) & 1u, deadline, err, abort_flag)) break;
       }
     }
     __syncwarp();
   } else if (warp == 1) {
     // ------------------------------------------------ MMA issuer
-    if (lane == 0) {
+    if (lane == 0 && rank == 0) {
       uint32_t g = 0, i = 0;
       bool ok = true;
       while (ok && it.next(m0, n0)) {
@@ -307,20 +477,38 @@ __global__ void __launch_bounds__(THREADS, 1)
           const uint32_t a0 = smem_u32(sA + s * A_STAGE), b0 = smem_u32(sB + s * B_STAGE);
 #pragma unroll
           for (int kk = 0; kk < BK / 16; ++kk)
-            mma_f16(d, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), idesc,
-                    (kb | kk) != 0 ? 1u : 0u);
-          mma_commit(&empty[s]);
+            mma_f16<CL>(d, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), idesc,
+                        (kb | kk) != 0 ? 1u : 0u);
+          if (CL == 1) mma_commit(&empty[s]);
+          else mma_commit_pair_mc(&empty[s], (uint16_t)0x3);
         }
-        mma_commit(&acc_full[buf]);
+        if (!ok) break;
+        if (CL == 1) mma_commit(&acc_full[buf]);
+        else mma_commit_pair_mc(&acc_full[buf], (uint16_t)0x3);
         ++i;
+      }
+      // every MMA issued (into both CTAs' tensor memory, for a pair) is done
+      // before the tensor memory is released
+      if (CL == 1) mma_commit(drain);
+      else mma_commit_pair(drain);
+      const unsigned long long until = now_ns() + deadline;  // bounded, even after an abort
+      while (!mbar_try_wait(drain, 0)) {
+        if (now_ns() > until) {
+          atomicOr(err, DEV_ERR_TIMEOUT);
+          break;
+        }
       }
     }
     __syncwarp();
   } else {
-    // ------------------------------------------------ epilogue (warps 2..5)
-    const int e = warp - 2;                // 0..3
+    // ------------------------------------------------ epilogue (warps 2..)
+    const int e = warp - 2;                // 0 .. EPI_WARPS - 1
     const int q = warp & 3;                // tensor-memory lane quarter this warp may read
+    constexpr int CPW = BN / 32 / (EPI_WARPS / 4);  // 32-column chunks per warp
+    const int c_begin = (e / 4) * CPW;     // this warp's share of the tile's columns
     uint8_t *stage0 = sStage + (size_t)e * 2 * STAGING;
+    // accumulator release goes to the MMA issuer's CTA (the even one)
+    const uint32_t acc_empty0 = CL > 1 ? cluster_addr(acc_empty, 0) : smem_u32(acc_empty);
     uint32_t i = 0, chunks = 0;
     while (it.next(m0, n0)) {
       const uint32_t buf = i & 1u, use = i >> 1;
@@ -328,7 +516,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       tc_fence_after();
       const int64_t row0 = m0 + q * 32;
       const int64_t row = row0 + lane;
-      for (int c = 0; c < BN / 32; ++c) {
+      for (int c = c_begin; c < c_begin + CPW; ++c) {
         const int64_t col0 = n0 + c * 32;
         if (col0 >= N || row0 >= M) break;                  // warp-uniform
         if (LOWER && row0 + 31 + diag < col0) break;        // chunk above the diagonal
@@ -385,15 +573,20 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(&acc_empty[buf]);
+      if (lane == 0) {
+        if (CL == 1) mbar_arrive(&acc_empty[buf]);
+        else mbar_arrive_cluster(acc_empty0 + buf * 8u);
+      }
       ++i;
     }
     if (lane == 0) bulk_wait_all();
     __syncwarp();
   }
   tc_fence_before();
-  __syncthreads();
-  if (warp == 1) tmem_dealloc(tmem, TMEM_COLS);
+  if (CL > 1) cluster_sync();
+  else __syncthreads();
+  tc_fence_after();
+  if (warp == 1) tmem_dealloc<CL>(tmem, TMEM_COLS);
 }
 
 template <typename T16>
@@ -561,6 +754,64 @@ cudaError_t pack_operands(const TcUpdateArgs &a, int64_t Kp, int terms, T16 *xp,
   return cudaGetLastError();
 }
 
+struct TcKernelArgs {
+  CUtensorMap map_a, map_b, map_c;
+  float *C;
+  int64_t ldc, M, N;
+  int nk;
+  int64_t diag, total;
+  uint32_t idesc;
+  const int *status;
+  int *err;
+  long long wait_ns;
+  int use_tma_store, vec_ok;
+};
+
+// Launch over `valid` tile groups: clusters of CL CTAs, as many groups as can
+// be resident at once (one CTA per SM), at most `valid`.
+template <bool LOWER, int CL>
+cudaError_t launch_kernel(const TcKernelArgs &k, int64_t valid, int dev, cudaStream_t st) {
+  auto kern = tc_update_kernel<LOWER, CL>;
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg<CL>::SMEM);
+  if (attr != cudaSuccess) return attr;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaLaunchConfig_t cfg{};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CL;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(Cfg<CL>::THREADS);
+  cfg.dynamicSmemBytes = Cfg<CL>::SMEM;
+  cfg.stream = st;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int64_t slots = sms;
+  if (CL > 1) {
+    // SMs are paired within a GPC, so an odd GPC leaves one SM without a pair
+    static const int max_clusters = [&] {
+      cudaLaunchConfig_t q = cfg;
+      q.gridDim = dim3((unsigned)(sms / CL * CL));
+      q.stream = 0;
+      int n = 0;
+      if (cudaOccupancyMaxActiveClusters(&n, kern, &q) != cudaSuccess || n <= 0) {
+        cudaGetLastError();
+        n = sms / CL;
+      }
+      return n;
+    }();
+    slots = max_clusters;
+  }
+  const int64_t groups = std::max<int64_t>(1, std::min<int64_t>(slots, valid));
+  cfg.gridDim = dim3((unsigned)(groups * CL));
+  count_launch();
+  return cudaLaunchKernelEx(&cfg, kern, k.map_a, k.map_b, k.map_c, k.C, k.ldc, k.M, k.N, k.nk,
+                            k.diag, k.total, k.idesc, k.status, k.err, k.wait_ns,
+                            k.use_tma_store, k.vec_ok);
+}
+
 }  // namespace
 
 bool tc_supported(int device) {
@@ -600,49 +851,42 @@ cudaError_t launch_update_tc(const TcUpdateArgs &a, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   CUtensorMap map_a, map_b, map_c;
   memset(&map_c, 0, sizeof map_c);
-  if (!make_operand_map(&map_a, xp, a.M, Ke, BM, a.f16) ||
-      !make_operand_map(&map_b, yp, a.N, Ke, BN, a.f16))
-    return cudaErrorInvalidValue;
   const int use_tma_store = make_c_map(&map_c, a.C, a.ldc, a.M, a.N) ? 1 : 0;
-  // instruction descriptor: FP32 accumulator, A/B = BF16 (1) or FP16 (0),
-  // both K-major, N >> 3 at bit 17, M >> 4 at bit 24
-  const uint32_t ab = a.f16 ? 0u : 1u;
-  const uint32_t idesc = (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(BN >> 3) << 17) |
-                         ((uint32_t)(BM >> 4) << 24);
   const int vec_ok = ((reinterpret_cast<uintptr_t>(a.C) & 15) == 0 && (a.ldc & 3) == 0) ? 1 : 0;
   // a tile takes microseconds; one second bounds every single wait
   const long long wait_ns = std::min<long long>((long long)a.spin_limit * 100LL, 1000000000LL);
-  // persistent grid: one CTA per SM, at most one per valid tile
+  // persistent grid: one CTA (cluster) per SM (pair of SMs), at most one per
+  // valid tile (pair of vertically adjacent tiles)
+  const int CL = a.cluster == 2 ? 2 : 1;
+  // instruction descriptor: FP32 accumulator, A/B = BF16 (1) or FP16 (0),
+  // both K-major, N >> 3 at bit 17, M >> 4 at bit 24 (M = 256 for a pair)
+  const uint32_t ab = a.f16 ? 0u : 1u;
+  const uint32_t idesc = (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(BN >> 3) << 17) |
+                         ((uint32_t)((BM * CL) >> 4) << 24);
   const int64_t nbi = (a.M + BM - 1) / BM, nbj = (a.N + BN - 1) / BN;
+  const int64_t nbg = (nbi + CL - 1) / CL;
   int64_t valid = 0;
-  for (int64_t bi = 0; bi < nbi; ++bi) {
+  for (int64_t bg = 0; bg < nbg; ++bg) {
     if (!a.lower) {
       valid += nbj;
       continue;
     }
-    const int64_t last = bi * BM + BM - 1 + a.diag;  // largest column index on/below diagonal
+    // largest column index on/below the diagonal in the group's lowest tile
+    const int64_t last = bg * CL * BM + CL * BM - 1 + a.diag;
     if (last >= 0) valid += std::min<int64_t>(nbj, last / BN + 1);
   }
   if (valid == 0) return cudaSuccess;
-  int sms = 0;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(sms, valid));
-  if (a.lower) {
-    static cudaError_t attr = cudaFuncSetAttribute(
-        tc_update_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
-    if (attr != cudaSuccess) return attr;
-    tc_update_kernel<true><<<grid, THREADS, SMEM_BYTES, st>>>(
-        map_a, map_b, map_c, a.C, a.ldc, a.M, a.N, (int)(Ke / BK), a.diag, idesc, a.status, a.err,
-        wait_ns, use_tma_store, vec_ok);
-  } else {
-    static cudaError_t attr = cudaFuncSetAttribute(
-        tc_update_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
-    if (attr != cudaSuccess) return attr;
-    tc_update_kernel<false><<<grid, THREADS, SMEM_BYTES, st>>>(
-        map_a, map_b, map_c, a.C, a.ldc, a.M, a.N, (int)(Ke / BK), a.diag, idesc, a.status, a.err,
-        wait_ns, use_tma_store, vec_ok);
-  }
-  count_launch();
+  if (!make_operand_map(&map_a, xp, a.M, Ke, BM, a.f16) ||
+      !make_operand_map(&map_b, yp, a.N, Ke, BN / CL, a.f16))
+    return cudaErrorInvalidValue;
+  const TcKernelArgs k{map_a, map_b, map_c, a.C, a.ldc, a.M, a.N, (int)(Ke / BK), a.diag,
+                       valid, idesc, a.status, a.err, wait_ns, use_tma_store, vec_ok};
+  if (a.lower)
+    e = CL == 2 ? launch_kernel<true, 2>(k, valid, dev, st) : launch_kernel<true, 1>(k, valid, dev, st);
+  else
+    e = CL == 2 ? launch_kernel<false, 2>(k, valid, dev, st)
+                : launch_kernel<false, 1>(k, valid, dev, st);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

@@ -76,10 +76,11 @@ def test_mixed_matches_simt_update_closely(h, dt):
     n, s = 640, 128
     A = torch.from_numpy(I.spd_gram(n, 5)).to(DEV)
     L1, _ = h.chol_factor(A, s, dt)
+    prev = h.get_option(binding.GB_OPT_TC_UPDATE)
     h.set_option(binding.GB_OPT_TC_UPDATE, 0)
     try:
         L2, _ = h.chol_factor(A, s, dt)
     finally:
-        h.set_option(binding.GB_OPT_TC_UPDATE, 1)
+        h.set_option(binding.GB_OPT_TC_UPDATE, prev)
     d = (L1.double() - L2.double()).abs().max().item() / L2.double().abs().max().item()
     assert d <= 4 * BOUNDS[dt]
