@@ -220,7 +220,10 @@ gb_status gb_lu_factor(gb_handle *h, int64_t n, int64_t s, gb_dtype dt, const vo
  *  s     step (s >= 1; s >= n: no delayed projection; s = 0: 64).
  *  info  0, or c + 1 (1-based) when the projected column c has zero (or
  *        NaN) norm, i.e. A is rank deficient there; Q and R are then
- *        unspecified from that column on.
+ *        unspecified from that column on.  -1: a bounded wait of the
+ *        column-step kernel expired (its cluster-wide sums did not arrive
+ *        within GB_OPT_SPIN_LIMIT, clamped to [10 ms, 1 s]); Q and R are
+ *        not valid.
  */
 gb_status gb_qr_factor(gb_handle *h, int64_t n, int64_t s, gb_dtype dt, const void *A,
                        int64_t lda, void *Q, int64_t ldq, void *R, int64_t ldr, int *info,

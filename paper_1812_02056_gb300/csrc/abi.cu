@@ -582,7 +582,8 @@ gb_status qr_blocked(gb_handle *h, int64_t n, int64_t s, const T *A, int64_t lda
       const int64_t bb = std::min(b, z + sb - z2);
       {
         PhaseTimer tp(h, st, GB_PHASE_PANEL, 4.0 * (double)n * (double)bb * (double)bb, 0.0);
-        GB_CUDA_TRY(launch_qr_panel<T>(Q, ldq, n, z2, (int)bb, status, st));
+        GB_CUDA_TRY(launch_qr_panel<T>(Q, ldq, n, z2, (int)bb, status, h->d_err, h->spin_limit,
+                                       st));
       }
       const int64_t rest = z + sb - (z2 + bb);
       if (rest > 0) {

@@ -235,7 +235,7 @@ cudaError_t launch_lu_batched_plan(int count, const int *order, const int *n, co
 int64_t qr_panel_max_cols(int64_t n, size_t esz);
 template <typename T>
 cudaError_t launch_qr_panel(T *Qm, int64_t ldq, int64_t n, int64_t col0, int bb, int *status,
-                            cudaStream_t st);
+                            int *err, int64_t spin_limit, cudaStream_t st);
 // C := X^T Y (X: K x M, Y: K x N, row-major); upper: C's upper triangle,
 // zeros below.  Skinny results split K into `work` when it is large enough
 // (gemm_tn_work_bytes).
