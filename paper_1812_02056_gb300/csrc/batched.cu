@@ -74,6 +74,90 @@ __device__ __forceinline__ float ddiv<float>(float a, float b) {
 
 __device__ __forceinline__ int64_t tri(int64_t i) { return i * (i + 1) / 2; }
 
+// The delayed update of an m x nc block: out(i, j) -= sum_{k < kn} X(i, k) Y(j, k),
+// for every (i, j) (LOWER: j <= i).  The 256 threads form a 16 x 16 grid; in
+// each (16 TR) x (16 TR) block tile a thread owns TR consecutive rows and TR
+// columns 16 apart (so the 16 threads of a row group read 16 consecutive
+// rows of Y: distinct banks), held as a TR x TR register tile.  A k step
+// costs 2 TR shared-memory loads for TR^2 multiply-adds (a dot product per
+// element would cost two loads per multiply-add).  Each element's sum still
+// runs over k in ascending order from zero and is subtracted once, so exact
+// mode keeps the oracle's rounding sequence.
+template <typename T, bool EXACT, bool LOWER, int TR, typename FX, typename FY, typename FO>
+__device__ __forceinline__ void tiled_update(int m, int nc, int kn, FX X, FY Y, FO out) {
+  constexpr int TB = 16 * TR;
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  const int nti = (m + TB - 1) / TB, ntj = (nc + TB - 1) / TB;
+  for (int t = 0; t < nti * ntj; ++t) {
+    const int ti = t / ntj, tj = t % ntj;
+    if (LOWER && tj > ti) continue;  // block tile strictly above the diagonal (TB square tiles)
+    const int i0 = ti * TB + ty * TR, j0 = tj * TB + tx;
+    if (i0 >= m || j0 >= nc) continue;
+    if (LOWER && j0 > i0 + TR - 1) continue;  // every element of this thread above the diagonal
+    int ii[TR], jj[TR];
+#pragma unroll
+    for (int a = 0; a < TR; ++a) {
+      ii[a] = min(i0 + a, m - 1);
+      jj[a] = min(j0 + 16 * a, nc - 1);
+    }
+    T acc[TR][TR];
+#pragma unroll
+    for (int a = 0; a < TR; ++a)
+#pragma unroll
+      for (int b = 0; b < TR; ++b) acc[a][b] = T(0);
+    for (int k = 0; k < kn; ++k) {
+      T xa[TR], yb[TR];
+#pragma unroll
+      for (int a = 0; a < TR; ++a) {
+        xa[a] = X(ii[a], k);
+        yb[a] = Y(jj[a], k);
+      }
+#pragma unroll
+      for (int a = 0; a < TR; ++a)
+#pragma unroll
+        for (int b = 0; b < TR; ++b) acc[a][b] = madd(acc[a][b], xa[a], yb[b], EXACT);
+    }
+#pragma unroll
+    for (int a = 0; a < TR; ++a)
+#pragma unroll
+      for (int b = 0; b < TR; ++b) {
+        const int i = i0 + a, j = j0 + 16 * b;
+        if (i < m && j < nc && (!LOWER || j <= i)) {
+          T *p = out(i, j);
+          *p = *p - acc[a][b];  // a lone subtraction is never contracted
+        }
+      }
+  }
+}
+
+// One dot product per element (warp w takes rows w, w + 8, ...; its lanes the
+// columns): no multiply-add is spent above the diagonal.  FP64 uses it: its
+// rate is bound by the FP64 units, not by shared-memory loads.
+template <typename T, bool EXACT, bool LOWER, typename FX, typename FY, typename FO>
+__device__ __forceinline__ void dot_update(int m, int nc, int kn, FX X, FY Y, FO out) {
+  const int tid = threadIdx.x;
+  for (int i = tid >> 5; i < m; i += BT / 32) {
+    const int jend = LOWER ? min(i + 1, nc) : nc;
+    for (int j = tid & 31; j < jend; j += 32) {
+      T sij = T(0);
+#pragma unroll 4
+      for (int k = 0; k < kn; ++k) sij = madd(sij, X(i, k), Y(j, k), EXACT);
+      T *p = out(i, j);
+      *p = *p - sij;  // a lone subtraction is never contracted
+    }
+  }
+}
+
+template <typename T, bool EXACT, bool LOWER, typename FX, typename FY, typename FO>
+__device__ __forceinline__ void block_update(int m, int nc, int kn, FX X, FY Y, FO out) {
+  if (sizeof(T) == 8)
+    dot_update<T, EXACT, LOWER>(m, nc, kn, X, Y, out);
+  else if (m >= 48 && nc >= 48)
+    tiled_update<T, EXACT, LOWER, 4>(m, nc, kn, X, Y, out);
+  else
+    tiled_update<T, EXACT, LOWER, 2>(m, nc, kn, X, Y, out);
+}
+
 // ------------------------------------------------- whole matrix in shared memory
 // S holds the packed lower triangle: (i, j), j <= i, at i (i + 1) / 2 + j.
 template <typename T, bool EXACT>
@@ -84,17 +168,11 @@ __device__ int chol_in_smem(T *S, int n, int s, T *red) {
   for (int c = 0; c < n; ++c) {
     if (c == z + s) {
       // delayed update: A[i][j] -= S_ij, S_ij = sum_{k=z}^{c-1} L_ik L_jk, c <= j <= i
-      // warp w takes rows c + w, c + w + 8, ...; its lanes take the columns
-      for (int i = c + (tid >> 5); i < n; i += BT / 32) {
-        const T *Li = S + tri(i);
-        for (int j = c + (tid & 31); j <= i; j += 32) {
-          const T *Lj = S + tri(j);
-          T sij = T(0);
-  #pragma unroll 4
-          for (int k = z; k < c; ++k) sij = madd(sij, Li[k], Lj[k], exact);
-          S[tri(i) + j] = S[tri(i) + j] - sij;  // a lone subtraction is never contracted
-        }
-      }
+      const int z0 = z, c0 = c;
+      block_update<T, EXACT, true>(
+          n - c, n - c, c - z, [&](int i, int k) { return S[tri(c0 + i) + z0 + k]; },
+          [&](int j, int k) { return S[tri(c0 + j) + z0 + k]; },
+          [&](int i, int j) { return &S[tri(c0 + i) + c0 + j]; });
       z = c;
       __syncthreads();
     }
@@ -120,21 +198,22 @@ __device__ int chol_in_smem(T *S, int n, int s, T *red) {
 
 // ------------------------------------------------- panel in shared memory
 // P: rows [z, n) x columns [z, z + sb) of the working matrix, row-major with
-// leading dimension s (the panel width bound).
+// leading dimension ldp >= s (odd when it fits: rows then fall in different
+// shared-memory banks).
 template <typename T, bool EXACT>
-__device__ int chol_panel_path(T *A, int64_t lda, int n, int s, T *P, T *red) {
+__device__ int chol_panel_path(T *A, int64_t lda, int n, int s, T *P, int ldp, T *red) {
   constexpr bool exact = EXACT;
   const int tid = threadIdx.x;
   for (int z = 0; z < n; z += s) {
     const int sb = min(s, n - z);
     const int rows = n - z;
     for (int r = tid >> 5; r < rows; r += BT / 32)
-      for (int q = tid & 31; q < sb; q += 32) P[(int64_t)r * s + q] = A[(int64_t)(z + r) * lda + z + q];
+      for (int q = tid & 31; q < sb; q += 32) P[(int64_t)r * ldp + q] = A[(int64_t)(z + r) * lda + z + q];
     __syncthreads();
     for (int c = 0; c < sb; ++c) {  // column z + c, local index c
-      const T *Pc = P + (int64_t)c * s;
+      const T *Pc = P + (int64_t)c * ldp;
       for (int r = c + tid; r < rows; r += BT) {
-        T *Pr = P + (int64_t)r * s;
+        T *Pr = P + (int64_t)r * ldp;
         T v = Pr[c];
 #pragma unroll 4
         for (int k = 0; k < c; ++k) v = msub(v, Pr[k], Pc[k], exact);
@@ -144,26 +223,20 @@ __device__ int chol_panel_path(T *A, int64_t lda, int n, int s, T *P, T *red) {
       const T d = red[0];
       if (!(d > T(0))) return z + c + 1;
       const T lcc = dsqrt(d);
-      for (int r = c + 1 + tid; r < rows; r += BT) P[(int64_t)r * s + c] = ddiv(P[(int64_t)r * s + c], lcc);
-      if (tid == 0) P[(int64_t)c * s + c] = lcc;
+      for (int r = c + 1 + tid; r < rows; r += BT) P[(int64_t)r * ldp + c] = ddiv(P[(int64_t)r * ldp + c], lcc);
+      if (tid == 0) P[(int64_t)c * ldp + c] = lcc;
       __syncthreads();
     }
     for (int r = tid >> 5; r < rows; r += BT / 32)
       for (int q = tid & 31; q < sb; q += 32)
-        if (q <= r) A[(int64_t)(z + r) * lda + z + q] = P[(int64_t)r * s + q];
+        if (q <= r) A[(int64_t)(z + r) * lda + z + q] = P[(int64_t)r * ldp + q];
     // delayed update of the trailing lower triangle: rows/cols [z+sb, n)
     const int m = n - z - sb;
-    for (int r = tid >> 5; r < m; r += BT / 32) {
-      const T *Pi = P + (int64_t)(sb + r) * s;
-      for (int q = tid & 31; q <= r; q += 32) {
-        const T *Pj = P + (int64_t)(sb + q) * s;
-        T sij = T(0);
-#pragma unroll 4
-        for (int k = 0; k < sb; ++k) sij = madd(sij, Pi[k], Pj[k], exact);
-        T *a = A + (int64_t)(z + sb + r) * lda + z + sb + q;
-        *a = *a - sij;
-      }
-    }
+    const int64_t base = (int64_t)(z + sb) * lda + z + sb;
+    block_update<T, EXACT, true>(
+        m, m, sb, [&](int r, int k) { return P[(int64_t)(sb + r) * ldp + k]; },
+        [&](int q, int k) { return P[(int64_t)(sb + q) * ldp + k]; },
+        [&](int r, int q) { return A + base + (int64_t)r * lda + q; });
     __syncthreads();  // global writes of this CTA are visible to it after the barrier
   }
   return 0;
@@ -181,15 +254,11 @@ __device__ int lu_in_smem(T *W, int n, int ld, int s) {
   for (int c = 0; c < n; ++c) {
     if (c == z + s) {
       // delayed update of the trailing square: W_ij -= S_ij, S_ij = sum_k L_ik U_kj
-      for (int i = c + (tid >> 5); i < n; i += BT / 32) {
-        const T *Li = W + (int64_t)i * ld;
-        for (int j = c + (tid & 31); j < n; j += 32) {
-          T sij = T(0);
-#pragma unroll 4
-          for (int k = z; k < c; ++k) sij = madd(sij, Li[k], W[(int64_t)k * ld + j], exact);
-          W[(int64_t)i * ld + j] = W[(int64_t)i * ld + j] - sij;
-        }
-      }
+      const int z0 = z, c0 = c;
+      block_update<T, EXACT, false>(
+          n - c, n - c, c - z, [&](int i, int k) { return W[(int64_t)(c0 + i) * ld + z0 + k]; },
+          [&](int j, int k) { return W[(int64_t)(z0 + k) * ld + c0 + j]; },
+          [&](int i, int j) { return &W[(int64_t)(c0 + i) * ld + c0 + j]; });
       z = c;
       __syncthreads();
     }
@@ -228,14 +297,14 @@ __device__ int lu_in_smem(T *W, int n, int ld, int s) {
 // Inside the diagonal block, L is read from PL (on and below the diagonal)
 // and U from PU (above it).
 template <typename T, bool EXACT>
-__device__ int lu_panel_path(T *A, int64_t lda, int n, int s, T *PL, T *PU) {
+__device__ int lu_panel_path(T *A, int64_t lda, int n, int s, T *PL, int ldp, T *PU) {
   constexpr bool exact = EXACT;
   const int tid = threadIdx.x;
   for (int z = 0; z < n; z += s) {
     const int sb = min(s, n - z);
     const int rows = n - z;
     for (int r = tid >> 5; r < rows; r += BT / 32)
-      for (int q = tid & 31; q < sb; q += 32) PL[(int64_t)r * s + q] = A[(int64_t)(z + r) * lda + z + q];
+      for (int q = tid & 31; q < sb; q += 32) PL[(int64_t)r * ldp + q] = A[(int64_t)(z + r) * lda + z + q];
     for (int r = tid >> 5; r < sb; r += BT / 32)
       for (int q = tid & 31; q < rows; q += 32) PU[(int64_t)r * n + q] = A[(int64_t)(z + r) * lda + z + q];
     __syncthreads();
@@ -244,14 +313,14 @@ __device__ int lu_panel_path(T *A, int64_t lda, int n, int s, T *PL, T *PU) {
       for (int t = tid; t < 2 * m - 1; t += BT) {
         if (t < m) {
           const int r = c + t;
-          T *Pr = PL + (int64_t)r * s;
+          T *Pr = PL + (int64_t)r * ldp;
           T v = Pr[c];
 #pragma unroll 4
           for (int k = 0; k < c; ++k) v = msub(v, Pr[k], PU[(int64_t)k * n + c], exact);
           Pr[c] = v;
         } else {
           const int q = c + 1 + (t - m);
-          const T *Pc = PL + (int64_t)c * s;
+          const T *Pc = PL + (int64_t)c * ldp;
           T u = PU[(int64_t)c * n + q];
 #pragma unroll 4
           for (int k = 0; k < c; ++k) u = msub(u, Pc[k], PU[(int64_t)k * n + q], exact);
@@ -259,28 +328,23 @@ __device__ int lu_panel_path(T *A, int64_t lda, int n, int s, T *PL, T *PU) {
         }
       }
       __syncthreads();
-      const T lcc = PL[(int64_t)c * s + c];
+      const T lcc = PL[(int64_t)c * ldp + c];
       if (lcc == T(0) || lcc != lcc) return z + c + 1;
       for (int q = c + 1 + tid; q < rows; q += BT) PU[(int64_t)c * n + q] = ddiv(PU[(int64_t)c * n + q], lcc);
       __syncthreads();
     }
     for (int r = tid >> 5; r < rows; r += BT / 32)
       for (int q = tid & 31; q < sb; q += 32)
-        if (q <= r) A[(int64_t)(z + r) * lda + z + q] = PL[(int64_t)r * s + q];
+        if (q <= r) A[(int64_t)(z + r) * lda + z + q] = PL[(int64_t)r * ldp + q];
     for (int r = tid >> 5; r < sb; r += BT / 32)
       for (int q = r + 1 + (tid & 31); q < rows; q += 32) A[(int64_t)(z + r) * lda + z + q] = PU[(int64_t)r * n + q];
     // delayed update of the trailing square: rows/cols [z+sb, n)
     const int mt = n - z - sb;
-    for (int r = tid >> 5; r < mt; r += BT / 32) {
-      const T *Pi = PL + (int64_t)(sb + r) * s;
-      for (int q = tid & 31; q < mt; q += 32) {
-        T sij = T(0);
-#pragma unroll 4
-        for (int k = 0; k < sb; ++k) sij = madd(sij, Pi[k], PU[(int64_t)k * n + sb + q], exact);
-        T *a = A + (int64_t)(z + sb + r) * lda + z + sb + q;
-        *a = *a - sij;
-      }
-    }
+    const int64_t base = (int64_t)(z + sb) * lda + z + sb;
+    block_update<T, EXACT, false>(
+        mt, mt, sb, [&](int r, int k) { return PL[(int64_t)(sb + r) * ldp + k]; },
+        [&](int q, int k) { return PU[(int64_t)k * n + sb + q]; },
+        [&](int r, int q) { return A + base + (int64_t)r * lda + q; });
     __syncthreads();
   }
   return 0;
@@ -336,8 +400,9 @@ __global__ void __launch_bounds__(BT, 2) batched_chol_kernel(Plan plan, int64_t 
           for (int q = threadIdx.x & 31; q < n; q += 32)
             L[(int64_t)r * ldl + q] = q <= r ? A[(int64_t)r * lda + q] : T(0);
         __syncthreads();
-        const int sp = (int)min64(s, smem_elems / n);  // panel width that fits
-        info = chol_panel_path<T, EXACT>(L, ldl, n, max(1, sp), buf, red);
+        const int sp = max(1, (int)min64(s, smem_elems / n));  // panel width that fits
+        const int ldp = (int64_t)n * (sp | 1) <= smem_elems ? (sp | 1) : sp;
+        info = chol_panel_path<T, EXACT>(L, ldl, n, sp, buf, ldp, red);
         __syncthreads();
       }
     }
@@ -387,10 +452,11 @@ __global__ void __launch_bounds__(BT, 2) batched_lu_kernel(Plan plan, int64_t sm
           for (int r = threadIdx.x >> 5; r < n; r += BT / 32)
             for (int q = threadIdx.x & 31; q < n; q += 32) LU[(int64_t)r * ldo + q] = A[(int64_t)r * lda + q];
         __syncthreads();
-        const int sp = (int)min64(s, smem_elems / (2 * (int64_t)n));  // both panels fit
+        const int sp = max(1, (int)min64(s, smem_elems / (2 * (int64_t)n)));  // both panels fit
+        const int ldp = (int64_t)n * ((sp | 1) + sp) <= smem_elems ? (sp | 1) : sp;
         T *PL = buf;
-        T *PU = buf + (int64_t)n * max(1, sp);
-        info = lu_panel_path<T, EXACT>(LU, ldo, n, max(1, sp), PL, PU);
+        T *PU = buf + (int64_t)n * ldp;
+        info = lu_panel_path<T, EXACT>(LU, ldo, n, sp, PL, ldp, PU);
         __syncthreads();
       }
     }

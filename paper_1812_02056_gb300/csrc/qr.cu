@@ -408,17 +408,22 @@ __global__ void __launch_bounds__(SK_NT)
   }
 }
 
-// C[i][j] = sum_z W[z][i][j], z ascending (the K slices of gemm_tn_kernel)
+// C[i][j] = sum_z W[z][i][j] over the K slices of the gemm_tn kernels: one
+// warp per element, lane l adding slices l, l + 32, ... in ascending order,
+// then a fixed shuffle tree (deterministic: the same bits on every run).
 template <typename T>
 __global__ void sum_slices_kernel(T *__restrict__ C, int64_t ldc, const T *__restrict__ W,
                                   int64_t M, int64_t N, int slices, const int *status) {
   if (*reinterpret_cast<const volatile int *>(status) != 0) return;
   const int64_t total = M * N;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    T acc = W[e];
-    for (int z = 1; z < slices; ++z) acc += W[(int64_t)z * total + e];
-    C[(e / N) * ldc + e % N] = acc;
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < total; e += warps) {
+    T acc = T(0);
+    for (int z = lane; z < slices; z += 32) acc += W[(int64_t)z * total + e];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) C[(e / N) * ldc + e % N] = acc;
   }
 }
 
@@ -488,7 +493,7 @@ cudaError_t launch_gemm_tn(T *C, int64_t ldc, const T *X, int64_t ldx, const T *
       gemm_tn_skinny_kernel<T><<<(unsigned)slices, SK_NT, smem, st>>>(
           W, M * N, X, ldx, Y, ldy, (int)M, (int)N, K, kslice, status);
       const int64_t total = M * N;
-      const unsigned g2 = (unsigned)std::min<int64_t>((total + 255) / 256, 4096);
+      const unsigned g2 = (unsigned)std::min<int64_t>((total * 32 + 255) / 256, 8192);
       sum_slices_kernel<T><<<g2, 256, 0, st>>>(C, ldc, W, M, N, (int)slices, status);
       count_launch(2);
       return cudaGetLastError();
@@ -523,7 +528,7 @@ cudaError_t launch_gemm_tn(T *C, int64_t ldc, const T *X, int64_t ldx, const T *
   gemm_tn_kernel<T, false><<<grid, 256, 0, st>>>(W, N, M * N, X, ldx, Y, ldy, M, N, K, kslice,
                                                   status);
   const int64_t total = M * N;
-  const unsigned g2 = (unsigned)std::min<int64_t>((total + 255) / 256, 4096);
+  const unsigned g2 = (unsigned)std::min<int64_t>((total * 32 + 255) / 256, 8192);
   sum_slices_kernel<T><<<g2, 256, 0, st>>>(C, ldc, W, M, N, (int)slices, status);
   count_launch(2);
   return cudaGetLastError();
