@@ -534,6 +534,24 @@ gb_status gb_lu_batched_plan(gb_handle *h, int64_t count, const int64_t *n, void
  */
 gb_status gb_batched_tune(gb_handle *h, gb_dtype dt, int64_t n_max, int *steps_out, void *stream);
 
+/*
+ * gb_tune_step -- the autotuner of the step for gb_chol_factor (kind 0),
+ * gb_lu_factor (kind 1) and gb_qr_factor (kind 2) called with s = 0: times
+ * the factorization of the n x n test matrix n I + ones in dtype dt for
+ * s in {32, 64, 128, 256, 512, 1024} (below n) and inner steps {16, 32, 64}
+ * (QR: {8, 16, 32}, the column-step width GB_OPT_QR_INNER_STEP), and keeps
+ * the fastest pair in the handle for every order in [2^k, 2^(k+1)) with
+ * k = floor(log2 n).  Later calls with s = 0 in that range use the pair (the
+ * inner step for that call only); without a tuned entry s = 0 keeps its
+ * fixed default.  s_out and b_out (optional) receive the pair.  This is the
+ * paper's remark that s may be chosen per problem (Sec. 2, last
+ * paragraph) made empirical.  Allocates and frees its test matrices;
+ * synchronous.  Errors: -2 kind, -3 dtype, -4 n outside [2, 65536],
+ * GB_ERR_UNSUPPORTED for a QR dtype other than GB_F64/GB_F32.
+ */
+gb_status gb_tune_step(gb_handle *h, int kind, gb_dtype dt, int64_t n, int64_t *s_out,
+                       int64_t *b_out, void *stream);
+
 #ifdef __cplusplus
 } /* extern "C" */
 #endif

@@ -89,6 +89,7 @@ SIGNATURES = {
     "gb_chol_factor": (_I32, [_P, _I64, _I64, _I32, _P, _I64, _P, _I64, _P, _P]),
     "gb_lu_factor": (_I32, [_P, _I64, _I64, _I32, _P, _I64, _P, _I64, _P, _P]),
     "gb_qr_factor": (_I32, [_P, _I64, _I64, _I32, _P, _I64, _P, _I64, _P, _I64, _P, _P]),
+    "gb_tune_step": (_I32, [_P, _I32, _I32, _I64, _P, _P, _P]),
     "gb_chol_solve": (_I32, [_P, _I64, _I64, _I32, _P, _I64, _P, _I64, _P, _I64, _P, _I64,
                              ctypes.POINTER(RefineOpts), ctypes.POINTER(SolveStats), _P]),
     "gb_lu_solve": (_I32, [_P, _I64, _I64, _I32, _P, _I64, _P, _I64, _P, _I64, _P, _I64,
@@ -256,6 +257,15 @@ class Handle:
     def gb_lu_factor(self, n, s, dt, A, lda, LU, ldlu, info, stream=None) -> int:
         return self.lib.gb_lu_factor(self.h, n, s, dt, _ptr(A), lda, _ptr(LU), ldlu, _ptr(info),
                                      _stream_ptr(stream))
+
+    def tune_step(self, kind: str, dtype: str, n: int, stream=None):
+        """Autotune (s, inner step) for ``kind`` in {"chol", "lu", "qr"} at
+        order ``n``; returns the pair, which later ``s = 0`` calls use."""
+        kinds = {"chol": 0, "lu": 1, "qr": 2}
+        s_out, b_out = ctypes.c_int64(), ctypes.c_int64()
+        check(self.lib.gb_tune_step(self.h, kinds[kind], DTYPES[dtype], int(n), ctypes.byref(s_out),
+                                    ctypes.byref(b_out), _stream_ptr(stream)), "gb_tune_step")
+        return s_out.value, b_out.value
 
     def gb_qr_factor(self, n, s, dt, A, lda, Q, ldq, R, ldr, info, stream=None) -> int:
         return self.lib.gb_qr_factor(self.h, n, s, dt, _ptr(A), lda, _ptr(Q), ldq, _ptr(R), ldr,

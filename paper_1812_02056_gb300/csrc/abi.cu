@@ -161,6 +161,18 @@ struct InfoWord {
   }
 };
 
+int tune_bucket(int64_t n) {
+  int b = 0;
+  while (b < 31 && ((int64_t)2 << b) <= n) ++b;
+  return b;  // floor(log2 n) for n >= 1
+}
+
+// The tuned (s, inner step) for a call with s = 0, or {0, 0} when none.
+gb_handle::TunedStep tuned_step(const gb_handle *h, int kind, gb_dtype dt, int64_t n) {
+  if (kind < 0 || kind > 2 || dt < 0 || dt > 4 || n < 1) return {};
+  return h->tuned[kind][dt][tune_bucket(n)];
+}
+
 int64_t default_step(gb_dtype dt, int64_t n) {
   (void)n;
   switch (dt) {
@@ -640,7 +652,21 @@ gb_status qr_common(gb_handle *h, int64_t n, int64_t s, gb_dtype dt, const void 
   DeviceGuard g(h->device);
   std::lock_guard<std::mutex> lk(h->mu);
   cudaStream_t st = (cudaStream_t)stream;
-  if (s == 0) s = 64;
+  const int saved_inner = h->qr_inner;
+  struct RestoreInner {
+    gb_handle *h;
+    int v;
+    ~RestoreInner() { h->qr_inner = v; }
+  } restore_inner{h, saved_inner};
+  if (s == 0) {
+    const auto t = tuned_step(h, 2, dt, n);
+    if (t.s > 0) {
+      s = t.s;
+      h->qr_inner = t.b;
+    } else {
+      s = 64;
+    }
+  }
   InfoWord iw;
   gb_status r = iw.init(h, info, st);
   if (r != GB_OK) return r;
@@ -684,7 +710,23 @@ gb_status factor_common(bool is_lu, gb_handle *h, int64_t n, int64_t s, gb_dtype
   DeviceGuard g(h->device);
   std::lock_guard<std::mutex> lk(h->mu);
   cudaStream_t st = (cudaStream_t)stream;
-  if (s == 0) s = default_step(dt, n);
+  // s = 0: the step gb_tune_step chose for this order, with its inner step
+  // for this call only; else the default rule
+  const int saved_inner = h->inner_step;
+  struct RestoreInner {
+    gb_handle *h;
+    int v;
+    ~RestoreInner() { h->inner_step = v; }
+  } restore_inner{h, saved_inner};
+  if (s == 0) {
+    const auto t = tuned_step(h, is_lu ? 1 : 0, dt, n);
+    if (t.s > 0) {
+      s = t.s;
+      h->inner_step = t.b;
+    } else {
+      s = default_step(dt, n);
+    }
+  }
   const size_t ein = elem_size_input(dt), ef = elem_size_factor(dt);
   const bool alias = (A == (const void *)L);
   if (alias && ein != ef) return -7;  // in place needs one element type
@@ -1404,6 +1446,106 @@ extern "C" gb_status gb_batched_tune(gb_handle *h, gb_dtype dt, int64_t n_max, i
   cudaStreamSynchronize(st);
   cudaFree(info);
   cudaFree(buf);
+  return r;
+}
+
+extern "C" gb_status gb_tune_step(gb_handle *h, int kind, gb_dtype dt, int64_t n, int64_t *s_out,
+                                  int64_t *b_out, void *stream) {
+  if (!h) return -1;
+  if (kind < 0 || kind > 2) return -2;
+  if (!valid_dtype(dt)) return -3;
+  if (kind == 2 && dt != GB_F64 && dt != GB_F32) return GB_ERR_UNSUPPORTED;
+  if (n < 2 || n > 65536) return -4;
+  DeviceGuard g(h->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t ein = elem_size_input(dt), ef = kind == 2 ? ein : elem_size_factor(dt);
+  const size_t nn = (size_t)n * (size_t)n;
+  void *A = nullptr, *F = nullptr, *R = nullptr;
+  int *info = nullptr;
+  gb_status r = GB_OK;
+  if (cudaMalloc(&A, nn * ein) != cudaSuccess || cudaMalloc(&F, nn * ef) != cudaSuccess ||
+      (kind == 2 && cudaMalloc(&R, nn * ef) != cudaSuccess) ||
+      cudaMalloc((void **)&info, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    r = GB_ERR_NOMEM;
+  }
+  // the test matrix n I + ones: symmetric positive definite, every leading
+  // minor positive, full rank
+  if (r == GB_OK) {
+    const cudaError_t e = ein == 8 ? launch_fill_spd<double>((double *)A, (int64_t)nn, 1, (int)n, st)
+                                   : launch_fill_spd<float>((float *)A, (int64_t)nn, 1, (int)n, st);
+    if (e != cudaSuccess) {
+      record_cuda_error(e, "fill_spd", __FILE__, __LINE__);
+      r = GB_ERR_CUDA;
+    }
+  }
+  const int64_t steps[] = {32, 64, 128, 256, 512, 1024};
+  const int inner_chol[] = {16, 32, 64}, inner_qr[] = {8, 16, 32};
+  const int *inner = kind == 2 ? inner_qr : inner_chol;
+  int &knob = kind == 2 ? h->qr_inner : h->inner_step;
+  int saved;
+  {
+    std::lock_guard<std::mutex> lk(h->mu);
+    saved = knob;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  int64_t best_s = 0;
+  int best_b = 0;
+  for (int64_t s : steps) {
+    if (r != GB_OK) break;
+    if (s >= n && s != steps[0]) break;
+    for (int bi = 0; bi < 3 && r == GB_OK; ++bi) {
+      const int b = inner[bi];
+      if (b > s) continue;
+      {
+        std::lock_guard<std::mutex> lk(h->mu);
+        knob = b;
+      }
+      float ms = 0;
+      for (int rep = 0; rep < 2 && r == GB_OK; ++rep) {  // rep 0 warms up
+        cudaEventRecord(e0, st);
+        if (kind == 0)
+          r = gb_chol_factor(h, n, s, dt, A, n, F, n, info, stream);
+        else if (kind == 1)
+          r = gb_lu_factor(h, n, s, dt, A, n, F, n, info, stream);
+        else
+          r = gb_qr_factor(h, n, s, dt, A, n, F, n, R, n, info, stream);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+          cudaGetLastError();
+          r = GB_ERR_CUDA;
+        }
+        cudaEventElapsedTime(&ms, e0, e1);
+      }
+      int host_info = 0;
+      if (r == GB_OK && cudaMemcpy(&host_info, info, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        r = GB_ERR_CUDA;
+      if (r == GB_OK && host_info == 0 && ms < best) {
+        best = ms;
+        best_s = s;
+        best_b = b;
+      }
+    }
+  }
+  {
+    std::lock_guard<std::mutex> lk(h->mu);
+    knob = saved;
+    if (r == GB_OK && best_s > 0) h->tuned[kind][dt][tune_bucket(n)] = {best_s, best_b};
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(A);
+  cudaFree(F);
+  if (R) cudaFree(R);
+  if (info) cudaFree(info);
+  if (r == GB_OK && best_s == 0) r = GB_ERR_BREAKDOWN;
+  if (r == GB_OK) {
+    if (s_out) *s_out = best_s;
+    if (b_out) *b_out = best_b;
+  }
   return r;
 }
 

@@ -55,6 +55,11 @@ struct gb_handle {
   int use_graphs = 1;
   int tc_update = 2;
   int qr_inner = 16;          // inner step of the QR panel (GB_OPT_QR_INNER_STEP)
+  // steps chosen by gb_tune_step for s = 0: [kind: chol, LU, QR][dtype][floor(log2 n)]
+  struct TunedStep {
+    int64_t s = 0;
+    int b = 0;
+  } tuned[3][5][32];
   int64_t spin_limit = 1 << 26;
   int *d_status = nullptr;   // scratch status word for host `info` pointers
   int *d_err = nullptr;      // device error word (DEV_ERR_*)
