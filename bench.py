@@ -467,8 +467,11 @@ def run_mixed(args):
            "results": {}}
     stream = torch.cuda.current_stream()
     xref = None
+    wanted = args.mixed_dtypes.split(",")
     for name, s in [("f64", args.s_f64), ("f32", args.s_mixed), ("mix_f16", args.s_mixed),
                     ("mix_bf16", args.s_mixed), ("mix_bf16x3", args.s_mixed)]:
+        if name not in wanted:
+            continue
         dt = binding.DTYPES[name]
         Ain = A.float() if name == "f32" else A
         L = torch.empty((n, n), dtype=torch.float64 if name == "f64" else torch.float32, device=dev)
@@ -858,6 +861,7 @@ def main():
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--s-f64", type=int, default=256)
     ap.add_argument("--s-mixed", type=int, default=1024)
+    ap.add_argument("--mixed-dtypes", default="f64,f32,mix_f16,mix_bf16,mix_bf16x3")
     ap.add_argument("--batch-count", type=int, default=10000)
     ap.add_argument("--batch-cpu-sample", type=int, default=200)
     ap.add_argument("--served-count", type=int, default=400)

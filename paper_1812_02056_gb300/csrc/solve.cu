@@ -200,48 +200,78 @@ __global__ void __launch_bounds__(TB)
   for (int i = 0; i < TB; ++i) D[i * TB + j] = (i < rows && j < rows) ? y[i] : Tc(0);
 }
 
+// Solve with inverted diagonal blocks.  CTAs take block rows in dependence
+// order from a ticket (position t: block t forward, block nb - 1 - t
+// backward).  `progress` counts the finished positions; blocks finish in
+// order, so progress = p means positions 0 .. p - 1 are solved.  A CTA
+// applies every solved block's contribution in chunks of up to TRSM_KC
+// columns -- as many blocks as are finished when it looks, so most of its
+// row panel is applied with one wait, not one wait per block -- and the
+// op(F) part of the next chunk is loaded before the wait (it does not depend
+// on X).  Then X_b = Dinv[b] (B_b - contributions), stored, and published.
+// Every wait is bounded by a %globaltimer deadline; on expiry the kernel
+// raises DEV_ERR_TIMEOUT in the error word, every other waiter sees it and
+// returns, and the host reports GB_ERR_TIMEOUT.
+template <typename Tc>
+struct TrsmCfg {
+  static constexpr int KC = 512 / (int)sizeof(Tc);  // columns per chunk: 128 FP32, 64 FP64
+};
+constexpr int TRSM_NRC = 16;  // right-hand sides per pass
+
 template <typename Tf, typename Tc>
 __global__ void __launch_bounds__(TRSM_THREADS)
     trsm_inv_kernel(const Tf *__restrict__ F, int64_t ldf, const Tc *__restrict__ Dinv, double *B,
-                    int64_t ldb, int64_t n, int64_t nrhs, int kind, int *ticket, int *flags,
-                    unsigned epoch, int *err, long long wait_ns) {
-  __shared__ Tc Fs[TB][TB + 1];
-  __shared__ Tc Xs[TB][NRC + 1];
-  __shared__ int s_ib, s_abort;
+                    int64_t ldb, int64_t n, int64_t nrhs, int kind, int *ticket, int *progress,
+                    int *err, long long wait_ns) {
+  constexpr int KC = TrsmCfg<Tc>::KC;
+  static_assert(KC % TB == 0, "whole blocks per chunk");
+  __shared__ Tc Fs[TB][KC + 1];
+  __shared__ Tc Xs[KC][TRSM_NRC + 1];
+  __shared__ int s_t, s_avail, s_abort;
   const int tid = threadIdx.x;
   const int nb = (int)((n + TB - 1) / TB);
   const bool fwd = (kind == TRSM_LOWER);
   if (tid == 0) {
-    const int t = atomicAdd(ticket, 1);
-    s_ib = fwd ? t : nb - 1 - t;
+    s_t = atomicAdd(ticket, 1);
     s_abort = 0;
   }
   __syncthreads();
-  const int ib = s_ib;
-  if (ib < 0 || ib >= nb) return;
+  const int t = s_t;
+  if (t < 0 || t >= nb) return;
+  const int ib = fwd ? t : nb - 1 - t;
   const int64_t r0 = (int64_t)ib * TB;
   const int rows = (int)min64(TB, n - r0);
-  const int tr = tid / (NRC / 4), tc = (tid % (NRC / 4)) * 4;
+  const int tr = tid >> 3, tc = (tid & 7) * 2;  // 32 rows x 16 columns, 2 per thread
 
-  for (int64_t c0 = 0; c0 < nrhs; c0 += NRC) {
-    const int cols = (int)min64(NRC, nrhs - c0);
-    Tc acc[4];
+  // columns of op(F) for positions [p0, p0 + w): forward blocks p0 .. p0+w-1,
+  // backward blocks nb-p0-w .. nb-p0-1 (both as one ascending column range)
+  auto col_range = [&](int p0, int w, int64_t &c0, int64_t &c1) {
+    const int64_t b0 = fwd ? p0 : nb - p0 - w;
+    c0 = b0 * TB;
+    c1 = min64((b0 + w) * TB, n);
+  };
+
+  for (int64_t rc0 = 0; rc0 < nrhs; rc0 += TRSM_NRC) {
+    const int cols = (int)min64(TRSM_NRC, nrhs - rc0);
+    Tc acc[2];
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-      acc[q] = (tr < rows && tc + q < cols) ? (Tc)B[(r0 + tr) * ldb + c0 + tc + q] : Tc(0);
-    for (int step = 0; step < (fwd ? ib : nb - 1 - ib); ++step) {
-      const int jb = fwd ? step : nb - 1 - step;
-      // load the off-diagonal block before waiting: it does not depend on X
-      const int64_t k0 = (int64_t)jb * TB;
-      const int kr = (int)min64(TB, n - k0);
-      for (int idx = tid; idx < TB * TB; idx += TRSM_THREADS) {
-        const int i = idx / TB, k = idx % TB;
-        Fs[i][k] = (i < rows && k < kr) ? (Tc)op_elem(F, ldf, kind, r0 + i, k0 + k) : Tc(0);
+    for (int q = 0; q < 2; ++q)
+      acc[q] = (tr < rows && tc + q < cols) ? (Tc)B[(r0 + tr) * ldb + rc0 + tc + q] : Tc(0);
+    int done = 0;
+    while (done < t) {
+      // op(F) for the next chunk, before waiting for its X
+      const int wmax = min(KC / TB, t - done);
+      int64_t f0, f1;
+      col_range(done, wmax, f0, f1);
+      const int fw = (int)(f1 - f0);
+      for (int idx = tid; idx < TB * KC; idx += TRSM_THREADS) {
+        const int i = idx / KC, k = idx % KC;
+        Fs[i][k] = (i < rows && k < fw) ? (Tc)op_elem(F, ldf, kind, r0 + i, f0 + k) : Tc(0);
       }
       if (tid == 0) {
-        int spins = 0;
+        int spins = 0, avail = ld_acquire(progress);
         const long long t0 = (long long)globaltimer_ns();
-        while (ld_acquire(&flags[jb]) != (int)epoch) {
+        while (avail <= done) {
           if ((++spins & 255) == 0) {
             if (ld_acquire(err) & DEV_ERR_TIMEOUT) {
               s_abort = 1;
@@ -253,53 +283,66 @@ __global__ void __launch_bounds__(TRSM_THREADS)
               break;
             }
           }
+          avail = ld_acquire(progress);
         }
+        s_avail = avail;
       }
       __syncthreads();
       if (s_abort) return;
-      for (int idx = tid; idx < TB * NRC; idx += TRSM_THREADS) {
-        const int k = idx / NRC, c = idx % NRC;
-        Xs[k][c] = (k < kr && c < cols) ? (Tc)__ldcg(&B[(k0 + k) * ldb + c0 + c]) : Tc(0);
+      // the finished positions of this chunk; in the backward sweep the chunk
+      // was laid out for wmax positions, so an unfinished prefix is skipped
+      const int w = min(wmax, s_avail - done);
+      int64_t c0, c1;
+      col_range(done, w, c0, c1);
+      const int koff = (int)(c0 - f0), kw = (int)(c1 - c0);
+      for (int idx = tid; idx < KC * TRSM_NRC; idx += TRSM_THREADS) {
+        const int k = idx / TRSM_NRC, c = idx % TRSM_NRC;
+        Xs[k][c] = (k < kw && c < cols) ? (Tc)__ldcg(&B[(c0 + k) * ldb + rc0 + c]) : Tc(0);
       }
       __syncthreads();
-#pragma unroll 8
-      for (int k = 0; k < TB; ++k) {
-        const Tc f = Fs[tr][k];
+      for (int k = 0; k < kw; ++k) {
+        const Tc f = Fs[tr][koff + k];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[q] = acc[q] - f * Xs[k][tc + q];
+        for (int q = 0; q < 2; ++q) acc[q] = acc[q] - f * Xs[k][tc + q];
       }
       __syncthreads();
+      done += w;
     }
     // X_b = Dinv[b] * acc
     const Tc *D = Dinv + (int64_t)ib * TB * TB;
     for (int idx = tid; idx < TB * TB; idx += TRSM_THREADS) Fs[idx / TB][idx % TB] = D[idx];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) Xs[tr][tc + q] = acc[q];
+    for (int q = 0; q < 2; ++q) Xs[tr][tc + q] = acc[q];
     __syncthreads();
-    Tc out[4] = {Tc(0), Tc(0), Tc(0), Tc(0)};
+    Tc out[2] = {Tc(0), Tc(0)};
 #pragma unroll 8
     for (int k = 0; k < TB; ++k) {
       const Tc d = Fs[tr][k];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) out[q] = out[q] + d * Xs[k][tc + q];
+      for (int q = 0; q < 2; ++q) out[q] = out[q] + d * Xs[k][tc + q];
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-      if (tr < rows && tc + q < cols) B[(r0 + tr) * ldb + c0 + tc + q] = (double)out[q];
+    for (int q = 0; q < 2; ++q)
+      if (tr < rows && tc + q < cols) B[(r0 + tr) * ldb + rc0 + tc + q] = (double)out[q];
     __syncthreads();
   }
   if (tid == 0) {
     __threadfence();
-    st_release(&flags[ib], (int)epoch);
+    st_release(progress, t + 1);  // every position before t is finished: progress was t
   }
 }
 
 // ------------------------------------------------------------- residual
-// R = B - A X in FP64.  CTA: RES_ROWS rows, X staged in shared memory by
-// k-chunks; warp w handles rows w, w + 8, ...; lanes split k.
-constexpr int RES_ROWS = 32;
-constexpr int RES_KC = 128;
+// R = B - A X in FP64: a tiled product.  A CTA of RES_THREADS threads owns
+// RES_ROWS rows and RES_NC right-hand sides; k-chunks of A (rows x RES_KC, padded to
+// an odd stride) and of X (RES_KC x RES_NC) are staged in shared memory with
+// coalesced loads; thread (r, g) accumulates row r against columns
+// 4g .. 4g + 3 over k in ascending order.  Each element of A is read once;
+// the kernel is bound by the FP64 units (16 multiply-adds per element).
+constexpr int RES_ROWS = 16;  // n / 16 CTAs: even load over the SMs
+constexpr int RES_KC = 64;
 constexpr int RES_NC = 16;
+constexpr int RES_THREADS = RES_ROWS * RES_NC / 4;  // 64
 
 __device__ __forceinline__ double finite_abs(double v) {
   const double a = fabs(v);
@@ -311,55 +354,53 @@ __device__ __forceinline__ void atomic_max_nonneg(double *addr, double v) {
   atomicMax(reinterpret_cast<long long *>(addr), __double_as_longlong(v));
 }
 
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(RES_THREADS)
     residual_kernel(const double *__restrict__ A, int64_t lda, const double *__restrict__ X,
                     int64_t ldx, const double *__restrict__ B, int64_t ldb, double *__restrict__ R,
                     int64_t ldr, int64_t n, int64_t nrhs, double *norms) {
-  __shared__ double Xs[RES_KC][RES_NC];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  __shared__ double As[RES_ROWS][RES_KC + 1];
+  __shared__ __align__(16) double Xs[RES_KC][RES_NC];
+  const int tid = threadIdx.x;
+  const int r = tid >> 2, g = tid & 3;  // row, group of 4 columns
   const int64_t i0 = (int64_t)blockIdx.x * RES_ROWS;
   for (int64_t c0 = 0; c0 < nrhs; c0 += RES_NC) {
     const int cols = (int)min64(RES_NC, nrhs - c0);
-    double acc[RES_ROWS / 8][RES_NC];
-#pragma unroll
-    for (int a = 0; a < RES_ROWS / 8; ++a)
-#pragma unroll
-      for (int c = 0; c < RES_NC; ++c) acc[a][c] = 0.0;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
     for (int64_t k0 = 0; k0 < n; k0 += RES_KC) {
       const int kr = (int)min64(RES_KC, n - k0);
       __syncthreads();
-      for (int idx = tid; idx < RES_KC * RES_NC; idx += 256) {
+      for (int idx = tid; idx < RES_ROWS * RES_KC; idx += RES_THREADS) {
+        const int ii = idx / RES_KC, k = idx % RES_KC;
+        const int64_t i = i0 + ii;
+        As[ii][k] = (i < n && k < kr) ? A[i * lda + k0 + k] : 0.0;
+      }
+      for (int idx = tid; idx < RES_KC * RES_NC; idx += RES_THREADS) {
         const int k = idx / RES_NC, c = idx % RES_NC;
         Xs[k][c] = (k < kr && c < cols) ? X[(k0 + k) * ldx + c0 + c] : 0.0;
       }
       __syncthreads();
-#pragma unroll
-      for (int a = 0; a < RES_ROWS / 8; ++a) {
-        const int64_t i = i0 + warp + 8 * a;
-        if (i >= n) continue;
-        for (int k = lane; k < kr; k += 32) {
-          const double av = A[i * lda + k0 + k];
-#pragma unroll
-          for (int c = 0; c < RES_NC; ++c) acc[a][c] = fma(av, Xs[k][c], acc[a][c]);
-        }
+#pragma unroll 8
+      for (int k = 0; k < RES_KC; ++k) {
+        const double av = As[r][k];
+        const double2 x01 = *reinterpret_cast<const double2 *>(&Xs[k][4 * g]);
+        const double2 x23 = *reinterpret_cast<const double2 *>(&Xs[k][4 * g + 2]);
+        acc[0] = fma(av, x01.x, acc[0]);
+        acc[1] = fma(av, x01.y, acc[1]);
+        acc[2] = fma(av, x23.x, acc[2]);
+        acc[3] = fma(av, x23.y, acc[3]);
       }
     }
+    const int64_t i = i0 + r;
 #pragma unroll
-    for (int a = 0; a < RES_ROWS / 8; ++a) {
-      const int64_t i = i0 + warp + 8 * a;
-#pragma unroll
-      for (int c = 0; c < RES_NC; ++c) {
-        double v = acc[a][c];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0 && i < n && c < cols) {
-          const double r = B[i * ldb + c0 + c] - v;
-          R[i * ldr + c0 + c] = r;
-          if (norms) {  // a non-finite value counts as +inf in every norm
-            atomic_max_nonneg(&norms[c0 + c], finite_abs(r));                       // ||r||_inf
-            atomic_max_nonneg(&norms[nrhs + c0 + c], finite_abs(X[i * ldx + c0 + c]));  // ||x||_inf
-            atomic_max_nonneg(&norms[2 * nrhs + c0 + c], finite_abs(B[i * ldb + c0 + c]));
-          }
+    for (int q = 0; q < 4; ++q) {
+      const int c = 4 * g + q;
+      if (i < n && c < cols) {
+        const double rv = B[i * ldb + c0 + c] - acc[q];
+        R[i * ldr + c0 + c] = rv;
+        if (norms) {  // a non-finite value counts as +inf in every norm
+          atomic_max_nonneg(&norms[c0 + c], finite_abs(rv));                          // ||r||_inf
+          atomic_max_nonneg(&norms[nrhs + c0 + c], finite_abs(X[i * ldx + c0 + c]));  // ||x||_inf
+          atomic_max_nonneg(&norms[2 * nrhs + c0 + c], finite_abs(B[i * ldb + c0 + c]));
         }
       }
     }
@@ -502,12 +543,12 @@ cudaError_t launch_trsm_inv(const Tf *F, int64_t ldf, const Tf *Dinv, double *B,
   if (n <= 0 || nrhs <= 0) return cudaSuccess;
   const int64_t nb = (n + TB - 1) / TB;
   if (nb + 1 > SYNC_WORDS) return cudaErrorInvalidValue;
-  cudaError_t e = cudaMemsetAsync(sync, 0, sizeof(int), st);  // ticket
+  (void)epoch;
+  cudaError_t e = cudaMemsetAsync(sync, 0, 2 * sizeof(int), st);  // ticket, progress
   if (e != cudaSuccess) return e;
   const long long wait_ns = (long long)spin_limit * 100LL;
   trsm_inv_kernel<Tf, Tf><<<(unsigned)nb, TRSM_THREADS, 0, st>>>(F, ldf, Dinv, B, ldb, n, nrhs, kind,
-                                                                 sync, sync + 1, epoch, err,
-                                                                 wait_ns);
+                                                                 sync, sync + 1, err, wait_ns);
   count_launch();
   return cudaGetLastError();
 }
@@ -520,8 +561,8 @@ cudaError_t launch_residual(const double *A, int64_t lda, const double *X, int64
     cudaError_t e = cudaMemsetAsync(norms, 0, sizeof(double) * 3 * nrhs, st);
     if (e != cudaSuccess) return e;
   }
-  residual_kernel<<<(unsigned)ceil_div(n, RES_ROWS), 256, 0, st>>>(A, lda, X, ldx, B, ldb, R, ldr,
-                                                                  n, nrhs, norms);
+  residual_kernel<<<(unsigned)ceil_div(n, RES_ROWS), RES_THREADS, 0, st>>>(A, lda, X, ldx, B, ldb,
+                                                                          R, ldr, n, nrhs, norms);
   count_launch();
   return cudaGetLastError();
 }
