@@ -473,6 +473,10 @@ def run_mixed(args):
         if name not in wanted:
             continue
         dt = binding.DTYPES[name]
+        tuned = None
+        if args.tune:
+            tuned = h.tune_step("chol", name, n)  # later s = 0 calls use the tuned pair
+            s = 0
         Ain = A.float() if name == "f32" else A
         L = torch.empty((n, n), dtype=torch.float64 if name == "f64" else torch.float32, device=dev)
         info = torch.zeros(1, dtype=torch.int32, device=dev)
@@ -497,7 +501,8 @@ def run_mixed(args):
         fm, sm, st, it, eta, inf = runs[-1]
         if name == "f64":
             xref = X.clone()
-        res = {"s": s, "factor_ms": fm, "solve_ms": sm, "time_to_solution_ms": fm + sm,
+        res = {"s": s if tuned is None else {"tuned_s": tuned[0], "tuned_inner": tuned[1]},
+               "factor_ms": fm, "solve_ms": sm, "time_to_solution_ms": fm + sm,
                "status": st, "info": inf, "ir_iterations": it, "eta": eta,
                "factor_gflops": n ** 3 / 3 / (fm * 1e-3) / 1e9,
                "factor_phase_ms": {k: round(v["ms"], 3) for k, v in prof.items()},
@@ -862,6 +867,8 @@ def main():
     ap.add_argument("--s-f64", type=int, default=256)
     ap.add_argument("--s-mixed", type=int, default=1024)
     ap.add_argument("--mixed-dtypes", default="f64,f32,mix_f16,mix_bf16,mix_bf16x3")
+    ap.add_argument("--tune", action="store_true",
+                    help="mixed mode: pick (s, inner step) with gb_tune_step, then factor with s = 0")
     ap.add_argument("--batch-count", type=int, default=10000)
     ap.add_argument("--batch-cpu-sample", type=int, default=200)
     ap.add_argument("--served-count", type=int, default=400)

@@ -150,15 +150,23 @@ __global__ void __launch_bounds__(TRSM_THREADS)
 }
 
 // ---------------------------------------- solve with inverted diagonal blocks
-// Pre-pass: Dinv[b] = inverse of the b-th TB x TB diagonal block of op(F),
-// one CTA of TB threads per block, thread j computing column j of the
+// Pre-pass: Dinv[b] = inverse of the b-th BS x BS diagonal block of op(F),
+// one CTA of BS threads per block, thread j computing column j of the
 // inverse by substitution.  The solve below then finishes a block with the
 // small product X_b = Dinv[b] * (b - contributions): no dependent chain of
-// length TB on the critical path.
+// length BS on the critical path.  BS = 64 for FP32 factors (half the
+// sequential blocks of a sweep), 32 for FP64 (whose multiply-adds on the
+// critical path are slow on this GPU).
+template <typename Tc>
+constexpr int inv_block() {
+  return sizeof(Tc) == 4 ? 64 : 32;
+}
+
 template <typename Tf, typename Tc>
-__global__ void __launch_bounds__(TB)
+__global__ void __launch_bounds__(inv_block<Tc>())
     diag_inv_kernel(const Tf *__restrict__ F, int64_t ldf, int64_t n, int kind,
                     Tc *__restrict__ Dinv) {
+  constexpr int TB = inv_block<Tc>();
   __shared__ Tc Bs[TB][TB + 1];
   const int b = blockIdx.x, j = threadIdx.x;
   const int64_t r0 = (int64_t)b * TB;
@@ -200,36 +208,45 @@ __global__ void __launch_bounds__(TB)
   for (int i = 0; i < TB; ++i) D[i * TB + j] = (i < rows && j < rows) ? y[i] : Tc(0);
 }
 
-// Solve with inverted diagonal blocks.  CTAs take block rows in dependence
-// order from a ticket (position t: block t forward, block nb - 1 - t
-// backward).  `progress` counts the finished positions; blocks finish in
-// order, so progress = p means positions 0 .. p - 1 are solved.  A CTA
-// applies every solved block's contribution in chunks of up to TRSM_KC
+// Solve with inverted diagonal blocks.  CTAs take block rows (BS rows) in
+// dependence order from a ticket (position t: block t forward, block
+// nb - 1 - t backward).  `progress` counts the finished positions; blocks
+// finish in order, so progress = p means positions 0 .. p - 1 are solved.  A
+// CTA applies every solved block's contribution in chunks of up to KC
 // columns -- as many blocks as are finished when it looks, so most of its
 // row panel is applied with one wait, not one wait per block -- and the
 // op(F) part of the next chunk is loaded before the wait (it does not depend
-// on X).  Then X_b = Dinv[b] (B_b - contributions), stored, and published.
-// Every wait is bounded by a %globaltimer deadline; on expiry the kernel
-// raises DEV_ERR_TIMEOUT in the error word, every other waiter sees it and
-// returns, and the host reports GB_ERR_TIMEOUT.
+// on X), as is the CTA's Dinv block.  Then X_b = Dinv[b] (B_b -
+// contributions), stored, and published.  Every wait is bounded by a
+// %globaltimer deadline; on expiry the kernel raises DEV_ERR_TIMEOUT in the
+// error word, every other waiter sees it and returns, and the host reports
+// GB_ERR_TIMEOUT.
 template <typename Tc>
 struct TrsmCfg {
-  static constexpr int KC = 512 / (int)sizeof(Tc);  // columns per chunk: 128 FP32, 64 FP64
+  static constexpr int BS = inv_block<Tc>();
+  static constexpr int KC = sizeof(Tc) == 4 ? 256 : 64;  // columns per chunk
+  static constexpr int NRC = 16;                         // right-hand sides per pass
+  static constexpr int TPR = TRSM_THREADS / BS;          // threads per row
+  static constexpr int OPT = NRC / TPR;                  // outputs per thread
+  static constexpr size_t SMEM =
+      sizeof(Tc) * ((size_t)BS * (KC + 1) + (size_t)KC * (NRC + 1) + (size_t)BS * (BS + 1));
 };
-constexpr int TRSM_NRC = 16;  // right-hand sides per pass
 
 template <typename Tf, typename Tc>
 __global__ void __launch_bounds__(TRSM_THREADS)
     trsm_inv_kernel(const Tf *__restrict__ F, int64_t ldf, const Tc *__restrict__ Dinv, double *B,
                     int64_t ldb, int64_t n, int64_t nrhs, int kind, int *ticket, int *progress,
                     int *err, long long wait_ns) {
-  constexpr int KC = TrsmCfg<Tc>::KC;
-  static_assert(KC % TB == 0, "whole blocks per chunk");
-  __shared__ Tc Fs[TB][KC + 1];
-  __shared__ Tc Xs[KC][TRSM_NRC + 1];
+  using C = TrsmCfg<Tc>;
+  constexpr int BS = C::BS, KC = C::KC, NRC = C::NRC, OPT = C::OPT;
+  static_assert(KC % BS == 0 && C::TPR * OPT == NRC, "layout");
+  extern __shared__ __align__(16) unsigned char trsm_smem[];
+  Tc *Fs = reinterpret_cast<Tc *>(trsm_smem);   // [BS][KC + 1]
+  Tc *Xs = Fs + (size_t)BS * (KC + 1);           // [KC][NRC + 1]
+  Tc *Ds = Xs + (size_t)KC * (NRC + 1);          // [BS][BS + 1]
   __shared__ int s_t, s_avail, s_abort;
   const int tid = threadIdx.x;
-  const int nb = (int)((n + TB - 1) / TB);
+  const int nb = (int)((n + BS - 1) / BS);
   const bool fwd = (kind == TRSM_LOWER);
   if (tid == 0) {
     s_t = atomicAdd(ticket, 1);
@@ -239,34 +256,38 @@ __global__ void __launch_bounds__(TRSM_THREADS)
   const int t = s_t;
   if (t < 0 || t >= nb) return;
   const int ib = fwd ? t : nb - 1 - t;
-  const int64_t r0 = (int64_t)ib * TB;
-  const int rows = (int)min64(TB, n - r0);
-  const int tr = tid >> 3, tc = (tid & 7) * 2;  // 32 rows x 16 columns, 2 per thread
+  const int64_t r0 = (int64_t)ib * BS;
+  const int rows = (int)min64(BS, n - r0);
+  const int tr = tid / C::TPR, tc = (tid % C::TPR) * OPT;
+  {
+    const Tc *D = Dinv + (int64_t)ib * BS * BS;
+    for (int idx = tid; idx < BS * BS; idx += TRSM_THREADS) Ds[(idx / BS) * (BS + 1) + idx % BS] = D[idx];
+  }
 
   // columns of op(F) for positions [p0, p0 + w): forward blocks p0 .. p0+w-1,
   // backward blocks nb-p0-w .. nb-p0-1 (both as one ascending column range)
   auto col_range = [&](int p0, int w, int64_t &c0, int64_t &c1) {
     const int64_t b0 = fwd ? p0 : nb - p0 - w;
-    c0 = b0 * TB;
-    c1 = min64((b0 + w) * TB, n);
+    c0 = b0 * BS;
+    c1 = min64((b0 + w) * BS, n);
   };
 
-  for (int64_t rc0 = 0; rc0 < nrhs; rc0 += TRSM_NRC) {
-    const int cols = (int)min64(TRSM_NRC, nrhs - rc0);
-    Tc acc[2];
+  for (int64_t rc0 = 0; rc0 < nrhs; rc0 += NRC) {
+    const int cols = (int)min64(NRC, nrhs - rc0);
+    Tc acc[OPT];
 #pragma unroll
-    for (int q = 0; q < 2; ++q)
+    for (int q = 0; q < OPT; ++q)
       acc[q] = (tr < rows && tc + q < cols) ? (Tc)B[(r0 + tr) * ldb + rc0 + tc + q] : Tc(0);
     int done = 0;
     while (done < t) {
       // op(F) for the next chunk, before waiting for its X
-      const int wmax = min(KC / TB, t - done);
+      const int wmax = min(KC / BS, t - done);
       int64_t f0, f1;
       col_range(done, wmax, f0, f1);
       const int fw = (int)(f1 - f0);
-      for (int idx = tid; idx < TB * KC; idx += TRSM_THREADS) {
+      for (int idx = tid; idx < BS * KC; idx += TRSM_THREADS) {
         const int i = idx / KC, k = idx % KC;
-        Fs[i][k] = (i < rows && k < fw) ? (Tc)op_elem(F, ldf, kind, r0 + i, f0 + k) : Tc(0);
+        Fs[i * (KC + 1) + k] = (i < rows && k < fw) ? (Tc)op_elem(F, ldf, kind, r0 + i, f0 + k) : Tc(0);
       }
       if (tid == 0) {
         int spins = 0, avail = ld_acquire(progress);
@@ -294,35 +315,46 @@ __global__ void __launch_bounds__(TRSM_THREADS)
       const int w = min(wmax, s_avail - done);
       int64_t c0, c1;
       col_range(done, w, c0, c1);
-      const int koff = (int)(c0 - f0), kw = (int)(c1 - c0);
-      for (int idx = tid; idx < KC * TRSM_NRC; idx += TRSM_THREADS) {
-        const int k = idx / TRSM_NRC, c = idx % TRSM_NRC;
-        Xs[k][c] = (k < kw && c < cols) ? (Tc)__ldcg(&B[(c0 + k) * ldb + rc0 + c]) : Tc(0);
+      const int kw = (int)(c1 - c0);
+      for (int idx = tid; idx < KC * NRC; idx += TRSM_THREADS) {
+        const int k = idx / NRC, c = idx % NRC;
+        Xs[k * (NRC + 1) + c] = (k < kw && c < cols) ? (Tc)__ldcg(&B[(c0 + k) * ldb + rc0 + c]) : Tc(0);
       }
       __syncthreads();
-      for (int k = 0; k < kw; ++k) {
-        const Tc f = Fs[tr][koff + k];
+      // blocks in position order (backward: descending), columns ascending
+      // inside a block: the same order for any chunking, so results do not
+      // depend on how far the other blocks had got
+      for (int pb = 0; pb < w; ++pb) {
+        const int64_t b0 = fwd ? (int64_t)(done + pb) : (int64_t)(nb - 1 - done - pb);
+        const int64_t bc0 = b0 * BS;
+        const int bw = (int)min64(BS, n - bc0);
+        const Tc *Fr = Fs + tr * (KC + 1) + (bc0 - f0);
+        const Tc *Xb = Xs + (bc0 - c0) * (NRC + 1) + tc;
+        for (int k = 0; k < bw; ++k) {
+          const Tc f = Fr[k];
+          const Tc *xk = Xb + k * (NRC + 1);
 #pragma unroll
-        for (int q = 0; q < 2; ++q) acc[q] = acc[q] - f * Xs[k][tc + q];
+          for (int q = 0; q < OPT; ++q) acc[q] = acc[q] - f * xk[q];
+        }
       }
       __syncthreads();
       done += w;
     }
     // X_b = Dinv[b] * acc
-    const Tc *D = Dinv + (int64_t)ib * TB * TB;
-    for (int idx = tid; idx < TB * TB; idx += TRSM_THREADS) Fs[idx / TB][idx % TB] = D[idx];
 #pragma unroll
-    for (int q = 0; q < 2; ++q) Xs[tr][tc + q] = acc[q];
+    for (int q = 0; q < OPT; ++q) Xs[tr * (NRC + 1) + tc + q] = acc[q];
     __syncthreads();
-    Tc out[2] = {Tc(0), Tc(0)};
-#pragma unroll 8
-    for (int k = 0; k < TB; ++k) {
-      const Tc d = Fs[tr][k];
+    Tc out[OPT];
 #pragma unroll
-      for (int q = 0; q < 2; ++q) out[q] = out[q] + d * Xs[k][tc + q];
+    for (int q = 0; q < OPT; ++q) out[q] = Tc(0);
+#pragma unroll 8
+    for (int k = 0; k < BS; ++k) {
+      const Tc d = Ds[tr * (BS + 1) + k];
+#pragma unroll
+      for (int q = 0; q < OPT; ++q) out[q] = out[q] + d * Xs[k * (NRC + 1) + tc + q];
     }
 #pragma unroll
-    for (int q = 0; q < 2; ++q)
+    for (int q = 0; q < OPT; ++q)
       if (tr < rows && tc + q < cols) B[(r0 + tr) * ldb + rc0 + tc + q] = (double)out[q];
     __syncthreads();
   }
@@ -522,16 +554,18 @@ cudaError_t launch_trsm(const Tf *F, int64_t ldf, double *B, int64_t ldb, int64_
 }
 
 size_t trsm_inv_bytes(int64_t n, size_t esz) {
-  const int64_t nb = (n + TB - 1) / TB;
-  return (size_t)nb * TB * TB * esz;
+  const int64_t bs = esz == 4 ? inv_block<float>() : inv_block<double>();
+  const int64_t nb = (n + bs - 1) / bs;
+  return (size_t)nb * bs * bs * esz;
 }
 
 template <typename Tf>
 cudaError_t launch_diag_inv(const Tf *F, int64_t ldf, int64_t n, int kind, Tf *Dinv,
                             cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  const int64_t nb = (n + TB - 1) / TB;
-  diag_inv_kernel<Tf, Tf><<<(unsigned)nb, TB, 0, st>>>(F, ldf, n, kind, Dinv);
+  constexpr int BS = inv_block<Tf>();
+  const int64_t nb = (n + BS - 1) / BS;
+  diag_inv_kernel<Tf, Tf><<<(unsigned)nb, BS, 0, st>>>(F, ldf, n, kind, Dinv);
   count_launch();
   return cudaGetLastError();
 }
@@ -541,14 +575,17 @@ cudaError_t launch_trsm_inv(const Tf *F, int64_t ldf, const Tf *Dinv, double *B,
                             int64_t n, int64_t nrhs, int kind, int *sync, unsigned epoch, int *err,
                             int64_t spin_limit, cudaStream_t st) {
   if (n <= 0 || nrhs <= 0) return cudaSuccess;
-  const int64_t nb = (n + TB - 1) / TB;
-  if (nb + 1 > SYNC_WORDS) return cudaErrorInvalidValue;
+  using C = TrsmCfg<Tf>;
+  const int64_t nb = (n + C::BS - 1) / C::BS;
   (void)epoch;
+  static const cudaError_t attr = cudaFuncSetAttribute(
+      trsm_inv_kernel<Tf, Tf>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+  if (attr != cudaSuccess) return attr;
   cudaError_t e = cudaMemsetAsync(sync, 0, 2 * sizeof(int), st);  // ticket, progress
   if (e != cudaSuccess) return e;
   const long long wait_ns = (long long)spin_limit * 100LL;
-  trsm_inv_kernel<Tf, Tf><<<(unsigned)nb, TRSM_THREADS, 0, st>>>(F, ldf, Dinv, B, ldb, n, nrhs, kind,
-                                                                 sync, sync + 1, err, wait_ns);
+  trsm_inv_kernel<Tf, Tf><<<(unsigned)nb, TRSM_THREADS, C::SMEM, st>>>(
+      F, ldf, Dinv, B, ldb, n, nrhs, kind, sync, sync + 1, err, wait_ns);
   count_launch();
   return cudaGetLastError();
 }
