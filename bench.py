@@ -836,6 +836,51 @@ def run_qr(args):
     return 0
 
 
+def run_left(args):
+    """Left-looking tile accumulation against the right-looking delayed
+    update, tensor-core Cholesky (mix_bf16, mix_f16) at n for several s:
+    factor time, TFLOP/s (n^3/3), per-phase device time, backward error."""
+    import torch
+
+    from paper_1812_02056_gb300 import _build, binding, inputs
+    _build.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    h = binding.Handle(0)
+    n = args.n
+    A = inputs.spd_gram(n, inputs.seed_for(inputs.W_MIXED, 5), device=dev)
+    out = {"mode": "left", "n": n, "results": {}}
+    L = torch.empty((n, n), dtype=torch.float32, device=dev)
+    info = torch.zeros(1, dtype=torch.int32, device=dev)
+    for dtype in ("mix_bf16", "mix_f16"):
+        dt = binding.DTYPES[dtype]
+        for s in [int(v) for v in args.left_steps.split(",")]:
+            for left in (0, 1):
+                h.set_option(binding.GB_OPT_LEFT_LOOKING, left)
+                binding.check(h.gb_chol_factor(n, s, dt, A, n, L, n, info), "warm-up")
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(args.reps):
+                    h.gb_chol_factor(n, s, dt, A, n, L, n, info)
+                e1.record()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / args.reps
+                h.set_option(binding.GB_OPT_PROFILE, 1)
+                h.profile_read()
+                h.gb_chol_factor(n, s, dt, A, n, L, n, info)
+                prof = h.profile_read().as_dict()
+                h.set_option(binding.GB_OPT_PROFILE, 0)
+                out["results"][f"{dtype}_s{s}_{'left' if left else 'right'}"] = {
+                    "ms": ms, "tflops": n ** 3 / 3 / (ms * 1e-3) / 1e12, "info": int(info.item()),
+                    "backward_error": h.backward_error(A, L, dtype),
+                    "phase_ms": {k: round(v["ms"], 3) for k, v in prof.items()}}
+        h.set_option(binding.GB_OPT_LEFT_LOOKING, 0)
+    print(json.dumps(out))
+    h.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -852,12 +897,13 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--mode", choices=["chol", "update", "mixed", "batched", "served", "strassen",
-                                       "qr"],
+                                       "qr", "left"],
                     default="chol",
                     help="chol: the benchmark line; update: the tensor-core rank-s update "
                          "alone; mixed: FP64 vs mixed-precision time to solution")
     ap.add_argument("--ks", default="256,512,1024,2048")
     ap.add_argument("--qr-steps", default="32,64,128,256")
+    ap.add_argument("--left-steps", default="256,512,1024")
     ap.add_argument("--qr-inner", default="8,16,32")
     ap.add_argument("--update-dtype", default="mix_bf16")
     ap.add_argument("--tc-modes", default="1,2",
@@ -888,6 +934,8 @@ def main():
         return run_served(args)
     if args.mode == "qr":
         return run_qr(args)
+    if args.mode == "left":
+        return run_left(args)
     if args.mode == "strassen":
         return run_strassen(args)
     return run_ours(args)

@@ -146,11 +146,21 @@ typedef enum gb_option {
                                (its diagonal halves stay classical); also
                                gb_rank_update without the lower mask.
                                Default 0.                                    */
-  GB_OPT_QR_INNER_STEP = 9  /* gb_qr_factor: columns per panel launch, each
+  GB_OPT_QR_INNER_STEP = 9, /* gb_qr_factor: columns per panel launch, each
                                orthogonalised against the earlier ones of its
                                inner block one at a time (default 16, range
                                1..256; capped by s and by the panel's shared
                                memory, 200 KiB per CTA for ceil(n/8) rows).  */
+  GB_OPT_LEFT_LOOKING = 10  /* 1: gb_chol_factor with GB_MIX_BF16 / GB_MIX_F16
+                               (tensor-core update on, s a multiple of 64,
+                               s < n, n a multiple of 8) accumulates the
+                               update of each s-block column from all earlier
+                               columns in one tensor-core product (K = z, the
+                               columns done) read from a resident 16-bit copy
+                               of L, instead of updating the trailing matrix
+                               every s columns: the same sums, grouped by
+                               tile; FP32 traffic of the working matrix once
+                               per block column.  Default 0.                 */
 } gb_option;
 
 gb_status gb_set_option(gb_handle *h, gb_option opt, int64_t value);

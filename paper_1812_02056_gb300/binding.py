@@ -38,6 +38,7 @@ GB_OPT_BATCHED_EXACT = 6
 GB_OPT_LOOKAHEAD = 7
 GB_OPT_STRASSEN = 8
 GB_OPT_QR_INNER_STEP = 9
+GB_OPT_LEFT_LOOKING = 10
 
 
 class GbError(RuntimeError):

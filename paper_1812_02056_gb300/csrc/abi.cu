@@ -413,6 +413,78 @@ gb_status chol_blocked_on(gb_handle *h, int64_t n, int64_t s, T *W, int64_t ld, 
   return GB_OK;
 }
 
+// ---------------------------------------------------- left-looking variant
+// The same sums as Algorithm 1 in another grouping (tile accumulation): the
+// trailing matrix is never updated; when the s-block [z, z + sb) is reached,
+// its columns receive every earlier column's contribution at once,
+//   W[z.., z..pe) -= L[z.., 0..z) L[z..pe, 0..z)^T   (K = z >> s),
+// on the tensor cores from a resident 16-bit copy of L (each finished block
+// column is rounded once into it), then the column steps run as before.
+// Mixed dtypes with one 16-bit plane (BF16, FP16); s a multiple of 64.
+template <typename T, typename Tc>
+gb_status chol_left_on(gb_handle *h, int64_t n, int64_t s, T *W, int64_t ld, int *status,
+                       gb_dtype dt, cudaStream_t st) {
+  static_assert(sizeof(T) == 4, "tensor-core path: FP32 working matrix");
+  const int64_t b = std::max(1, std::min(64, h->inner_step));
+  const int64_t ldp = (n + 63) / 64 * 64;  // resident copy: rows of ldp 16-bit elements
+  const bool f16 = dt == GB_MIX_F16;
+  gb_status r = ws_reserve(h, WS_LEFT, (size_t)n * (size_t)ldp * 2 + 256, st);
+  if (r != GB_OK) return r;
+  uint16_t *Lp = reinterpret_cast<uint16_t *>(h->ws[WS_LEFT].ptr);
+  for (int64_t z = 0; z < n; z += s) {
+    const int64_t sb = std::min(s, n - z);
+    const int64_t pe = z + sb;
+    if (z > 0) {
+      PhaseTimer t(h, st, GB_PHASE_UPDATE, update_flops(n - z, sb, z, true),
+                   (double)8 * lower_count(n - z, sb, 0) + 2.0 * (double)(n - z + sb) * z);
+      TcUpdateArgs a{};
+      a.C = reinterpret_cast<float *>(W + z * ld + z);
+      a.ldc = ld;
+      a.M = n - z;
+      a.N = sb;
+      a.K = z;
+      a.nn = false;
+      a.lower = true;
+      a.diag = 0;
+      a.f16 = f16;
+      a.split = 1;
+      a.status = status;
+      a.err = h->d_err;
+      a.spin_limit = h->spin_limit;
+      a.cluster = h->tc_update;
+      a.xpack = Lp + z * ldp;  // rows z.., columns 0..z of the resident L
+      a.ypack = Lp + z * ldp;  // its first sb rows
+      a.ldxp = ldp;
+      a.ldyp = ldp;
+      GB_CUDA_TRY(launch_update_tc(a, st));
+    }
+    for (int64_t j0 = z; j0 < pe; j0 += b) {
+      const int bw = (int)std::min(b, pe - j0);
+      const int64_t r0 = j0 + bw;
+      {
+        PhaseTimer t(h, st, GB_PHASE_PANEL,
+                     (double)bw * bw * bw / 3.0 + (double)(n - r0) * bw * bw,
+                     (double)bw * bw * 4 + 2.0 * (double)(n - r0) * bw * 4);
+        GB_CUDA_TRY((launch_chol_panel<T, true>(W, ld, j0, bw, n - r0, status, h->d_arrivals, st)));
+      }
+      if (r0 < pe) {
+        PhaseTimer t(h, st, GB_PHASE_INNER, update_flops(n - r0, pe - r0, bw, true),
+                     update_bytes(n - r0, pe - r0, bw, true, 4));
+        const T *R = W + r0 * ld + j0;
+        r = chol_update<T>(h, dt, W + r0 * ld + r0, R, R, ld, n - r0, pe - r0, bw, status,
+                           WS_PANEL, st);
+        if (r != GB_OK) return r;
+      }
+    }
+    if (pe < n) {  // round the finished block column into the resident copy
+      PhaseTimer t(h, st, GB_PHASE_COPY, 0.0, (double)(n - z) * sb * 6);
+      GB_CUDA_TRY(launch_pack16(reinterpret_cast<const float *>(W + z * ld + z), ld, n - z, sb,
+                                Lp + z * ldp + z, ldp, f16, st));
+    }
+  }
+  return GB_OK;
+}
+
 // C -= X Y (LU's R_L R_U, full block), tensor cores for the mixed dtypes,
 // CUDA cores (optionally one Strassen level) otherwise.
 template <typename T>
@@ -773,8 +845,11 @@ gb_status factor_common(bool is_lu, gb_handle *h, int64_t n, int64_t s, gb_dtype
       GB_CUDA_TRY((launch_copy_matrix<double, float>((const double *)sa.dev, sa.ldd, W, ld, n,
                                                      lower_only, st)));
       tcopy.reset();
-      r = is_lu ? lu_blocked<float, double>(h, n, s, W, ld, iw.dev, dt, st)
-                : chol_blocked<float, double>(h, n, s, W, ld, iw.dev, dt, st);
+      const bool left = !is_lu && h->left_looking && h->tc_update && split_of(dt) == 1 &&
+                        s % 64 == 0 && s < n && n % 8 == 0;
+      r = is_lu  ? lu_blocked<float, double>(h, n, s, W, ld, iw.dev, dt, st)
+          : left ? chol_left_on<float, double>(h, n, s, W, ld, iw.dev, dt, st)
+                 : chol_blocked<float, double>(h, n, s, W, ld, iw.dev, dt, st);
       break;
     }
   }
@@ -1076,6 +1151,7 @@ gb_status gb_set_option(gb_handle *h, gb_option opt, int64_t v) {
       if (v < 1 || v > 256) return -3;
       h->qr_inner = (int)v;
       return GB_OK;
+    case GB_OPT_LEFT_LOOKING: h->left_looking = v ? 1 : 0; return GB_OK;
     default: return -2;
   }
 }
@@ -1093,6 +1169,7 @@ gb_status gb_get_option(gb_handle *h, gb_option opt, int64_t *v) {
     case GB_OPT_LOOKAHEAD: *v = h->lookahead; return GB_OK;
     case GB_OPT_STRASSEN: *v = h->strassen; return GB_OK;
     case GB_OPT_QR_INNER_STEP: *v = h->qr_inner; return GB_OK;
+    case GB_OPT_LEFT_LOOKING: *v = h->left_looking; return GB_OK;
     default: return -2;
   }
 }

@@ -55,6 +55,7 @@ struct gb_handle {
   int use_graphs = 1;
   int tc_update = 2;
   int qr_inner = 16;          // inner step of the QR panel (GB_OPT_QR_INNER_STEP)
+  int left_looking = 0;       // GB_OPT_LEFT_LOOKING
   // steps chosen by gb_tune_step for s = 0: [kind: chol, LU, QR][dtype][floor(log2 n)]
   struct TunedStep {
     int64_t s = 0;
@@ -67,7 +68,7 @@ struct gb_handle {
   unsigned long long *d_arrivals = nullptr;  // arrival counter of the fused panel kernel
   double *d_scalars = nullptr;  // small FP64 reduction outputs
   unsigned sync_epoch = 0;
-  gb::Workspace ws[9];       // named workspaces, see WS_* below
+  gb::Workspace ws[10];      // named workspaces, see WS_* below
   std::mutex mu;
   // GB_OPT_PROFILE: event pairs recorded around launches, read later
   int profile = 0;
@@ -104,7 +105,7 @@ struct gb_handle {
 namespace gb {
 
 enum { WS_STAGE = 0, WS_PANEL = 1, WS_SOLVE = 2, WS_MISC = 3, WS_DINV = 4, WS_PANEL2 = 5,
-       WS_STRAS = 6, WS_STRAS2 = 7, WS_QR = 8 };
+       WS_STRAS = 6, WS_STRAS2 = 7, WS_QR = 8, WS_LEFT = 9 };
 constexpr int SYNC_WORDS = 1 << 16;
 
 // Make sure workspace `slot` holds >= bytes; waits for `stream` before
@@ -184,7 +185,15 @@ struct TcUpdateArgs {
   void *pack;        // workspace for the packed operands
   size_t pack_bytes;
   int cluster;       // 2: CTA pairs with pair MMAs (256 x 256 tiles); else 1
+  // resident operands (optional): 16-bit rows of X and Y, leading dimensions
+  // in elements; then X, Y and pack are not used and K must be a multiple of 64
+  const void *xpack, *ypack;
+  int64_t ldxp, ldyp;
 };
+// Round an FP32 rows x K block to 16-bit rows of ldo elements (K rounded up
+// to 64 with zeros) -- the resident operand layout of the update.
+cudaError_t launch_pack16(const float *X, int64_t ldx, int64_t rows, int64_t K, void *out,
+                          int64_t ldo, bool f16, cudaStream_t st);
 size_t tc_pack_bytes(int64_t M, int64_t N, int64_t K, bool nn, int split);
 cudaError_t launch_update_tc(const TcUpdateArgs &a, cudaStream_t st);
 bool tc_supported(int device);

@@ -621,18 +621,18 @@ __device__ __forceinline__ void split_planes(float x, T16 (&p)[3]) {
   p[2] = to16<T16>(r1 - from16<T16>(p[1]));
 }
 
-// out[i][t * Kp + k] = plane_t(X[i * ldx + k]) for k < K, 0 for K <= k < Kp.
+// out[i * ldo + t * Kp + k] = plane_t(X[i * ldx + k]) for k < K, 0 for K <= k < Kp.
 template <typename T16>
 __global__ void pack_rows_kernel(const float *__restrict__ X, int64_t ldx, int64_t rows,
                                  int64_t K, int64_t Kp, int terms, uint32_t code,
-                                 T16 *__restrict__ out) {
+                                 T16 *__restrict__ out, int64_t ldo) {
   const int64_t total = rows * Kp;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = e / Kp, k = e % Kp;
     T16 p[3];
     split_planes<T16>(k < K ? X[i * ldx + k] : 0.0f, p);
-    T16 *o = out + i * (Kp * terms) + k;
+    T16 *o = out + i * ldo + k;
     for (int t = 0; t < terms; ++t) o[t * Kp] = p[(code >> (2 * t)) & 3u];
   }
 }
@@ -682,16 +682,16 @@ EncodeTiledFn encode_fn() {
 }
 
 // 2-D map over a dense rows x cols 16-bit K-major buffer, box 64 x box_rows.
-bool make_operand_map(CUtensorMap *map, void *base, int64_t rows, int64_t cols, int box_rows,
-                      bool f16) {
+bool make_operand_map(CUtensorMap *map, const void *base, int64_t rows, int64_t cols,
+                      int box_rows, bool f16, int64_t row_stride) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return false;
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+  cuuint64_t strides[1] = {(cuuint64_t)row_stride * 2};
   cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = enc(map, f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
-                   base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
@@ -736,7 +736,8 @@ cudaError_t pack_operands(const TcUpdateArgs &a, int64_t Kp, int terms, T16 *xp,
   {
     const int64_t total = a.M * Kp;
     const unsigned grid = (unsigned)std::min<int64_t>((total + threads - 1) / threads, 65535 * 4);
-    pack_rows_kernel<T16><<<grid, threads, 0, st>>>(a.X, a.ldx, a.M, a.K, Kp, terms, cx, xp);
+    pack_rows_kernel<T16><<<grid, threads, 0, st>>>(a.X, a.ldx, a.M, a.K, Kp, terms, cx, xp,
+                                                    Kp * terms);
     count_launch();
   }
   if (!same) {
@@ -747,7 +748,8 @@ cudaError_t pack_operands(const TcUpdateArgs &a, int64_t Kp, int terms, T16 *xp,
     } else {
       const int64_t total = a.N * Kp;
       const unsigned grid = (unsigned)std::min<int64_t>((total + threads - 1) / threads, 65535 * 4);
-      pack_rows_kernel<T16><<<grid, threads, 0, st>>>(a.Y, a.ldy, a.N, a.K, Kp, terms, cy, yp);
+      pack_rows_kernel<T16><<<grid, threads, 0, st>>>(a.Y, a.ldy, a.N, a.K, Kp, terms, cy, yp,
+                                                      Kp * terms);
     }
     count_launch();
   }
@@ -824,6 +826,26 @@ bool tc_supported(int device) {
   return major == 10 && minor == 3 && encode_fn() != nullptr;
 }
 
+cudaError_t launch_pack16(const float *X, int64_t ldx, int64_t rows, int64_t K, void *out,
+                          int64_t ldo, bool f16, cudaStream_t st) {
+  if (rows <= 0 || K <= 0) return cudaSuccess;
+  const int one[1] = {0};
+  const uint32_t code = code_of(one, 1);
+  const int64_t Kp = round_up(K, BK);
+  if (ldo < Kp) return cudaErrorInvalidValue;
+  const int threads = 256;
+  const int64_t total = rows * Kp;
+  const unsigned grid = (unsigned)std::min<int64_t>((total + threads - 1) / threads, 65535 * 4);
+  if (f16)
+    pack_rows_kernel<__half><<<grid, threads, 0, st>>>(X, ldx, rows, K, Kp, 1, code,
+                                                       reinterpret_cast<__half *>(out), ldo);
+  else
+    pack_rows_kernel<__nv_bfloat16><<<grid, threads, 0, st>>>(
+        X, ldx, rows, K, Kp, 1, code, reinterpret_cast<__nv_bfloat16 *>(out), ldo);
+  count_launch();
+  return cudaGetLastError();
+}
+
 size_t tc_pack_bytes(int64_t M, int64_t N, int64_t K, bool nn, int split) {
   const int64_t Kp = round_up(std::max<int64_t>(K, 1), BK);
   (void)nn;
@@ -840,15 +862,32 @@ cudaError_t launch_update_tc(const TcUpdateArgs &a, cudaStream_t st) {
   const int terms = split_terms(a.split);
   const int64_t Kp = round_up(a.K, BK), Ke = Kp * terms;
   if (Ke / BK > INT32_MAX) return cudaErrorInvalidValue;
-  if (tc_pack_bytes(a.M, a.N, a.K, a.nn, a.split) > a.pack_bytes) return cudaErrorInvalidValue;
-  const bool same = !a.nn && terms == 1 && a.X == a.Y && a.ldx == a.ldy && a.M == a.N;
-  uint8_t *base = reinterpret_cast<uint8_t *>(a.pack);
-  void *xp = base;
-  void *yp = same ? base : base + (size_t)round_up(a.M, 8) * Ke * 2;
-  cudaError_t e = a.f16 ? pack_operands<__half>(a, Kp, terms, (__half *)xp, (__half *)yp, same, st)
-                        : pack_operands<__nv_bfloat16>(a, Kp, terms, (__nv_bfloat16 *)xp,
-                                                       (__nv_bfloat16 *)yp, same, st);
-  if (e != cudaSuccess) return e;
+  const void *xp, *yp;
+  int64_t xstride = Ke, ystride = Ke;
+  if (a.xpack) {
+    // operands already resident as 16-bit rows (one plane, K a multiple of
+    // 64, rows 16-byte aligned): no packing
+    if (terms != 1 || a.K % BK != 0 || !a.ypack) return cudaErrorInvalidValue;
+    if ((reinterpret_cast<uintptr_t>(a.xpack) & 15) || (reinterpret_cast<uintptr_t>(a.ypack) & 15) ||
+        (a.ldxp & 7) || (a.ldyp & 7) || a.ldxp < a.K || a.ldyp < a.K)
+      return cudaErrorInvalidValue;
+    xp = a.xpack;
+    yp = a.ypack;
+    xstride = a.ldxp;
+    ystride = a.ldyp;
+  } else {
+    if (tc_pack_bytes(a.M, a.N, a.K, a.nn, a.split) > a.pack_bytes) return cudaErrorInvalidValue;
+    const bool same = !a.nn && terms == 1 && a.X == a.Y && a.ldx == a.ldy && a.M == a.N;
+    uint8_t *base = reinterpret_cast<uint8_t *>(a.pack);
+    void *xw = base;
+    void *yw = same ? base : base + (size_t)round_up(a.M, 8) * Ke * 2;
+    cudaError_t e = a.f16 ? pack_operands<__half>(a, Kp, terms, (__half *)xw, (__half *)yw, same, st)
+                          : pack_operands<__nv_bfloat16>(a, Kp, terms, (__nv_bfloat16 *)xw,
+                                                         (__nv_bfloat16 *)yw, same, st);
+    if (e != cudaSuccess) return e;
+    xp = xw;
+    yp = yw;
+  }
   CUtensorMap map_a, map_b, map_c;
   memset(&map_c, 0, sizeof map_c);
   const int use_tma_store = make_c_map(&map_c, a.C, a.ldc, a.M, a.N) ? 1 : 0;
@@ -876,11 +915,12 @@ cudaError_t launch_update_tc(const TcUpdateArgs &a, cudaStream_t st) {
     if (last >= 0) valid += std::min<int64_t>(nbj, last / BN + 1);
   }
   if (valid == 0) return cudaSuccess;
-  if (!make_operand_map(&map_a, xp, a.M, Ke, BM, a.f16) ||
-      !make_operand_map(&map_b, yp, a.N, Ke, BN / CL, a.f16))
+  if (!make_operand_map(&map_a, xp, a.M, Ke, BM, a.f16, xstride) ||
+      !make_operand_map(&map_b, yp, a.N, Ke, BN / CL, a.f16, ystride))
     return cudaErrorInvalidValue;
   const TcKernelArgs k{map_a, map_b, map_c, a.C, a.ldc, a.M, a.N, (int)(Ke / BK), a.diag,
                        valid, idesc, a.status, a.err, wait_ns, use_tma_store, vec_ok};
+  cudaError_t e;
   if (a.lower)
     e = CL == 2 ? launch_kernel<true, 2>(k, valid, dev, st) : launch_kernel<true, 1>(k, valid, dev, st);
   else
