@@ -97,7 +97,10 @@ typedef enum gb_dtype {
 typedef struct gb_handle gb_handle;
 
 /* Create a handle bound to CUDA device `device` (made current by every call
- * that takes the handle).  Returns GB_ERR_CUDA if the device is absent. */
+ * that takes the handle).  Returns GB_ERR_CUDA if the device is absent.
+ * The handle owns its workspaces and a device memory pool for the copies of
+ * host buffers; the pool keeps its memory between calls (a host-buffer call
+ * at order n holds on to about its own n x n copies) until gb_destroy. */
 gb_status gb_create(gb_handle **h, int device);
 
 /* Wait for the handle's work, release its workspace and free it. */

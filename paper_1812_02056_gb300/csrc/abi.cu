@@ -101,7 +101,7 @@ struct Staged {
   // `p` is host memory, allocate a dense device copy (copying in when
   // copy_in) and remember to copy out at finish() when copy_out.
   gb_status take(const void *p, int64_t r, int64_t c, int64_t l, size_t e, bool copy_in,
-                 bool copy_out, cudaStream_t s) {
+                 bool copy_out, cudaStream_t s, cudaMemPool_t pool) {
     rows = r;
     cols = c;
     ld = l;
@@ -114,7 +114,9 @@ struct Staged {
     }
     ldd = c > 0 ? c : 1;
     size_t bytes = (size_t)std::max<int64_t>(r, 1) * (size_t)ldd * e;
-    if (cudaMallocAsync(&dev, bytes, s) != cudaSuccess) {
+    const cudaError_t ae =
+        pool ? cudaMallocFromPoolAsync(&dev, bytes, pool, s) : cudaMallocAsync(&dev, bytes, s);
+    if (ae != cudaSuccess) {
       cudaGetLastError();
       dev = nullptr;
       return GB_ERR_NOMEM;
@@ -744,9 +746,9 @@ gb_status qr_common(gb_handle *h, int64_t n, int64_t s, gb_dtype dt, const void 
   if (r != GB_OK) return r;
   if (n == 0) return iw.finish(st);
   Staged sa, sq, sr;
-  if ((r = sa.take(A, n, n, lda, esz, true, false, st)) != GB_OK) return r;
-  if ((r = sq.take(Q, n, n, ldq, esz, false, true, st)) != GB_OK) return r;
-  if ((r = sr.take(R, n, n, ldr, esz, false, true, st)) != GB_OK) return r;
+  if ((r = sa.take(A, n, n, lda, esz, true, false, st, h->stage_pool)) != GB_OK) return r;
+  if ((r = sq.take(Q, n, n, ldq, esz, false, true, st, h->stage_pool)) != GB_OK) return r;
+  if ((r = sr.take(R, n, n, ldr, esz, false, true, st, h->stage_pool)) != GB_OK) return r;
   if (dt == GB_F64) {
     GB_CUDA_TRY((launch_copy_matrix<double, double>((const double *)sa.dev, sa.ldd,
                                                     (double *)sq.dev, sq.ldd, n, false, st)));
@@ -810,12 +812,12 @@ gb_status factor_common(bool is_lu, gb_handle *h, int64_t n, int64_t s, gb_dtype
 
   Staged sa, sl;
   if (alias) {
-    if ((r = sl.take(L, n, n, ldl, ef, true, true, st)) != GB_OK) return r;
+    if ((r = sl.take(L, n, n, ldl, ef, true, true, st, h->stage_pool)) != GB_OK) return r;
     sa.dev = sl.dev;
     sa.ldd = sl.ldd;
   } else {
-    if ((r = sa.take(A, n, n, lda, ein, true, false, st)) != GB_OK) return r;
-    if ((r = sl.take(L, n, n, ldl, ef, false, true, st)) != GB_OK) return r;
+    if ((r = sa.take(A, n, n, lda, ein, true, false, st, h->stage_pool)) != GB_OK) return r;
+    if ((r = sl.take(L, n, n, ldl, ef, false, true, st, h->stage_pool)) != GB_OK) return r;
   }
   const int64_t ld = sl.ldd;
   const bool lower_only = !is_lu;
@@ -1006,15 +1008,15 @@ gb_status solve_entry(bool is_lu, gb_handle *h, int64_t n, int64_t nrhs, gb_dtyp
   const size_t ef = elem_size_factor(factor_dt);
   Staged sf, sa, sb, sx;
   gb_status r;
-  if ((r = sf.take(F, n, n, ldf, ef, true, false, st)) != GB_OK) return r;
-  if (A && (r = sa.take(A, n, n, lda, 8, true, false, st)) != GB_OK) return r;
+  if ((r = sf.take(F, n, n, ldf, ef, true, false, st, h->stage_pool)) != GB_OK) return r;
+  if (A && (r = sa.take(A, n, n, lda, 8, true, false, st, h->stage_pool)) != GB_OK) return r;
   if (X == B) {
-    if ((r = sx.take(X, n, nrhs, ldx, 8, true, true, st)) != GB_OK) return r;
+    if ((r = sx.take(X, n, nrhs, ldx, 8, true, true, st, h->stage_pool)) != GB_OK) return r;
     sb.dev = sx.dev;
     sb.ldd = sx.ldd;
   } else {
-    if ((r = sb.take(B, n, nrhs, ldb, 8, true, false, st)) != GB_OK) return r;
-    if ((r = sx.take(X, n, nrhs, ldx, 8, false, true, st)) != GB_OK) return r;
+    if ((r = sb.take(B, n, nrhs, ldb, 8, true, false, st, h->stage_pool)) != GB_OK) return r;
+    if ((r = sx.take(X, n, nrhs, ldx, 8, false, true, st, h->stage_pool)) != GB_OK) return r;
   }
   if (factor_dt == GB_F64)
     r = solve_common<double>(is_lu, h, n, nrhs, (const double *)sf.dev, sf.ldd,
@@ -1097,6 +1099,17 @@ gb_status gb_create(gb_handle **out, int device) {
     gb_destroy(h);
     return GB_ERR_NOMEM;
   }
+  cudaMemPoolProps props{};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = device;
+  if (cudaMemPoolCreate(&h->stage_pool, &props) == cudaSuccess) {
+    uint64_t keep = UINT64_MAX;  // never trim at synchronisation points
+    cudaMemPoolSetAttribute(h->stage_pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  } else {
+    cudaGetLastError();
+    h->stage_pool = nullptr;  // staging falls back to the device's default pool
+  }
   *out = h;
   return GB_OK;
 }
@@ -1123,6 +1136,7 @@ gb_status gb_destroy(gb_handle *h) {
   if (h->ev_join) cudaEventDestroy(h->ev_join);
   if (h->hi) cudaStreamDestroy(h->hi);
   if (h->aux) cudaStreamDestroy(h->aux);
+  if (h->stage_pool) cudaMemPoolDestroy(h->stage_pool);
   delete h;
   return GB_OK;
 }

@@ -56,6 +56,10 @@ struct gb_handle {
   int tc_update = 2;
   int qr_inner = 16;          // inner step of the QR panel (GB_OPT_QR_INNER_STEP)
   int left_looking = 0;       // GB_OPT_LEFT_LOOKING
+  // device copies of host buffers come from this pool, which keeps its
+  // memory between calls (allocating and mapping it again each call costs
+  // more than the copies)
+  cudaMemPool_t stage_pool = nullptr;
   // steps chosen by gb_tune_step for s = 0: [kind: chol, LU, QR][dtype][floor(log2 n)]
   struct TunedStep {
     int64_t s = 0;

@@ -168,44 +168,33 @@ __global__ void __launch_bounds__(inv_block<Tc>())
                     Tc *__restrict__ Dinv) {
   constexpr int TB = inv_block<Tc>();
   __shared__ Tc Bs[TB][TB + 1];
+  __shared__ Tc Ys[TB][TB + 1];  // column j of the inverse, built by thread j
   const int b = blockIdx.x, j = threadIdx.x;
   const int64_t r0 = (int64_t)b * TB;
   const int rows = (int)min64(TB, n - r0);
-  for (int i = 0; i < TB; ++i)
+  for (int i = 0; i < TB; ++i) {
     Bs[i][j] = (i < rows && j < rows) ? (Tc)op_elem(F, ldf, kind, r0 + i, r0 + j) : Tc(0);
+    Ys[i][j] = Tc(0);
+  }
   __syncthreads();
-  Tc y[TB];
-#pragma unroll
-  for (int i = 0; i < TB; ++i) y[i] = Tc(0);
   if (j < rows) {
     if (kind == TRSM_LOWER) {  // lower, non-unit: forward substitution on e_j
-#pragma unroll
-      for (int i = 0; i < TB; ++i) {
-        if (i >= j && i < rows) {
-          Tc v = (i == j) ? Tc(1) : Tc(0);
-#pragma unroll
-          for (int k = 0; k < i; ++k)
-            if (k >= j) v = v - Bs[i][k] * y[k];
-          y[i] = v / Bs[i][i];
-        }
+      for (int i = j; i < rows; ++i) {
+        Tc v = (i == j) ? Tc(1) : Tc(0);
+        for (int k = j; k < i; ++k) v = v - Bs[i][k] * Ys[k][j];
+        Ys[i][j] = v / Bs[i][i];
       }
     } else {  // upper (L^T, or unit U): back substitution on e_j
       const bool unit = (kind == TRSM_UNIT_UPPER);
-#pragma unroll
-      for (int i = TB - 1; i >= 0; --i) {
-        if (i <= j) {
-          Tc v = (i == j) ? Tc(1) : Tc(0);
-#pragma unroll
-          for (int k = i + 1; k < TB; ++k)
-            if (k <= j) v = v - Bs[i][k] * y[k];
-          y[i] = unit ? v : v / Bs[i][i];
-        }
+      for (int i = j; i >= 0; --i) {
+        Tc v = (i == j) ? Tc(1) : Tc(0);
+        for (int k = i + 1; k <= j; ++k) v = v - Bs[i][k] * Ys[k][j];
+        Ys[i][j] = unit ? v : v / Bs[i][i];
       }
     }
   }
   Tc *D = Dinv + (int64_t)b * TB * TB;
-#pragma unroll
-  for (int i = 0; i < TB; ++i) D[i * TB + j] = (i < rows && j < rows) ? y[i] : Tc(0);
+  for (int i = 0; i < TB; ++i) D[i * TB + j] = (i < rows && j < rows) ? Ys[i][j] : Tc(0);
 }
 
 // Solve with inverted diagonal blocks.  CTAs take block rows (BS rows) in
