@@ -429,14 +429,30 @@ def run_update(args):
             e1.record(stream)
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / args.reps
+            launches = (binding.kernel_launches() - l0) / args.reps
+            # the same calls with the profile option: event pairs split each
+            # call into its packing launches and the tensor-core kernel
+            h.set_option(binding.GB_OPT_PROFILE, 1)
+            h.profile_read()
+            for _ in range(args.reps):
+                call()
+            torch.cuda.synchronize()
+            prof = h.profile_read().as_dict()
+            h.set_option(binding.GB_OPT_PROFILE, 0)
             flops = 2.0 * K * m * (m + 1) / 2.0
             cbytes = 8.0 * m * (m + 1) / 2.0  # FP32 lower triangle read + written
             tflops = flops / (ms * 1e-3) / 1e12
+            kern_ms = prof["update"]["ms"] / max(1, prof["update"]["launches"])
+            pack_ms = prof["copy"]["ms"] / max(1, prof["copy"]["launches"])
+            kern_tflops = flops / (kern_ms * 1e-3) / 1e12 if kern_ms > 0 else None
             out["results"].append({
                 "K": K, "m": m, "tc_mode": mode, "ms": ms, "tflops": tflops,
                 "frac_of_bf16_peak": tflops / peaks["bf16_tflops"],
+                "kernel_ms": kern_ms, "pack_ms": pack_ms, "kernel_tflops": kern_tflops,
+                "kernel_frac_of_bf16_peak": (kern_tflops / peaks["bf16_tflops"]
+                                             if kern_tflops else None),
                 "hbm_bound_tflops": peaks["hbm_gbs"] * 1e9 * flops / cbytes / 1e12,
-                "launches_per_call": (binding.kernel_launches() - l0) / args.reps})
+                "launches_per_call": launches})
         h.set_option(binding.GB_OPT_TC_UPDATE, default_mode)
         del C, R
         torch.cuda.empty_cache()

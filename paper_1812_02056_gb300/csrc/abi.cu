@@ -1119,7 +1119,7 @@ gb_status gb_destroy(gb_handle *h) {
   DeviceGuard g(h->device);
   cudaDeviceSynchronize();
   for (auto &r : h->prof_pending) {
-    cudaEventDestroy(r.start);
+    if (r.owns_start) cudaEventDestroy(r.start);
     cudaEventDestroy(r.stop);
   }
   for (auto e : h->prof_pool) cudaEventDestroy(e);
@@ -1661,7 +1661,7 @@ extern "C" gb_status gb_profile_read(gb_handle *h, gb_profile *out) {
       out->flops[rec.phase] += rec.flops;
       out->bytes[rec.phase] += rec.bytes;
     }
-    h->prof_pool.push_back(rec.start);
+    if (rec.owns_start) h->prof_pool.push_back(rec.start);
     h->prof_pool.push_back(rec.stop);
   }
   h->prof_pending.clear();
@@ -1729,7 +1729,34 @@ extern "C" gb_status gb_rank_update(gb_handle *h, gb_dtype dt, int lower, int y_
     if (r != GB_OK) return r;
     a.pack = h->ws[WS_PANEL].ptr;
     a.pack_bytes = h->ws[WS_PANEL].bytes;
+    // under the profile option: packing timed as GB_PHASE_COPY, the
+    // tensor-core kernel as GB_PHASE_UPDATE
+    cudaEvent_t e0 = nullptr, e2 = nullptr;
+    if (h->profile) {
+      e0 = take_event(h);
+      a.packed = take_event(h);
+      e2 = take_event(h);
+      if (!e0 || !a.packed || !e2) {
+        for (cudaEvent_t ev : {e0, a.packed, e2})
+          if (ev) h->prof_pool.push_back(ev);
+        e0 = e2 = a.packed = nullptr;
+      } else {
+        cudaEventRecord(e0, st);
+      }
+    }
     cudaError_t e = launch_update_tc(a, st);
+    if (e0 && e != cudaSuccess) {
+      for (cudaEvent_t ev : {e0, a.packed, e2}) h->prof_pool.push_back(ev);
+    } else if (e0) {
+      cudaEventRecord(e2, st);
+      // FP32 rows read once, 16-bit planes written; C read and written once
+      const double planes = (double)split_of(dt);
+      const double rows = (double)(M + (a.X == a.Y && !nn && M == N ? 0 : N));
+      const double cells = lower ? lower_count(M, N, 0) : (double)M * N;
+      h->prof_pending.push_back({GB_PHASE_COPY, e0, a.packed, 0.0, (4.0 + 2.0 * planes) * rows * K});
+      h->prof_pending.push_back({GB_PHASE_UPDATE, a.packed, e2, update_flops(M, N, K, lower != 0),
+                                 8.0 * cells + 2.0 * planes * (double)(M + N) * K, false});
+    }
     if (e == cudaErrorNotSupported) return GB_ERR_UNSUPPORTED;
     GB_CUDA_TRY(e);
   }

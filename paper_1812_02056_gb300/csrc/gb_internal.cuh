@@ -87,6 +87,7 @@ struct gb_handle {
     int phase;
     cudaEvent_t start, stop;
     double flops, bytes;
+    bool owns_start = true;  // false: start is an earlier record's stop
   };
   std::vector<ProfRec> prof_pending;
   std::vector<cudaEvent_t> prof_pool;
@@ -193,6 +194,8 @@ struct TcUpdateArgs {
   // in elements; then X, Y and pack are not used and K must be a multiple of 64
   const void *xpack, *ypack;
   int64_t ldxp, ldyp;
+  cudaEvent_t packed; // optional: recorded on the stream between the packing
+                      // launches and the tensor-core kernel (profiling)
 };
 // Round an FP32 rows x K block to 16-bit rows of ldo elements (K rounded up
 // to 64 with zeros) -- the resident operand layout of the update.

@@ -201,11 +201,12 @@ __global__ void __launch_bounds__(inv_block<Tc>())
 // dependence order from a ticket (position t: block t forward, block
 // nb - 1 - t backward).  `progress` counts the finished positions; blocks
 // finish in order, so progress = p means positions 0 .. p - 1 are solved.  A
-// CTA applies every solved block's contribution in chunks of up to KC
-// columns -- as many blocks as are finished when it looks, so most of its
-// row panel is applied with one wait, not one wait per block -- and the
-// op(F) part of the next chunk is loaded before the wait (it does not depend
-// on X), as is the CTA's Dinv block.  Then X_b = Dinv[b] (B_b -
+// CTA walks its row panel in chunks of up to KC columns: the op(F) part of a
+// chunk is loaded once, before any wait (it does not depend on X), as is the
+// CTA's Dinv block; then each wait applies as many of the chunk's blocks as
+// are finished when it looks (all of them far behind the wavefront, one per
+// wait when caught up), so a CTA that trails the wavefront re-reads neither
+// op(F) nor X.  Then X_b = Dinv[b] (B_b -
 // contributions), stored, and published.  Every wait is bounded by a
 // %globaltimer deadline; on expiry the kernel raises DEV_ERR_TIMEOUT in the
 // error word, every other waiter sees it and returns, and the host reports
@@ -269,7 +270,8 @@ __global__ void __launch_bounds__(TRSM_THREADS)
       acc[q] = (tr < rows && tc + q < cols) ? (Tc)B[(r0 + tr) * ldb + rc0 + tc + q] : Tc(0);
     int done = 0;
     while (done < t) {
-      // op(F) for the next chunk, before waiting for its X
+      // op(F) for the next chunk of positions, loaded once, before waiting
+      // for any of its X
       const int wmax = min(KC / BS, t - done);
       int64_t f0, f1;
       col_range(done, wmax, f0, f1);
@@ -278,56 +280,60 @@ __global__ void __launch_bounds__(TRSM_THREADS)
         const int i = idx / KC, k = idx % KC;
         Fs[i * (KC + 1) + k] = (i < rows && k < fw) ? (Tc)op_elem(F, ldf, kind, r0 + i, f0 + k) : Tc(0);
       }
-      if (tid == 0) {
-        int spins = 0, avail = ld_acquire(progress);
-        const long long t0 = (long long)globaltimer_ns();
-        while (avail <= done) {
-          if ((++spins & 255) == 0) {
-            if (ld_acquire(err) & DEV_ERR_TIMEOUT) {
-              s_abort = 1;
-              break;
+      int applied = 0;  // positions of this chunk applied so far
+      while (applied < wmax) {
+        const int p0 = done + applied;
+        if (tid == 0) {
+          int spins = 0, avail = ld_acquire(progress);
+          const long long t0 = (long long)globaltimer_ns();
+          while (avail <= p0) {
+            if ((++spins & 255) == 0) {
+              if (ld_acquire(err) & DEV_ERR_TIMEOUT) {
+                s_abort = 1;
+                break;
+              }
+              if ((long long)globaltimer_ns() - t0 > wait_ns) {
+                atomicOr(err, DEV_ERR_TIMEOUT);
+                s_abort = 1;
+                break;
+              }
             }
-            if ((long long)globaltimer_ns() - t0 > wait_ns) {
-              atomicOr(err, DEV_ERR_TIMEOUT);
-              s_abort = 1;
-              break;
-            }
+            avail = ld_acquire(progress);
           }
-          avail = ld_acquire(progress);
+          s_avail = avail;
         }
-        s_avail = avail;
-      }
-      __syncthreads();
-      if (s_abort) return;
-      // the finished positions of this chunk; in the backward sweep the chunk
-      // was laid out for wmax positions, so an unfinished prefix is skipped
-      const int w = min(wmax, s_avail - done);
-      int64_t c0, c1;
-      col_range(done, w, c0, c1);
-      const int kw = (int)(c1 - c0);
-      for (int idx = tid; idx < KC * NRC; idx += TRSM_THREADS) {
-        const int k = idx / NRC, c = idx % NRC;
-        Xs[k * (NRC + 1) + c] = (k < kw && c < cols) ? (Tc)__ldcg(&B[(c0 + k) * ldb + rc0 + c]) : Tc(0);
-      }
-      __syncthreads();
-      // blocks in position order (backward: descending), columns ascending
-      // inside a block: the same order for any chunking, so results do not
-      // depend on how far the other blocks had got
-      for (int pb = 0; pb < w; ++pb) {
-        const int64_t b0 = fwd ? (int64_t)(done + pb) : (int64_t)(nb - 1 - done - pb);
-        const int64_t bc0 = b0 * BS;
-        const int bw = (int)min64(BS, n - bc0);
-        const Tc *Fr = Fs + tr * (KC + 1) + (bc0 - f0);
-        const Tc *Xb = Xs + (bc0 - c0) * (NRC + 1) + tc;
-        for (int k = 0; k < bw; ++k) {
-          const Tc f = Fr[k];
-          const Tc *xk = Xb + k * (NRC + 1);
+        __syncthreads();
+        if (s_abort) return;
+        // the finished positions p0 .. p0 + w - 1 of this chunk
+        const int w = min(wmax - applied, s_avail - p0);
+        int64_t c0, c1;
+        col_range(p0, w, c0, c1);
+        const int kw = (int)(c1 - c0);
+        for (int idx = tid; idx < KC * NRC; idx += TRSM_THREADS) {
+          const int k = idx / NRC, c = idx % NRC;
+          Xs[k * (NRC + 1) + c] = (k < kw && c < cols) ? (Tc)__ldcg(&B[(c0 + k) * ldb + rc0 + c]) : Tc(0);
+        }
+        __syncthreads();
+        // blocks in position order (backward: descending), columns ascending
+        // inside a block: the same order for any chunking, so results do not
+        // depend on how far the other blocks had got
+        for (int pb = 0; pb < w; ++pb) {
+          const int64_t b0 = fwd ? (int64_t)(p0 + pb) : (int64_t)(nb - 1 - p0 - pb);
+          const int64_t bc0 = b0 * BS;
+          const int bw = (int)min64(BS, n - bc0);
+          const Tc *Fr = Fs + tr * (KC + 1) + (bc0 - f0);
+          const Tc *Xb = Xs + (bc0 - c0) * (NRC + 1) + tc;
+          for (int k = 0; k < bw; ++k) {
+            const Tc f = Fr[k];
+            const Tc *xk = Xb + k * (NRC + 1);
 #pragma unroll
-          for (int q = 0; q < OPT; ++q) acc[q] = acc[q] - f * xk[q];
+            for (int q = 0; q < OPT; ++q) acc[q] = acc[q] - f * xk[q];
+          }
         }
+        __syncthreads();
+        applied += w;
       }
-      __syncthreads();
-      done += w;
+      done += wmax;
     }
     // X_b = Dinv[b] * acc
 #pragma unroll

@@ -622,18 +622,51 @@ __device__ __forceinline__ void split_planes(float x, T16 (&p)[3]) {
 }
 
 // out[i * ldo + t * Kp + k] = plane_t(X[i * ldx + k]) for k < K, 0 for K <= k < Kp.
+// Each thread converts 8 consecutive k of one row (Kp is a multiple of 64):
+// two 16-byte loads and one 16-byte store per plane when `vec_in` (X 16-byte
+// aligned, ldx % 4 == 0) and `vec_out` (out 16-byte aligned, ldo % 8 == 0).
 template <typename T16>
 __global__ void pack_rows_kernel(const float *__restrict__ X, int64_t ldx, int64_t rows,
                                  int64_t K, int64_t Kp, int terms, uint32_t code,
-                                 T16 *__restrict__ out, int64_t ldo) {
-  const int64_t total = rows * Kp;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e / Kp, k = e % Kp;
-    T16 p[3];
-    split_planes<T16>(k < K ? X[i * ldx + k] : 0.0f, p);
-    T16 *o = out + i * ldo + k;
-    for (int t = 0; t < terms; ++t) o[t * Kp] = p[(code >> (2 * t)) & 3u];
+                                 T16 *__restrict__ out, int64_t ldo, int vec_in, int vec_out) {
+  const int64_t groups = Kp >> 3;
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= groups) return;
+  const int64_t k0 = g << 3;
+  for (int64_t i = (int64_t)blockIdx.y * blockDim.y + threadIdx.y; i < rows;
+       i += (int64_t)gridDim.y * blockDim.y) {
+    const float *src = X + i * ldx + k0;
+    float x[8];
+    if (vec_in && k0 + 8 <= K) {
+      const float4 a = __ldg(reinterpret_cast<const float4 *>(src));
+      const float4 b = __ldg(reinterpret_cast<const float4 *>(src + 4));
+      x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+      x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+    } else {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) x[u] = k0 + u < K ? src[u] : 0.0f;
+    }
+    T16 p[3][8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      T16 q[3];
+      split_planes<T16>(x[u], q);
+      p[0][u] = q[0];
+      p[1][u] = q[1];
+      p[2][u] = q[2];
+    }
+    T16 *o = out + i * ldo + k0;
+    for (int t = 0; t < terms; ++t) {
+      const T16 *v = p[(code >> (2 * t)) & 3u];
+      if (vec_out) {
+        uint4 w;
+        memcpy(&w, v, 16);
+        *reinterpret_cast<uint4 *>(o + t * Kp) = w;
+      } else {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) o[t * Kp + u] = v[u];
+      }
+    }
   }
 }
 
@@ -727,31 +760,37 @@ constexpr int X3_PLANES[6] = {2, 1, 0, 1, 0, 0};
 constexpr int Y3_PLANES[6] = {0, 1, 2, 0, 1, 0};
 
 template <typename T16>
+void launch_pack_rows(const float *X, int64_t ldx, int64_t rows, int64_t K, int64_t Kp, int terms,
+                      uint32_t code, T16 *out, int64_t ldo, cudaStream_t st) {
+  // a block is gx groups of 8 columns by gy rows, about 128 threads
+  const int64_t groups = Kp / 8;
+  const int gx = (int)std::min<int64_t>(groups, 128), gy = std::max(1, 128 / gx);
+  const dim3 grid((unsigned)((groups + gx - 1) / gx),
+                  (unsigned)std::min<int64_t>((rows + gy - 1) / gy, 65535));
+  const dim3 block((unsigned)gx, (unsigned)gy);
+  const int vec_in = ((reinterpret_cast<uintptr_t>(X) & 15) == 0 && (ldx & 3) == 0) ? 1 : 0;
+  const int vec_out = ((reinterpret_cast<uintptr_t>(out) & 15) == 0 && (ldo & 7) == 0) ? 1 : 0;
+  pack_rows_kernel<T16><<<grid, block, 0, st>>>(X, ldx, rows, K, Kp, terms, code, out, ldo,
+                                                vec_in, vec_out);
+  count_launch();
+}
+
+template <typename T16>
 cudaError_t pack_operands(const TcUpdateArgs &a, int64_t Kp, int terms, T16 *xp, T16 *yp, bool same,
                           cudaStream_t st) {
   const int one[1] = {0};
   const uint32_t cx = terms == 1 ? code_of(one, 1) : code_of(X3_PLANES, 6);
   const uint32_t cy = terms == 1 ? code_of(one, 1) : code_of(Y3_PLANES, 6);
-  const int threads = 256;
-  {
-    const int64_t total = a.M * Kp;
-    const unsigned grid = (unsigned)std::min<int64_t>((total + threads - 1) / threads, 65535 * 4);
-    pack_rows_kernel<T16><<<grid, threads, 0, st>>>(a.X, a.ldx, a.M, a.K, Kp, terms, cx, xp,
-                                                    Kp * terms);
-    count_launch();
-  }
+  launch_pack_rows<T16>(a.X, a.ldx, a.M, a.K, Kp, terms, cx, xp, Kp * terms, st);
   if (!same) {
     if (a.nn) {
       dim3 grid((unsigned)((a.N + 31) / 32), (unsigned)((Kp + 31) / 32));
       pack_transpose_kernel<T16><<<grid, dim3(32, 8), 0, st>>>(a.Y, a.ldy, a.K, a.N, Kp, terms,
                                                                 cy, yp);
+      count_launch();
     } else {
-      const int64_t total = a.N * Kp;
-      const unsigned grid = (unsigned)std::min<int64_t>((total + threads - 1) / threads, 65535 * 4);
-      pack_rows_kernel<T16><<<grid, threads, 0, st>>>(a.Y, a.ldy, a.N, a.K, Kp, terms, cy, yp,
-                                                      Kp * terms);
+      launch_pack_rows<T16>(a.Y, a.ldy, a.N, a.K, Kp, terms, cy, yp, Kp * terms, st);
     }
-    count_launch();
   }
   return cudaGetLastError();
 }
@@ -833,16 +872,11 @@ cudaError_t launch_pack16(const float *X, int64_t ldx, int64_t rows, int64_t K, 
   const uint32_t code = code_of(one, 1);
   const int64_t Kp = round_up(K, BK);
   if (ldo < Kp) return cudaErrorInvalidValue;
-  const int threads = 256;
-  const int64_t total = rows * Kp;
-  const unsigned grid = (unsigned)std::min<int64_t>((total + threads - 1) / threads, 65535 * 4);
   if (f16)
-    pack_rows_kernel<__half><<<grid, threads, 0, st>>>(X, ldx, rows, K, Kp, 1, code,
-                                                       reinterpret_cast<__half *>(out), ldo);
+    launch_pack_rows<__half>(X, ldx, rows, K, Kp, 1, code, reinterpret_cast<__half *>(out), ldo, st);
   else
-    pack_rows_kernel<__nv_bfloat16><<<grid, threads, 0, st>>>(
-        X, ldx, rows, K, Kp, 1, code, reinterpret_cast<__nv_bfloat16 *>(out), ldo);
-  count_launch();
+    launch_pack_rows<__nv_bfloat16>(X, ldx, rows, K, Kp, 1, code,
+                                    reinterpret_cast<__nv_bfloat16 *>(out), ldo, st);
   return cudaGetLastError();
 }
 
@@ -914,6 +948,7 @@ cudaError_t launch_update_tc(const TcUpdateArgs &a, cudaStream_t st) {
     const int64_t last = bg * CL * BM + CL * BM - 1 + a.diag;
     if (last >= 0) valid += std::min<int64_t>(nbj, last / BN + 1);
   }
+  if (a.packed) cudaEventRecord(a.packed, st);
   if (valid == 0) return cudaSuccess;
   if (!make_operand_map(&map_a, xp, a.M, Ke, BM, a.f16, xstride) ||
       !make_operand_map(&map_b, yp, a.N, Ke, BN / CL, a.f16, ystride))

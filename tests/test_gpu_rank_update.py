@@ -57,7 +57,7 @@ def _expected(C, X, Y, kxn, dt):
 @pytest.mark.parametrize("dt", ["mix_bf16", "mix_f16", "mix_bf16x3", "f32", "f64"])
 @pytest.mark.parametrize("M,N,K,lower,kxn", [
     (300, 300, 117, 1, 0), (129, 129, 16, 1, 0), (520, 520, 1024, 1, 0), (1, 1, 1, 1, 0),
-    (200, 520, 64, 0, 1), (384, 256, 200, 0, 1), (77, 333, 1000, 0, 0)])
+    (200, 520, 64, 0, 1), (384, 256, 200, 0, 1), (77, 333, 1000, 0, 0), (260, 260, 100, 1, 0)])
 def test_rank_update_exact_integers(h, dt, M, N, K, lower, kxn):
     g = torch.Generator().manual_seed(M * 7 + N * 3 + K)
     tt = torch.float64 if dt == "f64" else torch.float32
