@@ -72,10 +72,14 @@ const char *gb_status_string(gb_status st);
  * Arithmetic of a factorization.
  *  GB_F64      A and L/U are double; every step in FP64.
  *  GB_F32      A and L/U are float;  every step in FP32.
- *  GB_MIX_BF16 A is double, L/U are float.  The working matrix is FP32; the
- *              diagonal-block column steps (square root, pivots) run in
- *              FP64; the panel rows in FP32; the delayed rank-s update runs
- *              on the tensor cores with BF16 operands and FP32 accumulation.
+ *  GB_MIX_BF16 A is double, L/U are float.  The working matrix is FP32;
+ *              Cholesky's pivots (square root and its reciprocal) are the
+ *              FP64 operations rounded to FP32, computed as the identical
+ *              correctly rounded FP32 operations (double rounding is
+ *              innocuous for sqrt and division from 53 to 24 bits); LU's
+ *              diagonal blocks run in FP64; the panel rows in FP32; the
+ *              delayed rank-s update runs on the tensor cores with BF16
+ *              operands and FP32 accumulation.
  *  GB_MIX_F16  as GB_MIX_BF16 with FP16 operands.
  *  GB_MIX_BF16X3  as GB_MIX_BF16, but each operand of the update is split
  *              into three BF16 planes (x = p0 + p1 + p2, each the rounding of

@@ -361,12 +361,7 @@ gb_status chol_blocked_on(gb_handle *h, int64_t n, int64_t s, T *W, int64_t ld, 
         PhaseTimer t(h, st, GB_PHASE_PANEL,
                      (double)bw * bw * bw / 3.0 + (double)(n - r0) * bw * bw,
                      (double)bw * bw * e + 2.0 * (double)(n - r0) * bw * e);
-        if constexpr (sizeof(Tc) > sizeof(T))  // mixed: FP64 square roots and pivots
-          GB_CUDA_TRY((launch_chol_panel<T, true>(W, ld, j0, bw, n - r0, status, h->d_arrivals,
-                                                  st)));
-        else
-          GB_CUDA_TRY((launch_chol_panel<T, false>(W, ld, j0, bw, n - r0, status, h->d_arrivals,
-                                                   st)));
+        GB_CUDA_TRY(launch_chol_panel<T>(W, ld, j0, bw, n - r0, status, h->d_arrivals, st));
       }
       if (r0 < pe) {  // the s-block's remaining columns receive this inner block
         PhaseTimer t(h, st, GB_PHASE_INNER, update_flops(n - r0, pe - r0, bw, true),
@@ -467,7 +462,7 @@ gb_status chol_left_on(gb_handle *h, int64_t n, int64_t s, T *W, int64_t ld, int
         PhaseTimer t(h, st, GB_PHASE_PANEL,
                      (double)bw * bw * bw / 3.0 + (double)(n - r0) * bw * bw,
                      (double)bw * bw * 4 + 2.0 * (double)(n - r0) * bw * 4);
-        GB_CUDA_TRY((launch_chol_panel<T, true>(W, ld, j0, bw, n - r0, status, h->d_arrivals, st)));
+        GB_CUDA_TRY(launch_chol_panel<T>(W, ld, j0, bw, n - r0, status, h->d_arrivals, st));
       }
       if (r0 < pe) {
         PhaseTimer t(h, st, GB_PHASE_INNER, update_flops(n - r0, pe - r0, bw, true),

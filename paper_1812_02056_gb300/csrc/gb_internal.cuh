@@ -131,7 +131,7 @@ cudaError_t launch_chol_rows(T *W, int64_t ld, int64_t row0, int64_t nrows, int6
                              int *status, cudaStream_t st);
 // Fused column steps of one inner block (diagonal block in every CTA, then
 // its rows); `arrivals` is a zeroed counter the kernel leaves zeroed.
-template <typename T, bool FP64_PIVOT>
+template <typename T>
 cudaError_t launch_chol_panel(T *W, int64_t ld, int64_t j0, int bw, int64_t nrows, int *status,
                               unsigned long long *arrivals, cudaStream_t st);
 template <typename T, typename Tc>

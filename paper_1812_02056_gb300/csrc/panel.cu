@@ -27,6 +27,21 @@ __device__ __forceinline__ int load_status(const int *status) {
   return *reinterpret_cast<const volatile int *>(status);
 }
 
+// Global -> shared copy of one element (4 or 8 bytes) that completes
+// asynchronously (zero-filled when `valid` is false); waited for with
+// cp_async_wait_all by the same thread.
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T *dst, const T *src, bool valid) {
+  static_assert(sizeof(T) == 4 || sizeof(T) == 8, "element size");
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(d), "l"(src),
+               "n"((int)sizeof(T)), "r"(valid ? (int)sizeof(T) : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
 constexpr int DIAG_THREADS = 256;  // 16 x 16 threads, 4 x 4 elements each
 
 // ---------------------------------------------------------------- Cholesky
@@ -135,6 +150,13 @@ __global__ void __launch_bounds__(ROWS_PER_CTA)
 // subtracted by short runtime loops (small loop bodies, reused across
 // iterations), then the chunk's own columns are finished one at a time.
 // Every entry still receives its products in ascending k, one at a time.
+// One barrier per column: at the start of a chunk each diagonal entry's
+// running value is published, and every thread keeps its own copy of the
+// chunk's diagonal, updated with the same products (L_jc * L_jc, in the same
+// order) as the row that owns it, so that each thread forms the pivot
+// itself; a breakdown is seen by every thread at once.
+// The rows below the block are fetched into shared memory with asynchronous
+// copies issued before the diagonal block is factored.
 // The factored block is written back by the last CTA to have loaded it:
 // each CTA bumps an arrival counter after loading; the CTA that arrives as
 // number grid - 1 knows every other CTA already holds its own copy, writes
@@ -143,23 +165,17 @@ __global__ void __launch_bounds__(ROWS_PER_CTA)
 // Inside the diagonal block the column below L_cc is scaled by 1 / L_cc
 // (one reciprocal per column, as LAPACK's unblocked Cholesky does); the rows
 // below the block divide by L_cc as the paper writes.
-// FP64_PIVOT: square root and reciprocal in FP64 on FP32 data (the mixed
-// dtypes).  MODE: PANEL_FUSED, PANEL_DIAG (one CTA: factor and write the
+// The pivot's square root and reciprocal are IEEE round-to-nearest
+// operations in T.  For FP32 data they give the same bits as the FP64
+// operations rounded to FP32: double rounding is innocuous for the square
+// root and for division when the wider format carries at least 2p + 2
+// significand bits (53 >= 2 * 24 + 2; S. A. Figueroa, "When is double
+// rounding innocuous?", 1995), so the mixed dtypes' FP64 pivots cost no FP64
+// instruction.  MODE: PANEL_FUSED, PANEL_DIAG (one CTA: factor and write the
 // block), PANEL_ROWS_ONLY (read the finished block, then the rows).
 enum { PANEL_FUSED = 0, PANEL_DIAG = 1, PANEL_ROWS_ONLY = 2 };
 constexpr int PB = 64;   // inner block width bound
 constexpr int CH = 16;   // chunk width
-
-template <typename T, bool FP64_PIVOT>
-__device__ __forceinline__ T pivot_sqrt(T d) {
-  if (FP64_PIVOT) return (T)sqrt((double)d);
-  return sqrt(d);
-}
-template <typename T, bool FP64_PIVOT>
-__device__ __forceinline__ T pivot_div(T a, T b) {
-  if (FP64_PIVOT) return (T)((double)a / (double)b);
-  return a / b;
-}
 
 template <typename T>
 struct PanelSmem {
@@ -169,7 +185,7 @@ struct PanelSmem {
   }
 };
 
-template <typename T, bool FP64_PIVOT, int MODE, int ROWS>
+template <typename T, int MODE, int ROWS>
 __global__ void __launch_bounds__(ROWS)
     chol_panel_kernel(T *__restrict__ W, int64_t ld, int64_t j0, int bw, int64_t row0,
                       int64_t nrows, int *status, unsigned long long *arrivals) {
@@ -178,11 +194,21 @@ __global__ void __launch_bounds__(ROWS)
   T(*Ld)[PB + 1] = reinterpret_cast<T(*)[PB + 1]>(smem_raw);  // Ld[i][k] = L_ik, k <= i
   T(*LdT)[PADT] = reinterpret_cast<T(*)[PADT]>(smem_raw + sizeof(T) * PB * (PB + 1));  // LdT[k][i] = L_ik
   T(*Ys)[ROWS] = reinterpret_cast<T(*)[ROWS]>(smem_raw + sizeof(T) * (PB * (PB + 1) + PB * PADT));
-  __shared__ T s_piv;
-  __shared__ int s_ok, s_last;
+  __shared__ T s_diag[CH];
+  __shared__ int s_last;
   if (load_status(status) != 0) return;
   const int tid = threadIdx.x;
   T *D = W + j0 * ld + j0;
+
+  // this thread's row below the block, copied into its column of Ys while
+  // the diagonal block is factored
+  const int64_t r = row0 + (int64_t)blockIdx.x * ROWS + tid;
+  const bool has_row = MODE != PANEL_DIAG && r < row0 + nrows;
+  T *row = has_row ? W + r * ld + j0 : D;  // D: a valid address for the zero-filled copies
+  if (MODE != PANEL_DIAG) {
+#pragma unroll 16
+    for (int u = 0; u < PB; ++u) cp_async_elem<T>(&Ys[u][tid], row + (u < bw ? u : 0), has_row && u < bw);
+  }
 
   // all loads of the block in flight at once: registers first, then shared memory
   constexpr int PER = PB * PB / ROWS;
@@ -230,25 +256,32 @@ __global__ void __launch_bounds__(ROWS)
           for (int j = 0; j < CH; ++j) v[j] = v[j] - lik * LdT[k][c0 + j];
         }
       }
+      // every thread's copy of the chunk's diagonal: A_cc minus the products
+      // of the columns before the chunk
+#pragma unroll
+      for (int j = 0; j < CH; ++j)
+        if (tid == c0 + j && j < cw) s_diag[j] = v[j];
+      __syncthreads();
+      T dd[CH];
+#pragma unroll
+      for (int j = 0; j < CH; ++j) dd[j] = s_diag[j];
 #pragma unroll
       for (int cc = 0; cc < CH; ++cc) {  // the chunk's columns, one at a time
         if (cc < cw) {
           const int c = c0 + cc;
-          if (tid == c) {
-            const T d = v[cc];
-            s_ok = (d > T(0)) ? 1 : 0;  // not positive, or NaN: breakdown
-            const T piv = pivot_sqrt<T, FP64_PIVOT>(d);
-            s_piv = pivot_div<T, FP64_PIVOT>(T(1), piv);  // the column is scaled by 1 / L_cc
-            v[cc] = piv;
-            LdT[c][c] = piv;
-          }
-          __syncthreads();
-          if (!s_ok) {  // uniform
+          const T d = dd[cc];
+          if (!(d > T(0))) {  // not positive, or NaN: breakdown, seen by every thread
             if (blockIdx.x == 0 && tid == 0) atomicCAS(status, 0, (int)(j0 + c + 1));
+            if (MODE != PANEL_DIAG) cp_async_wait_all();
             return;
           }
-          if (tid > c && tid < bw) {
-            v[cc] = v[cc] * s_piv;
+          const T piv = sqrt(d);
+          const T rpiv = T(1) / piv;  // the column is scaled by 1 / L_cc
+          if (tid == c) {
+            v[cc] = piv;
+            LdT[c][c] = piv;
+          } else if (tid > c && tid < bw) {
+            v[cc] = v[cc] * rpiv;
             LdT[c][tid] = v[cc];
           }
           __syncthreads();
@@ -257,6 +290,11 @@ __global__ void __launch_bounds__(ROWS)
 #pragma unroll
             for (int cc2 = cc + 1; cc2 < CH; ++cc2)
               if (c0 + cc2 <= tid) v[cc2] = v[cc2] - lic * LdT[c][c0 + cc2];
+          }
+#pragma unroll
+          for (int cc2 = cc + 1; cc2 < CH; ++cc2) {  // the same products as row c0 + cc2's own
+            const T l = LdT[c][c0 + cc2];
+            dd[cc2] = dd[cc2] - l * l;
           }
         }
       }
@@ -273,47 +311,38 @@ __global__ void __launch_bounds__(ROWS)
         if (i < bw && k <= i) D[(int64_t)i * ld + k] = Ld[i][k];
       }
     }
-    if (MODE == PANEL_DIAG) return;
   }
 
-  // ---- rows below the block: thread t owns row row0 + blockIdx.x * ROWS + t
-  const int64_t r = row0 + (int64_t)blockIdx.x * ROWS + tid;
-  if (r >= row0 + nrows) return;
-  T *row = W + r * ld + j0;
-  // the row's entries, all loads in flight at once, parked in its column of Ys
+  if constexpr (MODE != PANEL_DIAG) {
+    // ---- rows below the block: thread t owns row row0 + blockIdx.x * ROWS + t
+    cp_async_wait_all();  // this thread's own copies into its column of Ys
+    if (!has_row) return;
+    for (int c0 = 0; c0 < bw; c0 += CH) {
+      const int cw = min(CH, bw - c0);
+      T y[CH];
 #pragma unroll
-  for (int u = 0; u < PB; u += 16) {
-    T tmp[16];
+      for (int j = 0; j < CH; ++j) y[j] = Ys[c0 + j][tid];
+      for (int k = 0; k < c0; ++k) {  // products of the finished columns
+        const T yk = Ys[k][tid];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) tmp[q] = (u + q < bw) ? row[u + q] : T(0);
-#pragma unroll
-    for (int q = 0; q < 16; ++q) Ys[u + q][tid] = tmp[q];
-  }
-  for (int c0 = 0; c0 < bw; c0 += CH) {
-    const int cw = min(CH, bw - c0);
-    T y[CH];
-#pragma unroll
-    for (int j = 0; j < CH; ++j) y[j] = Ys[c0 + j][tid];
-    for (int k = 0; k < c0; ++k) {  // products of the finished columns
-      const T yk = Ys[k][tid];
-#pragma unroll
-      for (int j = 0; j < CH; ++j) y[j] = y[j] - yk * LdT[k][c0 + j];
-    }
-#pragma unroll
-    for (int j = 0; j < CH; ++j) {  // the chunk's columns, one at a time
-      if (j < cw) {
-        const T yj = y[j] / LdT[c0 + j][c0 + j];
-        y[j] = yj;
-#pragma unroll
-        for (int j2 = j + 1; j2 < CH; ++j2) y[j2] = y[j2] - yj * LdT[c0 + j][c0 + j2];
+        for (int j = 0; j < CH; ++j) y[j] = y[j] - yk * LdT[k][c0 + j];
       }
-    }
 #pragma unroll
-    for (int j = 0; j < CH; ++j)
-      if (j < cw) {
-        Ys[c0 + j][tid] = y[j];
-        row[c0 + j] = y[j];
+      for (int j = 0; j < CH; ++j) {  // the chunk's columns, one at a time
+        if (j < cw) {
+          const T yj = y[j] / LdT[c0 + j][c0 + j];
+          y[j] = yj;
+#pragma unroll
+          for (int j2 = j + 1; j2 < CH; ++j2) y[j2] = y[j2] - yj * LdT[c0 + j][c0 + j2];
+        }
       }
+#pragma unroll
+      for (int j = 0; j < CH; ++j)
+        if (j < cw) {
+          Ys[c0 + j][tid] = y[j];
+          row[c0 + j] = y[j];
+        }
+    }
   }
 }
 
@@ -503,33 +532,32 @@ cudaError_t launch_chol_rows(T *W, int64_t ld, int64_t row0, int64_t nrows, int6
   return chol_rows_b<T, 64>(W, ld, row0, nrows, j0, bw, status, st);
 }
 
-template <typename T, bool FP64_PIVOT, int MODE, int ROWS>
+template <typename T, int MODE, int ROWS>
 cudaError_t panel_launch(unsigned grid, T *W, int64_t ld, int64_t j0, int bw, int64_t nrows,
                          int *status, unsigned long long *arrivals, cudaStream_t st) {
   constexpr size_t smem = PanelSmem<T>::bytes(ROWS);
-  static cudaError_t attr = allow_smem(chol_panel_kernel<T, FP64_PIVOT, MODE, ROWS>, smem);
+  static cudaError_t attr = allow_smem(chol_panel_kernel<T, MODE, ROWS>, smem);
   if (attr != cudaSuccess) return attr;
-  chol_panel_kernel<T, FP64_PIVOT, MODE, ROWS><<<grid, ROWS, smem, st>>>(W, ld, j0, bw, j0 + bw,
-                                                                       nrows, status, arrivals);
+  chol_panel_kernel<T, MODE, ROWS><<<grid, ROWS, smem, st>>>(W, ld, j0, bw, j0 + bw, nrows,
+                                                           status, arrivals);
   count_launch();
   return cudaGetLastError();
 }
 
-template <typename T, bool FP64_PIVOT>
+template <typename T>
 cudaError_t launch_chol_panel(T *W, int64_t ld, int64_t j0, int bw, int64_t nrows, int *status,
                               unsigned long long *arrivals, cudaStream_t st) {
   if (bw < 1 || bw > PB) return cudaErrorInvalidValue;
   if (sizeof(T) == 8) {
     // FP64: the block's DFMA work once (one CTA), then the rows over every SM
-    cudaError_t e = panel_launch<T, FP64_PIVOT, PANEL_DIAG, 64>(1, W, ld, j0, bw, 0, status,
-                                                                 arrivals, st);
+    cudaError_t e = panel_launch<T, PANEL_DIAG, 64>(1, W, ld, j0, bw, 0, status, arrivals, st);
     if (e != cudaSuccess || nrows <= 0) return e;
-    return panel_launch<T, FP64_PIVOT, PANEL_ROWS_ONLY, 64>((unsigned)((nrows + 63) / 64), W, ld,
-                                                             j0, bw, nrows, status, arrivals, st);
+    return panel_launch<T, PANEL_ROWS_ONLY, 64>((unsigned)((nrows + 63) / 64), W, ld, j0, bw,
+                                                 nrows, status, arrivals, st);
   }
   const int64_t grid = std::max<int64_t>(1, (nrows + 127) / 128);
-  return panel_launch<T, FP64_PIVOT, PANEL_FUSED, 128>((unsigned)grid, W, ld, j0, bw, nrows,
-                                                        status, arrivals, st);
+  return panel_launch<T, PANEL_FUSED, 128>((unsigned)grid, W, ld, j0, bw, nrows, status, arrivals,
+                                            st);
 }
 
 template <typename T, typename Tc>
@@ -578,9 +606,8 @@ template cudaError_t launch_chol_diag<float, float>(float *, int64_t, int64_t, i
 template cudaError_t launch_chol_diag<float, double>(float *, int64_t, int64_t, int, int *, cudaStream_t);
 template cudaError_t launch_chol_rows<double>(double *, int64_t, int64_t, int64_t, int64_t, int, int *, cudaStream_t);
 template cudaError_t launch_chol_rows<float>(float *, int64_t, int64_t, int64_t, int64_t, int, int *, cudaStream_t);
-template cudaError_t launch_chol_panel<double, false>(double *, int64_t, int64_t, int, int64_t, int *, unsigned long long *, cudaStream_t);
-template cudaError_t launch_chol_panel<float, false>(float *, int64_t, int64_t, int, int64_t, int *, unsigned long long *, cudaStream_t);
-template cudaError_t launch_chol_panel<float, true>(float *, int64_t, int64_t, int, int64_t, int *, unsigned long long *, cudaStream_t);
+template cudaError_t launch_chol_panel<double>(double *, int64_t, int64_t, int, int64_t, int *, unsigned long long *, cudaStream_t);
+template cudaError_t launch_chol_panel<float>(float *, int64_t, int64_t, int, int64_t, int *, unsigned long long *, cudaStream_t);
 template cudaError_t launch_lu_diag<double, double>(double *, int64_t, int64_t, int, int *, cudaStream_t);
 template cudaError_t launch_lu_diag<float, float>(float *, int64_t, int64_t, int, int *, cudaStream_t);
 template cudaError_t launch_lu_diag<float, double>(float *, int64_t, int64_t, int, int *, cudaStream_t);
