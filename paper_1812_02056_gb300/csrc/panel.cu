@@ -177,6 +177,26 @@ enum { PANEL_FUSED = 0, PANEL_DIAG = 1, PANEL_ROWS_ONLY = 2 };
 constexpr int PB = 64;   // inner block width bound
 constexpr int CH = 16;   // chunk width
 
+// 16 consecutive elements of a 16-byte aligned shared-memory row.
+__device__ __forceinline__ void load_row16(float (&o)[16], const float *p) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const float4 w = reinterpret_cast<const float4 *>(p)[q];
+    o[4 * q] = w.x;
+    o[4 * q + 1] = w.y;
+    o[4 * q + 2] = w.z;
+    o[4 * q + 3] = w.w;
+  }
+}
+__device__ __forceinline__ void load_row16(double (&o)[16], const double *p) {
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const double2 w = reinterpret_cast<const double2 *>(p)[q];
+    o[2 * q] = w.x;
+    o[2 * q + 1] = w.y;
+  }
+}
+
 template <typename T>
 struct PanelSmem {
   static constexpr int PADT = PB + 16 / (int)sizeof(T);  // 16-byte aligned rows
@@ -194,8 +214,7 @@ __global__ void __launch_bounds__(ROWS)
   T(*Ld)[PB + 1] = reinterpret_cast<T(*)[PB + 1]>(smem_raw);  // Ld[i][k] = L_ik, k <= i
   T(*LdT)[PADT] = reinterpret_cast<T(*)[PADT]>(smem_raw + sizeof(T) * PB * (PB + 1));  // LdT[k][i] = L_ik
   T(*Ys)[ROWS] = reinterpret_cast<T(*)[ROWS]>(smem_raw + sizeof(T) * (PB * (PB + 1) + PB * PADT));
-  __shared__ T s_diag[CH];
-  __shared__ int s_last;
+  __shared__ int s_last, s_bad;
   if (load_status(status) != 0) return;
   const int tid = threadIdx.x;
   T *D = W + j0 * ld + j0;
@@ -233,77 +252,91 @@ __global__ void __launch_bounds__(ROWS)
       LdT[k][i] = T(0);
     }
     __syncthreads();
+    if (tid == 0) s_bad = 0;
     if (MODE == PANEL_DIAG) {
       if (tid == 0) s_last = 1;
-    } else if (tid == 0) {
+    } else if (tid == ROWS - 1) {  // the last warp: warp 0 starts the block at once
       __threadfence();
       const unsigned long long a = atomicAdd(arrivals, 1ULL);
       s_last = (a == (unsigned long long)gridDim.x - 1) ? 1 : 0;
       if (s_last) atomicExch(arrivals, 0ULL);  // every CTA has arrived
     }
-    // thread i < bw works on row i of the block; the chunk's 16 columns of
-    // that row stay in registers while the chunk is finished
+    // Per 16-column chunk: every row i in [c0, bw) first receives the
+    // products of the finished columns k < c0 (thread i, its row in
+    // registers); then warp 0 finishes the chunk's columns one at a time,
+    // lane l holding rows c0 + l and c0 + 32 + l, with the pivot and the
+    // column's entries passed between lanes by shuffles (no barrier inside
+    // the chunk).
+    const int lane = tid & 31;
     for (int c0 = 0; c0 < bw; c0 += CH) {
       const int cw = min(CH, bw - c0);
-      const bool mine = tid >= c0 && tid < bw;
-      T v[CH];
+      if (tid >= c0 && tid < bw) {  // products of the finished columns k < c0
+        T v[CH];
 #pragma unroll
-      for (int j = 0; j < CH; ++j) v[j] = (mine && j < cw && c0 + j <= tid) ? Ld[tid][c0 + j] : T(0);
-      if (mine) {  // products of the finished columns k < c0
-        for (int k = 0; k < c0; ++k) {
-          const T lik = Ld[tid][k];
+        for (int j = 0; j < CH; ++j) v[j] = Ld[tid][c0 + j];
+        for (int k0 = 0; k0 < c0; k0 += 4) {  // c0 is a multiple of 16
 #pragma unroll
-          for (int j = 0; j < CH; ++j) v[j] = v[j] - lik * LdT[k][c0 + j];
-        }
-      }
-      // every thread's copy of the chunk's diagonal: A_cc minus the products
-      // of the columns before the chunk
+          for (int u = 0; u < 4; ++u) {
+            const T lik = Ld[tid][k0 + u];
+            T lk[CH];
+            load_row16(lk, &LdT[k0 + u][c0]);
 #pragma unroll
-      for (int j = 0; j < CH; ++j)
-        if (tid == c0 + j && j < cw) s_diag[j] = v[j];
-      __syncthreads();
-      T dd[CH];
-#pragma unroll
-      for (int j = 0; j < CH; ++j) dd[j] = s_diag[j];
-#pragma unroll
-      for (int cc = 0; cc < CH; ++cc) {  // the chunk's columns, one at a time
-        if (cc < cw) {
-          const int c = c0 + cc;
-          const T d = dd[cc];
-          if (!(d > T(0))) {  // not positive, or NaN: breakdown, seen by every thread
-            if (blockIdx.x == 0 && tid == 0) atomicCAS(status, 0, (int)(j0 + c + 1));
-            if (MODE != PANEL_DIAG) cp_async_wait_all();
-            return;
-          }
-          const T piv = sqrt(d);
-          const T rpiv = T(1) / piv;  // the column is scaled by 1 / L_cc
-          if (tid == c) {
-            v[cc] = piv;
-            LdT[c][c] = piv;
-          } else if (tid > c && tid < bw) {
-            v[cc] = v[cc] * rpiv;
-            LdT[c][tid] = v[cc];
-          }
-          __syncthreads();
-          if (tid > c && tid < bw) {
-            const T lic = v[cc];
-#pragma unroll
-            for (int cc2 = cc + 1; cc2 < CH; ++cc2)
-              if (c0 + cc2 <= tid) v[cc2] = v[cc2] - lic * LdT[c][c0 + cc2];
-          }
-#pragma unroll
-          for (int cc2 = cc + 1; cc2 < CH; ++cc2) {  // the same products as row c0 + cc2's own
-            const T l = LdT[c][c0 + cc2];
-            dd[cc2] = dd[cc2] - l * l;
+            for (int j = 0; j < CH; ++j) v[j] = v[j] - lik * lk[j];
           }
         }
-      }
-      if (mine) {
 #pragma unroll
-        for (int j = 0; j < CH; ++j)
-          if (j < cw && c0 + j <= tid) Ld[tid][c0 + j] = v[j];
+        for (int j = 0; j < CH; ++j) Ld[tid][c0 + j] = v[j];
       }
       __syncthreads();
+      if (tid < 32) {
+        const int ra = c0 + lane, rb = c0 + 32 + lane;  // rb > every column of the chunk
+        T va[CH], vb[CH];
+#pragma unroll
+        for (int j = 0; j < CH; ++j) {
+          va[j] = ra < bw ? Ld[ra][c0 + j] : T(0);
+          vb[j] = rb < bw ? Ld[rb][c0 + j] : T(0);
+        }
+        int bad = 0;
+#pragma unroll
+        for (int cc = 0; cc < CH; ++cc) {  // the chunk's columns, one at a time
+          if (cc < cw && !bad) {
+            const T d = __shfl_sync(0xffffffffu, va[cc], cc);  // row c's running diagonal
+            if (!(d > T(0))) {  // not positive, or NaN: breakdown (uniform over the warp)
+              bad = c0 + cc + 1;
+            } else {
+              const T piv = sqrt(d);
+              const T rpiv = T(1) / piv;  // the column is scaled by 1 / L_cc
+              va[cc] = lane == cc ? piv : va[cc] * rpiv;
+              vb[cc] = vb[cc] * rpiv;
+#pragma unroll
+              for (int cc2 = cc + 1; cc2 < CH; ++cc2) {
+                const T l = __shfl_sync(0xffffffffu, va[cc], cc2);  // L_{c0+cc2, c}
+                va[cc2] = va[cc2] - va[cc] * l;
+                vb[cc2] = vb[cc2] - vb[cc] * l;
+              }
+            }
+          }
+        }
+        // the chunk's columns of rows >= c0 (entries on or below the diagonal)
+#pragma unroll
+        for (int j = 0; j < CH; ++j) {
+          if (j < cw && ra < bw && c0 + j <= ra) {
+            Ld[ra][c0 + j] = va[j];
+            LdT[c0 + j][ra] = va[j];
+          }
+          if (j < cw && rb < bw) {
+            Ld[rb][c0 + j] = vb[j];
+            LdT[c0 + j][rb] = vb[j];
+          }
+        }
+        if (lane == 0) s_bad = bad;
+      }
+      __syncthreads();
+      if (s_bad) {  // uniform
+        if (blockIdx.x == 0 && tid == 0) atomicCAS(status, 0, (int)(j0 + s_bad));
+        if (MODE != PANEL_DIAG) cp_async_wait_all();
+        return;
+      }
     }
     if (s_last) {
       for (int idx = tid; idx < PB * PB; idx += ROWS) {
@@ -322,10 +355,15 @@ __global__ void __launch_bounds__(ROWS)
       T y[CH];
 #pragma unroll
       for (int j = 0; j < CH; ++j) y[j] = Ys[c0 + j][tid];
-      for (int k = 0; k < c0; ++k) {  // products of the finished columns
-        const T yk = Ys[k][tid];
+      for (int k0 = 0; k0 < c0; k0 += 4) {  // products of the finished columns
 #pragma unroll
-        for (int j = 0; j < CH; ++j) y[j] = y[j] - yk * LdT[k][c0 + j];
+        for (int u = 0; u < 4; ++u) {
+          const T yk = Ys[k0 + u][tid];
+          T lk[CH];
+          load_row16(lk, &LdT[k0 + u][c0]);
+#pragma unroll
+          for (int j = 0; j < CH; ++j) y[j] = y[j] - yk * lk[j];
+        }
       }
 #pragma unroll
       for (int j = 0; j < CH; ++j) {  // the chunk's columns, one at a time

@@ -309,9 +309,10 @@ __global__ void __launch_bounds__(TRSM_THREADS)
         int64_t c0, c1;
         col_range(p0, w, c0, c1);
         const int kw = (int)(c1 - c0);
-        for (int idx = tid; idx < KC * NRC; idx += TRSM_THREADS) {
+        // only the kw rows the products below read
+        for (int idx = tid; idx < kw * NRC; idx += TRSM_THREADS) {
           const int k = idx / NRC, c = idx % NRC;
-          Xs[k * (NRC + 1) + c] = (k < kw && c < cols) ? (Tc)__ldcg(&B[(c0 + k) * ldb + rc0 + c]) : Tc(0);
+          Xs[k * (NRC + 1) + c] = c < cols ? (Tc)__ldcg(&B[(c0 + k) * ldb + rc0 + c]) : Tc(0);
         }
         __syncthreads();
         // blocks in position order (backward: descending), columns ascending
