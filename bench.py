@@ -564,7 +564,8 @@ def run_batched(args):
         dt = binding.DTYPES[dtype]
         steps = np.zeros(16, dtype=np.int32)
         t0 = time.perf_counter()
-        binding.check(h.gb_batched_tune(dt, 512, steps), "tune")
+        if not args.no_tune:
+            binding.check(h.gb_batched_tune(dt, 512, steps), "tune")
         tune_s = time.perf_counter() - t0
         a_arr = (buf.data_ptr() + offs * esz).astype(np.uint64)
         l_arr = (outb.data_ptr() + offs * esz).astype(np.uint64)
@@ -640,17 +641,18 @@ def run_batched(args):
         del buf, outb, g, g2
         torch.cuda.empty_cache()
     # CPU oracle on a bounded sample of the same workload
-    idx = np.random.default_rng(2).choice(len(sizes), args.batch_cpu_sample, replace=False)
-    mats = [inputs.spd_gram(int(sizes[i]), inputs.seed_for(inputs.W_BATCHED, 2) + int(i))
-            for i in idx]
-    t0 = time.perf_counter()
-    for A in mats:
-        oracle.chol(A, 32)
-    el = time.perf_counter() - t0
-    fs = float(sum(int(sizes[i]) ** 3 for i in idx) / 3.0)
-    out["cpu_baseline"] = {"value": fs / el / 1e9, "unit": "GFLOP/s", "kind": "oracle",
-                           "cores": oracle.num_threads(),
-                           "sample": f"{len(idx)} matrices of the workload, FP64, s=32"}
+    if args.batch_cpu_sample > 0:
+        idx = np.random.default_rng(2).choice(len(sizes), args.batch_cpu_sample, replace=False)
+        mats = [inputs.spd_gram(int(sizes[i]), inputs.seed_for(inputs.W_BATCHED, 2) + int(i))
+                for i in idx]
+        t0 = time.perf_counter()
+        for A in mats:
+            oracle.chol(A, 32)
+        el = time.perf_counter() - t0
+        fs = float(sum(int(sizes[i]) ** 3 for i in idx) / 3.0)
+        out["cpu_baseline"] = {"value": fs / el / 1e9, "unit": "GFLOP/s", "kind": "oracle",
+                               "cores": oracle.num_threads(),
+                               "sample": f"{len(idx)} matrices of the workload, FP64, s=32"}
     print(json.dumps(out))
     h.close()
     return 0
@@ -932,6 +934,8 @@ def main():
     ap.add_argument("--tune", action="store_true",
                     help="mixed mode: pick (s, inner step) with gb_tune_step, then factor with s = 0")
     ap.add_argument("--batch-count", type=int, default=10000)
+    ap.add_argument("--no-tune", action="store_true",
+                    help="batched: keep the library's default step rule (no autotuner launches)")
     ap.add_argument("--batch-cpu-sample", type=int, default=200)
     ap.add_argument("--served-count", type=int, default=400)
     ap.add_argument("--served-nmax", type=int, default=8192)

@@ -100,11 +100,17 @@ __device__ __forceinline__ void tiled_update(int m, int nc, int kn, FX X, FY Y, 
       ii[a] = min(i0 + a, m - 1);
       jj[a] = min(j0 + 16 * a, nc - 1);
     }
-    T acc[TR][TR];
+    // the outputs are read before the products (global memory on the panel
+    // path: the load latency overlaps the k loop); nothing else writes them
+    T acc[TR][TR], cv[TR][TR];
 #pragma unroll
     for (int a = 0; a < TR; ++a)
 #pragma unroll
-      for (int b = 0; b < TR; ++b) acc[a][b] = T(0);
+      for (int b = 0; b < TR; ++b) {
+        acc[a][b] = T(0);
+        const int i = i0 + a, j = j0 + 16 * b;
+        cv[a][b] = (i < m && j < nc && (!LOWER || j <= i)) ? *out(i, j) : T(0);
+      }
     for (int k = 0; k < kn; ++k) {
       T xa[TR], yb[TR];
 #pragma unroll
@@ -122,10 +128,8 @@ __device__ __forceinline__ void tiled_update(int m, int nc, int kn, FX X, FY Y, 
 #pragma unroll
       for (int b = 0; b < TR; ++b) {
         const int i = i0 + a, j = j0 + 16 * b;
-        if (i < m && j < nc && (!LOWER || j <= i)) {
-          T *p = out(i, j);
-          *p = *p - acc[a][b];  // a lone subtraction is never contracted
-        }
+        if (i < m && j < nc && (!LOWER || j <= i))
+          *out(i, j) = cv[a][b] - acc[a][b];  // a lone subtraction is never contracted
       }
   }
 }
@@ -139,11 +143,12 @@ __device__ __forceinline__ void dot_update(int m, int nc, int kn, FX X, FY Y, FO
   for (int i = tid >> 5; i < m; i += BT / 32) {
     const int jend = LOWER ? min(i + 1, nc) : nc;
     for (int j = tid & 31; j < jend; j += 32) {
+      T *p = out(i, j);
+      const T cij = *p;  // read before the products: its latency overlaps them
       T sij = T(0);
 #pragma unroll 4
       for (int k = 0; k < kn; ++k) sij = madd(sij, X(i, k), Y(j, k), EXACT);
-      T *p = out(i, j);
-      *p = *p - sij;  // a lone subtraction is never contracted
+      *p = cij - sij;  // a lone subtraction is never contracted
     }
   }
 }
@@ -158,40 +163,120 @@ __device__ __forceinline__ void block_update(int m, int nc, int kn, FX X, FY Y, 
     tiled_update<T, EXACT, LOWER, 2>(m, nc, kn, X, Y, out);
 }
 
+// ------------------------------------------------- column steps of one s-block
+// Columns [0, sb) of rows [0, R) (R >= sb) of the block since the checkpoint,
+// row r's entries at row(r)[0 .. sb): Algorithm 1's column steps, in chunks
+// of CCH columns.  Per chunk:
+//   (a) warp 0, lane l holding row c0 + l of the chunk: the products of the
+//       block's finished columns k < c0 (k ascending), then
+//   (b) the chunk's cw x cw diagonal part column by column, the pivot and
+//       each column's entries passed between lanes by shuffles;
+//   (c) every row below the chunk subtracts the finished columns' products
+//       and then the chunk's columns one at a time, dividing by L_cc.
+// Two barriers per chunk instead of two per column.  Each entry still
+// receives its products in ascending k, one at a time, and one division by
+// its pivot -- the same operations in the same order as column by column, so
+// exact mode keeps the oracle's rounding sequence.  Returns 0, or the local
+// column + 1 of a pivot that is not positive (or NaN).
+constexpr int CCH = 16;
+
+template <typename T, bool EXACT, typename ROW>
+__device__ int chol_block_columns(int R, int sb, ROW row, int *s_bad) {
+  const int tid = threadIdx.x, lane = tid & 31;
+  for (int c0 = 0; c0 < sb; c0 += CCH) {
+    const int cw = min(CCH, sb - c0);
+    if (tid < 32) {  // (a) and (b): lane l < cw holds row c0 + l
+      const bool act = lane < cw;
+      T *Lr = row(c0 + (act ? lane : 0));
+      T va[CCH];
+#pragma unroll
+      for (int j = 0; j < CCH; ++j) va[j] = (act && j <= lane) ? Lr[c0 + j] : T(0);
+      if (act) {
+        for (int k = 0; k < c0; ++k) {
+          const T a = Lr[k];
+#pragma unroll
+          for (int j = 0; j < CCH; ++j)
+            if (j <= lane) va[j] = msub(va[j], a, row(c0 + j)[k], EXACT);
+        }
+      }
+      int bad = 0;
+#pragma unroll
+      for (int cc = 0; cc < CCH; ++cc) {
+        if (cc < cw && !bad) {
+          const T d = __shfl_sync(0xffffffffu, va[cc], cc);
+          if (!(d > T(0))) {  // uniform over the warp
+            bad = c0 + cc + 1;
+          } else {
+            const T lcc = dsqrt(d);
+            if (lane == cc) va[cc] = lcc;
+            else if (lane > cc) va[cc] = ddiv(va[cc], lcc);
+#pragma unroll
+            for (int cc2 = cc + 1; cc2 < CCH; ++cc2) {
+              const T l = __shfl_sync(0xffffffffu, va[cc], cc2);  // L_{c0+cc2, c0+cc}
+              if (lane >= cc2) va[cc2] = msub(va[cc2], va[cc], l, EXACT);
+            }
+          }
+        }
+      }
+      if (lane < cw) {
+#pragma unroll
+        for (int j = 0; j < CCH; ++j)
+          if (j <= lane) Lr[c0 + j] = va[j];
+      }
+      if (lane == 0) *s_bad = bad;
+    }
+    __syncthreads();
+    const int bad = *s_bad;
+    if (bad) return bad;  // uniform
+    for (int r = c0 + cw + tid; r < R; r += BT) {  // (c)
+      T *Lr = row(r);
+      T v[CCH];
+#pragma unroll
+      for (int j = 0; j < CCH; ++j) v[j] = j < cw ? Lr[c0 + j] : T(0);
+      for (int k = 0; k < c0; ++k) {
+        const T a = Lr[k];
+#pragma unroll
+        for (int j = 0; j < CCH; ++j)
+          if (j < cw) v[j] = msub(v[j], a, row(c0 + j)[k], EXACT);
+      }
+#pragma unroll
+      for (int cc = 0; cc < CCH; ++cc) {
+        if (cc < cw) {
+          const T *Lc = row(c0 + cc);
+          v[cc] = ddiv(v[cc], Lc[c0 + cc]);
+#pragma unroll
+          for (int cc2 = cc + 1; cc2 < CCH; ++cc2)
+            if (cc2 < cw) v[cc2] = msub(v[cc2], v[cc], row(c0 + cc2)[c0 + cc], EXACT);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < CCH; ++j)
+        if (j < cw) Lr[c0 + j] = v[j];
+    }
+    __syncthreads();
+  }
+  return 0;
+}
+
 // ------------------------------------------------- whole matrix in shared memory
 // S holds the packed lower triangle: (i, j), j <= i, at i (i + 1) / 2 + j.
 template <typename T, bool EXACT>
-__device__ int chol_in_smem(T *S, int n, int s, T *red) {
-  constexpr bool exact = EXACT;
-  const int tid = threadIdx.x;
-  int z = 0;
-  for (int c = 0; c < n; ++c) {
-    if (c == z + s) {
-      // delayed update: A[i][j] -= S_ij, S_ij = sum_{k=z}^{c-1} L_ik L_jk, c <= j <= i
-      const int z0 = z, c0 = c;
+__device__ int chol_in_smem(T *S, int n, int s, int *s_bad) {
+  for (int z = 0; z < n; z += s) {
+    if (z > 0) {
+      // delayed update of the previous block [z - s, z): A[i][j] -= S_ij,
+      // S_ij = sum_{k=z-s}^{z-1} L_ik L_jk, z <= j <= i
+      const int z0 = z - s, c0 = z;
       block_update<T, EXACT, true>(
-          n - c, n - c, c - z, [&](int i, int k) { return S[tri(c0 + i) + z0 + k]; },
+          n - c0, n - c0, s, [&](int i, int k) { return S[tri(c0 + i) + z0 + k]; },
           [&](int j, int k) { return S[tri(c0 + j) + z0 + k]; },
           [&](int i, int j) { return &S[tri(c0 + i) + c0 + j]; });
-      z = c;
       __syncthreads();
     }
-    // column step c: v_i = A_ic - sum_{k=z}^{c-1} L_ik L_ck for i >= c
-    const T *Lc = S + tri(c);
-    for (int i = c + tid; i < n; i += BT) {
-      const T *Li = S + tri(i);
-      T v = Li[c];
-#pragma unroll 4
-      for (int k = z; k < c; ++k) v = msub(v, Li[k], Lc[k], exact);
-      if (i == c) red[0] = v; else S[tri(i) + c] = v;
-    }
-    __syncthreads();
-    const T d = red[0];
-    if (!(d > T(0))) return c + 1;  // uniform: every thread read the same d
-    const T lcc = dsqrt(d);
-    for (int i = c + 1 + tid; i < n; i += BT) S[tri(i) + c] = ddiv(S[tri(i) + c], lcc);
-    if (tid == 0) S[tri(c) + c] = lcc;
-    __syncthreads();
+    const int sb = min(s, n - z);
+    const int bad = chol_block_columns<T, EXACT>(
+        n - z, sb, [&](int r) { return S + tri(z + r) + z; }, s_bad);
+    if (bad) return z + bad;
   }
   return 0;
 }
@@ -199,34 +284,35 @@ __device__ int chol_in_smem(T *S, int n, int s, T *red) {
 // ------------------------------------------------- panel in shared memory
 // P: rows [z, n) x columns [z, z + sb) of the working matrix, row-major with
 // leading dimension ldp >= s (odd when it fits: rows then fall in different
-// shared-memory banks).
+// shared-memory banks).  Once the trailing matrix's lower triangle fits in
+// the `smem_elems` elements of P's buffer, it moves there and the rest of
+// the factorization runs as the whole-matrix path (same steps, same order).
 template <typename T, bool EXACT>
-__device__ int chol_panel_path(T *A, int64_t lda, int n, int s, T *P, int ldp, T *red) {
-  constexpr bool exact = EXACT;
+__device__ int chol_panel_path(T *A, int64_t lda, int n, int s, T *P, int ldp, int *s_bad,
+                               int64_t smem_elems) {
   const int tid = threadIdx.x;
   for (int z = 0; z < n; z += s) {
+    if (z > 0 && tri(n - z) <= smem_elems) {
+      const int m = n - z;
+      T *S = P;
+      for (int r = tid >> 5; r < m; r += BT / 32)
+        for (int q = tid & 31; q <= r; q += 32) S[tri(r) + q] = A[(int64_t)(z + r) * lda + z + q];
+      __syncthreads();
+      const int bad = chol_in_smem<T, EXACT>(S, m, s, s_bad);
+      __syncthreads();
+      for (int r = tid >> 5; r < m; r += BT / 32)
+        for (int q = tid & 31; q <= r; q += 32) A[(int64_t)(z + r) * lda + z + q] = S[tri(r) + q];
+      __syncthreads();
+      return bad ? z + bad : 0;
+    }
     const int sb = min(s, n - z);
     const int rows = n - z;
     for (int r = tid >> 5; r < rows; r += BT / 32)
       for (int q = tid & 31; q < sb; q += 32) P[(int64_t)r * ldp + q] = A[(int64_t)(z + r) * lda + z + q];
     __syncthreads();
-    for (int c = 0; c < sb; ++c) {  // column z + c, local index c
-      const T *Pc = P + (int64_t)c * ldp;
-      for (int r = c + tid; r < rows; r += BT) {
-        T *Pr = P + (int64_t)r * ldp;
-        T v = Pr[c];
-#pragma unroll 4
-        for (int k = 0; k < c; ++k) v = msub(v, Pr[k], Pc[k], exact);
-        if (r == c) red[0] = v; else Pr[c] = v;
-      }
-      __syncthreads();
-      const T d = red[0];
-      if (!(d > T(0))) return z + c + 1;
-      const T lcc = dsqrt(d);
-      for (int r = c + 1 + tid; r < rows; r += BT) P[(int64_t)r * ldp + c] = ddiv(P[(int64_t)r * ldp + c], lcc);
-      if (tid == 0) P[(int64_t)c * ldp + c] = lcc;
-      __syncthreads();
-    }
+    const int bad = chol_block_columns<T, EXACT>(
+        rows, sb, [&](int r) { return P + (int64_t)r * ldp; }, s_bad);
+    if (bad) return z + bad;
     for (int r = tid >> 5; r < rows; r += BT / 32)
       for (int q = tid & 31; q < sb; q += 32)
         if (q <= r) A[(int64_t)(z + r) * lda + z + q] = P[(int64_t)r * ldp + q];
@@ -367,7 +453,7 @@ template <typename T, bool EXACT>
 __global__ void __launch_bounds__(BT, 2) batched_chol_kernel(Plan plan, int64_t smem_elems) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *buf = reinterpret_cast<T *>(smem_raw);
-  __shared__ T red[1];
+  __shared__ int s_bad;
   __shared__ int s_idx;
   for (;;) {
     if (threadIdx.x == 0) {
@@ -389,7 +475,7 @@ __global__ void __launch_bounds__(BT, 2) batched_chol_kernel(Plan plan, int64_t 
         for (int r = threadIdx.x >> 5; r < n; r += BT / 32)
           for (int q = threadIdx.x & 31; q <= r; q += 32) buf[tri(r) + q] = A[(int64_t)r * lda + q];
         __syncthreads();
-        info = chol_in_smem<T, EXACT>(buf, n, min(s, n), red);
+        info = chol_in_smem<T, EXACT>(buf, n, min(s, n), &s_bad);
         __syncthreads();
         for (int r = threadIdx.x >> 5; r < n; r += BT / 32)
           for (int q = threadIdx.x & 31; q < n; q += 32)
@@ -402,7 +488,7 @@ __global__ void __launch_bounds__(BT, 2) batched_chol_kernel(Plan plan, int64_t 
         __syncthreads();
         const int sp = max(1, (int)min64(s, smem_elems / n));  // panel width that fits
         const int ldp = (int64_t)n * (sp | 1) <= smem_elems ? (sp | 1) : sp;
-        info = chol_panel_path<T, EXACT>(L, ldl, n, sp, buf, ldp, red);
+        info = chol_panel_path<T, EXACT>(L, ldl, n, sp, buf, ldp, &s_bad, smem_elems);
         __syncthreads();
       }
     }
