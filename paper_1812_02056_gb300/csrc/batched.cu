@@ -111,6 +111,7 @@ __device__ __forceinline__ void tiled_update(int m, int nc, int kn, FX X, FY Y, 
         const int i = i0 + a, j = j0 + 16 * b;
         cv[a][b] = (i < m && j < nc && (!LOWER || j <= i)) ? *out(i, j) : T(0);
       }
+#pragma unroll 4
     for (int k = 0; k < kn; ++k) {
       T xa[TR], yb[TR];
 #pragma unroll
