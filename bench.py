@@ -476,7 +476,11 @@ def run_mixed(args):
     h = binding.Handle(0)
     n, nrhs = args.n, 16
     t0 = time.perf_counter()
-    A = inputs.spd_logspaced(n, inputs.seed_for(inputs.W_MIXED), cond=1e4, device=dev)
+    if args.host_inputs:  # numpy QR on the host (no device QR library in the process)
+        A = torch.from_numpy(inputs.spd_logspaced(n, inputs.seed_for(inputs.W_MIXED),
+                                                  cond=1e4)).to(dev)
+    else:
+        A = inputs.spd_logspaced(n, inputs.seed_for(inputs.W_MIXED), cond=1e4, device=dev)
     B = torch.from_numpy(inputs.rhs(n, nrhs, inputs.seed_for(inputs.W_MIXED, 1))).to(dev)
     gen_s = time.perf_counter() - t0
     out = {"mode": "mixed", "n": n, "nrhs": nrhs, "cond": 1e4, "input_generation_s": gen_s,
@@ -934,6 +938,8 @@ def main():
     ap.add_argument("--tune", action="store_true",
                     help="mixed mode: pick (s, inner step) with gb_tune_step, then factor with s = 0")
     ap.add_argument("--batch-count", type=int, default=10000)
+    ap.add_argument("--host-inputs", action="store_true",
+                    help="mixed: build A with numpy on the host instead of on the device")
     ap.add_argument("--no-tune", action="store_true",
                     help="batched: keep the library's default step rule (no autotuner launches)")
     ap.add_argument("--batch-cpu-sample", type=int, default=200)

@@ -123,14 +123,23 @@ struct Staged {
     }
     owned = true;
     if (copy_out) host_dst = const_cast<void *>(p);
-    if (copy_in && r > 0 && c > 0)
-      GB_CUDA_TRY(cudaMemcpy2DAsync(dev, ldd * e, p, l * e, c * e, r, cudaMemcpyHostToDevice, s));
+    if (copy_in && r > 0 && c > 0) {
+      if (l == c)  // dense rows: one linear copy
+        GB_CUDA_TRY(cudaMemcpyAsync(dev, p, (size_t)r * c * e, cudaMemcpyHostToDevice, s));
+      else
+        GB_CUDA_TRY(cudaMemcpy2DAsync(dev, ldd * e, p, l * e, c * e, r, cudaMemcpyHostToDevice, s));
+    }
     return GB_OK;
   }
   gb_status finish() {
-    if (host_dst && rows > 0 && cols > 0)
-      GB_CUDA_TRY(cudaMemcpy2DAsync(host_dst, ld * esz, dev, ldd * esz, cols * esz, rows,
+    if (host_dst && rows > 0 && cols > 0) {
+      if (ld == cols)
+        GB_CUDA_TRY(cudaMemcpyAsync(host_dst, dev, (size_t)rows * cols * esz,
                                     cudaMemcpyDeviceToHost, st));
+      else
+        GB_CUDA_TRY(cudaMemcpy2DAsync(host_dst, ld * esz, dev, ldd * esz, cols * esz, rows,
+                                      cudaMemcpyDeviceToHost, st));
+    }
     return GB_OK;
   }
   ~Staged() {
@@ -937,8 +946,10 @@ gb_status solve_common(bool is_lu, gb_handle *h, int64_t n, int64_t nrhs, const 
 
   // iterative refinement in FP64
   const size_t rbytes = (size_t)n * nrhs * 8;
-  if ((r = ws_reserve(h, WS_SOLVE, rbytes, st)) != GB_OK) return r;
+  const size_t pbytes = residual_work_bytes(n, nrhs, h->sm_count);
+  if ((r = ws_reserve(h, WS_SOLVE, rbytes + pbytes, st)) != GB_OK) return r;
   double *R = (double *)h->ws[WS_SOLVE].ptr;
+  double *P = pbytes ? R + (size_t)n * nrhs : nullptr;
   double *norms = h->d_scalars;  // [0]: ||A||_inf; [1..]: 3 * nrhs norms
   if ((size_t)(1 + 3 * nrhs) > 4096) return GB_ERR_UNSUPPORTED;
   GB_CUDA_TRY(launch_inf_norm_rows(A, lda, n, norms, st));
@@ -946,7 +957,8 @@ gb_status solve_common(bool is_lu, gb_handle *h, int64_t n, int64_t nrhs, const 
   int it = 0;
   double eta = 0.0;
   for (;;) {
-    GB_CUDA_TRY(launch_residual(A, lda, X, ldx, B, ldb, R, nrhs, n, nrhs, norms + 1, st));
+    GB_CUDA_TRY(launch_residual(A, lda, X, ldx, B, ldb, R, nrhs, n, nrhs, norms + 1, P, pbytes,
+                                h->sm_count, st));
     GB_CUDA_TRY(cudaMemcpyAsync(hn.data(), norms, sizeof(double) * hn.size(),
                                 cudaMemcpyDeviceToHost, st));
     GB_CUDA_TRY(cudaStreamSynchronize(st));

@@ -221,9 +221,14 @@ template <typename Tf>
 cudaError_t launch_trsm_inv(const Tf *F, int64_t ldf, const Tf *Dinv, double *B, int64_t ldb,
                             int64_t n, int64_t nrhs, int kind, int *sync, unsigned epoch, int *err,
                             int64_t spin_limit, cudaStream_t st);
+// r = b - A x in FP64 (and the norms of r, x, b per column when `norms`);
+// small orders split the columns of A into slices whose partial products go
+// to `work` (residual_work_bytes; without it, one slice).
 cudaError_t launch_residual(const double *A, int64_t lda, const double *X, int64_t ldx,
                             const double *B, int64_t ldb, double *R, int64_t ldr, int64_t n,
-                            int64_t nrhs, double *norms, cudaStream_t st);
+                            int64_t nrhs, double *norms, double *work, size_t work_bytes,
+                            int sm_count, cudaStream_t st);
+size_t residual_work_bytes(int64_t n, int64_t nrhs, int sm_count);
 cudaError_t launch_inf_norm_rows(const double *A, int64_t lda, int64_t n, double *out,
                                  cudaStream_t st);
 cudaError_t launch_axpy_cols(double *X, int64_t ldx, const double *D, int64_t ldd, int64_t n,

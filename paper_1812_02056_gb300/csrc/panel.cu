@@ -215,6 +215,7 @@ __global__ void __launch_bounds__(ROWS)
   T(*LdT)[PADT] = reinterpret_cast<T(*)[PADT]>(smem_raw + sizeof(T) * PB * (PB + 1));  // LdT[k][i] = L_ik
   T(*Ys)[ROWS] = reinterpret_cast<T(*)[ROWS]>(smem_raw + sizeof(T) * (PB * (PB + 1) + PB * PADT));
   __shared__ int s_last, s_bad;
+  __shared__ T s_piv;
   if (load_status(status) != 0) return;
   const int tid = threadIdx.x;
   T *D = W + j0 * ld + j0;
@@ -261,81 +262,140 @@ __global__ void __launch_bounds__(ROWS)
       s_last = (a == (unsigned long long)gridDim.x - 1) ? 1 : 0;
       if (s_last) atomicExch(arrivals, 0ULL);  // every CTA has arrived
     }
-    // Per 16-column chunk: every row i in [c0, bw) first receives the
-    // products of the finished columns k < c0 (thread i, its row in
-    // registers); then warp 0 finishes the chunk's columns one at a time,
-    // lane l holding rows c0 + l and c0 + 32 + l, with the pivot and the
-    // column's entries passed between lanes by shuffles (no barrier inside
-    // the chunk).
-    const int lane = tid & 31;
-    for (int c0 = 0; c0 < bw; c0 += CH) {
-      const int cw = min(CH, bw - c0);
-      if (tid >= c0 && tid < bw) {  // products of the finished columns k < c0
+    if constexpr (sizeof(T) == 8) {
+      // FP64 data: GB300 issues FP64 arithmetic at a small fraction of the
+      // FP32 rate per scheduler, so the block's column updates stay spread
+      // over the rows' threads (two warps): thread i < bw holds row i's
+      // chunk columns; per column, the owner of the diagonal forms the pivot
+      // and one barrier publishes it, a second the scaled column.
+      for (int c0 = 0; c0 < bw; c0 += CH) {
+        const bool mine = tid >= c0 && tid < bw;
+        const int cw = min(CH, bw - c0);
         T v[CH];
 #pragma unroll
-        for (int j = 0; j < CH; ++j) v[j] = Ld[tid][c0 + j];
-        for (int k0 = 0; k0 < c0; k0 += 4) {  // c0 is a multiple of 16
+        for (int j = 0; j < CH; ++j) v[j] = (mine && j < cw && c0 + j <= tid) ? Ld[tid][c0 + j] : T(0);
+        if (mine) {  // products of the finished columns k < c0
+          for (int k = 0; k < c0; ++k) {
+            const T lik = Ld[tid][k];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const T lik = Ld[tid][k0 + u];
-            T lk[CH];
-            load_row16(lk, &LdT[k0 + u][c0]);
-#pragma unroll
-            for (int j = 0; j < CH; ++j) v[j] = v[j] - lik * lk[j];
+            for (int j = 0; j < CH; ++j) v[j] = v[j] - lik * LdT[k][c0 + j];
           }
         }
 #pragma unroll
-        for (int j = 0; j < CH; ++j) Ld[tid][c0 + j] = v[j];
-      }
-      __syncthreads();
-      if (tid < 32) {
-        const int ra = c0 + lane, rb = c0 + 32 + lane;  // rb > every column of the chunk
-        T va[CH], vb[CH];
-#pragma unroll
-        for (int j = 0; j < CH; ++j) {
-          va[j] = ra < bw ? Ld[ra][c0 + j] : T(0);
-          vb[j] = rb < bw ? Ld[rb][c0 + j] : T(0);
-        }
-        int bad = 0;
-#pragma unroll
         for (int cc = 0; cc < CH; ++cc) {  // the chunk's columns, one at a time
-          if (cc < cw && !bad) {
-            const T d = __shfl_sync(0xffffffffu, va[cc], cc);  // row c's running diagonal
-            if (!(d > T(0))) {  // not positive, or NaN: breakdown (uniform over the warp)
-              bad = c0 + cc + 1;
-            } else {
+          if (cc < cw) {
+            const int c = c0 + cc;
+            if (tid == c) {
+              const T d = v[cc];
+              s_bad = (d > T(0)) ? 0 : c + 1;  // not positive, or NaN: breakdown
               const T piv = sqrt(d);
-              const T rpiv = T(1) / piv;  // the column is scaled by 1 / L_cc
-              va[cc] = lane == cc ? piv : va[cc] * rpiv;
-              vb[cc] = vb[cc] * rpiv;
+              s_piv = T(1) / piv;  // the column is scaled by 1 / L_cc
+              v[cc] = piv;
+              LdT[c][c] = piv;
+            }
+            __syncthreads();
+            if (s_bad) {  // uniform
+              if (blockIdx.x == 0 && tid == 0) atomicCAS(status, 0, (int)(j0 + s_bad));
+              if (MODE != PANEL_DIAG) cp_async_wait_all();
+              return;
+            }
+            if (tid > c && tid < bw) {
+              v[cc] = v[cc] * s_piv;
+              LdT[c][tid] = v[cc];
+            }
+            __syncthreads();
+            if (tid > c && tid < bw) {
+              const T lic = v[cc];
 #pragma unroll
-              for (int cc2 = cc + 1; cc2 < CH; ++cc2) {
-                const T l = __shfl_sync(0xffffffffu, va[cc], cc2);  // L_{c0+cc2, c}
-                va[cc2] = va[cc2] - va[cc] * l;
-                vb[cc2] = vb[cc2] - vb[cc] * l;
-              }
+              for (int cc2 = cc + 1; cc2 < CH; ++cc2)
+                if (c0 + cc2 <= tid) v[cc2] = v[cc2] - lic * LdT[c][c0 + cc2];
             }
           }
         }
-        // the chunk's columns of rows >= c0 (entries on or below the diagonal)
+        if (mine) {
 #pragma unroll
-        for (int j = 0; j < CH; ++j) {
-          if (j < cw && ra < bw && c0 + j <= ra) {
-            Ld[ra][c0 + j] = va[j];
-            LdT[c0 + j][ra] = va[j];
-          }
-          if (j < cw && rb < bw) {
-            Ld[rb][c0 + j] = vb[j];
-            LdT[c0 + j][rb] = vb[j];
-          }
+          for (int j = 0; j < CH; ++j)
+            if (j < cw && c0 + j <= tid) Ld[tid][c0 + j] = v[j];
         }
-        if (lane == 0) s_bad = bad;
+        __syncthreads();
       }
-      __syncthreads();
-      if (s_bad) {  // uniform
-        if (blockIdx.x == 0 && tid == 0) atomicCAS(status, 0, (int)(j0 + s_bad));
-        if (MODE != PANEL_DIAG) cp_async_wait_all();
-        return;
+    } else {
+      // Per 16-column chunk: every row i in [c0, bw) first receives the
+      // products of the finished columns k < c0 (thread i, its row in
+      // registers); then warp 0 finishes the chunk's columns one at a time,
+      // lane l holding rows c0 + l and c0 + 32 + l, with the pivot and the
+      // column's entries passed between lanes by shuffles (no barrier inside
+      // the chunk).
+      const int lane = tid & 31;
+      for (int c0 = 0; c0 < bw; c0 += CH) {
+        const int cw = min(CH, bw - c0);
+        if (tid >= c0 && tid < bw) {  // products of the finished columns k < c0
+          T v[CH];
+#pragma unroll
+          for (int j = 0; j < CH; ++j) v[j] = Ld[tid][c0 + j];
+          for (int k0 = 0; k0 < c0; k0 += 4) {  // c0 is a multiple of 16
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const T lik = Ld[tid][k0 + u];
+              T lk[CH];
+              load_row16(lk, &LdT[k0 + u][c0]);
+#pragma unroll
+              for (int j = 0; j < CH; ++j) v[j] = v[j] - lik * lk[j];
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < CH; ++j) Ld[tid][c0 + j] = v[j];
+        }
+        __syncthreads();
+        if (tid < 32) {
+          const int ra = c0 + lane, rb = c0 + 32 + lane;  // rb > every column of the chunk
+          T va[CH], vb[CH];
+#pragma unroll
+          for (int j = 0; j < CH; ++j) {
+            va[j] = ra < bw ? Ld[ra][c0 + j] : T(0);
+            vb[j] = rb < bw ? Ld[rb][c0 + j] : T(0);
+          }
+          int bad = 0;
+#pragma unroll
+          for (int cc = 0; cc < CH; ++cc) {  // the chunk's columns, one at a time
+            if (cc < cw && !bad) {
+              const T d = __shfl_sync(0xffffffffu, va[cc], cc);  // row c's running diagonal
+              if (!(d > T(0))) {  // not positive, or NaN: breakdown (uniform over the warp)
+                bad = c0 + cc + 1;
+              } else {
+                const T piv = sqrt(d);
+                const T rpiv = T(1) / piv;  // the column is scaled by 1 / L_cc
+                va[cc] = lane == cc ? piv : va[cc] * rpiv;
+                vb[cc] = vb[cc] * rpiv;
+#pragma unroll
+                for (int cc2 = cc + 1; cc2 < CH; ++cc2) {
+                  const T l = __shfl_sync(0xffffffffu, va[cc], cc2);  // L_{c0+cc2, c}
+                  va[cc2] = va[cc2] - va[cc] * l;
+                  vb[cc2] = vb[cc2] - vb[cc] * l;
+                }
+              }
+            }
+          }
+          // the chunk's columns of rows >= c0 (entries on or below the diagonal)
+#pragma unroll
+          for (int j = 0; j < CH; ++j) {
+            if (j < cw && ra < bw && c0 + j <= ra) {
+              Ld[ra][c0 + j] = va[j];
+              LdT[c0 + j][ra] = va[j];
+            }
+            if (j < cw && rb < bw) {
+              Ld[rb][c0 + j] = vb[j];
+              LdT[c0 + j][rb] = vb[j];
+            }
+          }
+          if (lane == 0) s_bad = bad;
+        }
+        __syncthreads();
+        if (s_bad) {  // uniform
+          if (blockIdx.x == 0 && tid == 0) atomicCAS(status, 0, (int)(j0 + s_bad));
+          if (MODE != PANEL_DIAG) cp_async_wait_all();
+          return;
+        }
       }
     }
     if (s_last) {

@@ -382,20 +382,26 @@ __device__ __forceinline__ void atomic_max_nonneg(double *addr, double v) {
   atomicMax(reinterpret_cast<long long *>(addr), __double_as_longlong(v));
 }
 
+// With `P` (gridDim.y K slices of `kslice` columns): slice blockIdx.y writes
+// its partial products P[slice][i][c] instead; residual_finish_kernel sums
+// the slices in order.  Small orders use slices so that the grid still
+// fills every SM.
 __global__ void __launch_bounds__(RES_THREADS)
     residual_kernel(const double *__restrict__ A, int64_t lda, const double *__restrict__ X,
                     int64_t ldx, const double *__restrict__ B, int64_t ldb, double *__restrict__ R,
-                    int64_t ldr, int64_t n, int64_t nrhs, double *norms) {
+                    int64_t ldr, int64_t n, int64_t nrhs, double *norms, int64_t kslice,
+                    double *__restrict__ P) {
   __shared__ double As[RES_ROWS][RES_KC + 1];
   __shared__ __align__(16) double Xs[RES_KC][RES_NC];
   const int tid = threadIdx.x;
   const int r = tid >> 2, g = tid & 3;  // row, group of 4 columns
   const int64_t i0 = (int64_t)blockIdx.x * RES_ROWS;
+  const int64_t kb = (int64_t)blockIdx.y * kslice, ke = min64(n, kb + kslice);
   for (int64_t c0 = 0; c0 < nrhs; c0 += RES_NC) {
     const int cols = (int)min64(RES_NC, nrhs - c0);
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int64_t k0 = 0; k0 < n; k0 += RES_KC) {
-      const int kr = (int)min64(RES_KC, n - k0);
+    for (int64_t k0 = kb; k0 < ke; k0 += RES_KC) {
+      const int kr = (int)min64(RES_KC, ke - k0);
       __syncthreads();
       for (int idx = tid; idx < RES_ROWS * RES_KC; idx += RES_THREADS) {
         const int ii = idx / RES_KC, k = idx % RES_KC;
@@ -419,6 +425,14 @@ __global__ void __launch_bounds__(RES_THREADS)
       }
     }
     const int64_t i = i0 + r;
+    if (P) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int c = 4 * g + q;
+        if (i < n && c < cols) P[((int64_t)blockIdx.y * n + i) * nrhs + c0 + c] = acc[q];
+      }
+      continue;
+    }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int c = 4 * g + q;
@@ -586,16 +600,65 @@ cudaError_t launch_trsm_inv(const Tf *F, int64_t ldf, const Tf *Dinv, double *B,
   return cudaGetLastError();
 }
 
+// r = b - (P[0] + P[1] + ... ) with the slices summed in order; the norms as
+// in residual_kernel.
+__global__ void residual_finish_kernel(const double *__restrict__ P, int slices,
+                                       const double *__restrict__ X, int64_t ldx,
+                                       const double *__restrict__ B, int64_t ldb,
+                                       double *__restrict__ R, int64_t ldr, int64_t n,
+                                       int64_t nrhs, double *norms) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * nrhs) return;
+  const int64_t i = e / nrhs, c = e % nrhs;
+  double acc = P[e];
+  for (int sl = 1; sl < slices; ++sl) acc += P[(int64_t)sl * n * nrhs + e];
+  const double rv = B[i * ldb + c] - acc;
+  R[i * ldr + c] = rv;
+  if (norms) {
+    atomic_max_nonneg(&norms[c], finite_abs(rv));
+    atomic_max_nonneg(&norms[nrhs + c], finite_abs(X[i * ldx + c]));
+    atomic_max_nonneg(&norms[2 * nrhs + c], finite_abs(B[i * ldb + c]));
+  }
+}
+
+int residual_slices(int64_t n, int sm_count) {
+  const int64_t blocks = ceil_div(n, RES_ROWS);
+  const int64_t want = 4 * (int64_t)sm_count;  // about eight warps per SM
+  if (blocks >= want || n < 4 * RES_KC) return 1;
+  return (int)std::min<int64_t>(8, std::min<int64_t>(ceil_div(want, blocks), n / (2 * RES_KC)));
+}
+
+size_t residual_work_bytes(int64_t n, int64_t nrhs, int sm_count) {
+  const int sl = residual_slices(n, sm_count);
+  return sl > 1 ? (size_t)sl * n * nrhs * sizeof(double) : 0;
+}
+
 cudaError_t launch_residual(const double *A, int64_t lda, const double *X, int64_t ldx,
                             const double *B, int64_t ldb, double *R, int64_t ldr, int64_t n,
-                            int64_t nrhs, double *norms, cudaStream_t st) {
+                            int64_t nrhs, double *norms, double *work, size_t work_bytes,
+                            int sm_count, cudaStream_t st) {
   if (n <= 0 || nrhs <= 0) return cudaSuccess;
   if (norms) {
     cudaError_t e = cudaMemsetAsync(norms, 0, sizeof(double) * 3 * nrhs, st);
     if (e != cudaSuccess) return e;
   }
-  residual_kernel<<<(unsigned)ceil_div(n, RES_ROWS), RES_THREADS, 0, st>>>(A, lda, X, ldx, B, ldb,
-                                                                          R, ldr, n, nrhs, norms);
+  int sl = residual_slices(n, sm_count);
+  if (sl > 1 && (!work || work_bytes < residual_work_bytes(n, nrhs, sm_count))) sl = 1;
+  if (sl == 1) {
+    residual_kernel<<<(unsigned)ceil_div(n, RES_ROWS), RES_THREADS, 0, st>>>(
+        A, lda, X, ldx, B, ldb, R, ldr, n, nrhs, norms, n, nullptr);
+    count_launch();
+    return cudaGetLastError();
+  }
+  // K slices: whole 64-column chunks, the last slice possibly shorter
+  const int64_t kslice = ceil_div(ceil_div(n, sl), RES_KC) * RES_KC;
+  sl = (int)ceil_div(n, kslice);
+  residual_kernel<<<dim3((unsigned)ceil_div(n, RES_ROWS), (unsigned)sl), RES_THREADS, 0, st>>>(
+      A, lda, X, ldx, B, ldb, R, ldr, n, nrhs, nullptr, kslice, work);
+  count_launch();
+  const int64_t total = n * nrhs;
+  residual_finish_kernel<<<(unsigned)ceil_div(total, 256), 256, 0, st>>>(work, sl, X, ldx, B, ldb,
+                                                                         R, ldr, n, nrhs, norms);
   count_launch();
   return cudaGetLastError();
 }
