@@ -123,14 +123,9 @@ __host__ __device__ __forceinline__ int64_t max64(int64_t a, int64_t b) { return
 
 // ------------------------------------------------------------ kernels (host)
 // Column steps of one inner block [j0, j0+bw) of the working matrix W (row
-// major, ld), rows j0..n-1.  Storage T, diag-block arithmetic Tc.
-template <typename T, typename Tc>
-cudaError_t launch_chol_diag(T *W, int64_t ld, int64_t j0, int bw, int *status, cudaStream_t st);
-template <typename T>
-cudaError_t launch_chol_rows(T *W, int64_t ld, int64_t row0, int64_t nrows, int64_t j0, int bw,
-                             int *status, cudaStream_t st);
-// Fused column steps of one inner block (diagonal block in every CTA, then
-// its rows); `arrivals` is a zeroed counter the kernel leaves zeroed.
+// major, ld), rows j0..n-1, storage T.
+// Cholesky: fused column steps of one inner block (diagonal block in every
+// CTA, then its rows); `arrivals` is a zeroed counter the kernel leaves zeroed.
 template <typename T>
 cudaError_t launch_chol_panel(T *W, int64_t ld, int64_t j0, int bw, int64_t nrows, int *status,
                               unsigned long long *arrivals, cudaStream_t st);

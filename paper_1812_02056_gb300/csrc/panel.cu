@@ -8,11 +8,14 @@
 //             U_ci = (A_ci - sum_{k=z}^{c-1} L_ck U_ki) / L_cc      (i > c)
 // is formed here with its sum taken in ascending k, one product at a time, as
 // the paper writes it.  The work is split by dependence, not reordered:
-//   *_diag_kernel  the bw x bw diagonal block, whose columns depend on one
-//                  another (one CTA, shared memory, bw dependent steps);
-//   *_rows_kernel  rows below the block: each row is an independent forward
-//                  substitution against the finished diagonal block;
-//   lu_cols_kernel columns of U right of the block, likewise independent.
+//   the bw x bw diagonal block, whose columns depend on one another (one
+//     CTA, shared memory, bw dependent steps): chol_panel_kernel's first
+//     part (every CTA for FP32 data; one PANEL_DIAG launch for FP64),
+//     lu_diag_kernel;
+//   the rows below the block: each row is an independent forward
+//     substitution against the finished diagonal block (chol_panel_kernel's
+//     second part, lu_rows_kernel);
+//   lu_cols_kernel: columns of U right of the block, likewise independent.
 // W already holds A minus every delayed update applied before this block.
 #include <math.h>
 
@@ -44,104 +47,7 @@ __device__ __forceinline__ void cp_async_wait_all() {
 
 constexpr int DIAG_THREADS = 256;  // 16 x 16 threads, 4 x 4 elements each
 
-// ---------------------------------------------------------------- Cholesky
-template <typename T, typename Tc>
-__global__ void __launch_bounds__(DIAG_THREADS)
-    chol_diag_kernel(T *__restrict__ W, int64_t ld, int64_t j0, int bw, int *status) {
-  __shared__ Tc S[64][65];
-  if (load_status(status) != 0) return;
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  T *D = W + j0 * ld + j0;
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int i = ty + 16 * a, j = tx + 16 * b;
-      S[i][j] = (i < bw && j <= i) ? (Tc)D[(int64_t)i * ld + j] : Tc(0);
-    }
-  __syncthreads();
-  for (int c = 0; c < bw; ++c) {
-    const Tc d = S[c][c];  // A_cc minus sum_{k<c} L_ck^2, one product at a time
-    if (!(d > Tc(0))) {    // not positive, or NaN: Algorithm 1 assumes this away
-      if (tid == 0) atomicCAS(status, 0, (int)(j0 + c + 1));
-      return;  // d is the same for every thread: the whole CTA leaves
-    }
-    const Tc lcc = sqrt(d);
-    if (tid > c && tid < bw) S[tid][c] = S[tid][c] / lcc;
-    __syncthreads();
-    if (tid == 0) S[c][c] = lcc;
-    // subtract column c's product from the entries still to be finished
-    // (lower triangle of the trailing (bw-c-1)^2 block, enumerated densely so
-    // that no lane idles); each entry receives its products in ascending k
-    const int m = bw - c - 1;
-    const int tri = m * (m + 1) / 2;
-    for (int e = tid; e < tri; e += DIAG_THREADS) {
-      int r = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
-      while (r * (r + 1) / 2 > e) --r;
-      while ((r + 1) * (r + 2) / 2 <= e) ++r;
-      const int i = c + 1 + r, j = c + 1 + (e - r * (r + 1) / 2);
-      S[i][j] = S[i][j] - S[i][c] * S[j][c];
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int i = ty + 16 * a, j = tx + 16 * b;
-      if (i < bw && j <= i) D[(int64_t)i * ld + j] = (T)S[i][j];
-    }
-}
-
 constexpr int ROWS_PER_CTA = 64;  // one row per thread; small CTAs spread rows over all SMs
-
-// Rows [row0, row0 + nrows) of the panel columns [j0, j0 + bw): each thread
-// owns one row x and solves x_c = (a_c - sum_{k<c} x_k L_ck) / L_cc.
-template <typename T, int B>
-__global__ void __launch_bounds__(ROWS_PER_CTA)
-    chol_rows_kernel(T *__restrict__ W, int64_t ld, int64_t row0, int64_t nrows, int64_t j0,
-                     int bw, const int *status) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T(*LD)[B + 1] = reinterpret_cast<T(*)[B + 1]>(smem_raw);
-  T(*X)[B + 1] = reinterpret_cast<T(*)[B + 1]>(smem_raw + sizeof(T) * B * (B + 1));
-  if (load_status(status) != 0) return;
-  const int tid = threadIdx.x;
-  const int64_t rbase = row0 + (int64_t)blockIdx.x * ROWS_PER_CTA;
-  const int rows_here = (int)min64(ROWS_PER_CTA, row0 + nrows - rbase);
-  for (int idx = tid; idx < B * B; idx += ROWS_PER_CTA) {
-    const int i = idx / B, j = idx % B;
-    LD[i][j] = (i < bw && j <= i) ? W[(j0 + i) * ld + j0 + j] : T(0);
-  }
-  for (int idx = tid; idx < ROWS_PER_CTA * B; idx += ROWS_PER_CTA) {
-    const int r = idx / B, j = idx % B;
-    X[r][j] = (r < rows_here && j < bw) ? W[(rbase + r) * ld + j0 + j] : T(0);
-  }
-  __syncthreads();
-  if (tid < rows_here) {
-    T x[B];
-#pragma unroll
-    for (int c = 0; c < B; ++c) x[c] = X[tid][c];
-    // x_c is final once every x_k (k < c) has been subtracted; subtracting
-    // x_c's product from all later entries right away keeps each entry's
-    // products in ascending k while exposing independent work
-#pragma unroll
-    for (int c = 0; c < B; ++c) {
-      if (c < bw) {
-        const T xc = x[c] / LD[c][c];
-        x[c] = xc;
-#pragma unroll
-        for (int c2 = c + 1; c2 < B; ++c2) x[c2] = x[c2] - xc * LD[c2][c];
-      }
-    }
-#pragma unroll
-    for (int c = 0; c < B; ++c) X[tid][c] = x[c];
-  }
-  __syncthreads();
-  for (int idx = tid; idx < ROWS_PER_CTA * B; idx += ROWS_PER_CTA) {
-    const int r = idx / B, j = idx % B;
-    if (r < rows_here && j < bw) W[(rbase + r) * ld + j0 + j] = X[r][j];
-  }
-}
 
 // ------------------------------------------------ fused column-step kernel
 // One launch per inner block: every CTA factors the bw x bw diagonal block
@@ -576,14 +482,6 @@ __global__ void copy_matrix_kernel(const Tin *__restrict__ A, int64_t lda, Tout 
 }  // namespace
 
 // ------------------------------------------------------------------ launchers
-template <typename T, typename Tc>
-cudaError_t launch_chol_diag(T *W, int64_t ld, int64_t j0, int bw, int *status, cudaStream_t st) {
-  if (bw < 1 || bw > 64) return cudaErrorInvalidValue;
-  chol_diag_kernel<T, Tc><<<1, DIAG_THREADS, 0, st>>>(W, ld, j0, bw, status);
-  count_launch();
-  return cudaGetLastError();
-}
-
 template <typename T, int B>
 constexpr size_t rows_smem_bytes() {
   return sizeof(T) * (size_t)(B + ROWS_PER_CTA) * (B + 1);
@@ -598,18 +496,6 @@ cudaError_t allow_smem(K kernel, size_t bytes) {
 }
 
 template <typename T, int B>
-cudaError_t chol_rows_b(T *W, int64_t ld, int64_t row0, int64_t nrows, int64_t j0, int bw,
-                        int *status, cudaStream_t st) {
-  constexpr size_t smem = rows_smem_bytes<T, B>();
-  static cudaError_t attr = allow_smem(chol_rows_kernel<T, B>, smem);
-  if (attr != cudaSuccess) return attr;
-  const unsigned grid = (unsigned)ceil_div(nrows, ROWS_PER_CTA);
-  chol_rows_kernel<T, B><<<grid, ROWS_PER_CTA, smem, st>>>(W, ld, row0, nrows, j0, bw, status);
-  count_launch();
-  return cudaGetLastError();
-}
-
-template <typename T, int B>
 cudaError_t lu_rows_b(T *W, int64_t ld, int64_t row0, int64_t nrows, int64_t j0, int bw,
                       int *status, cudaStream_t st) {
   constexpr size_t smem = rows_smem_bytes<T, B>();
@@ -619,15 +505,6 @@ cudaError_t lu_rows_b(T *W, int64_t ld, int64_t row0, int64_t nrows, int64_t j0,
   lu_rows_kernel<T, B><<<grid, ROWS_PER_CTA, smem, st>>>(W, ld, row0, nrows, j0, bw, status);
   count_launch();
   return cudaGetLastError();
-}
-
-template <typename T>
-cudaError_t launch_chol_rows(T *W, int64_t ld, int64_t row0, int64_t nrows, int64_t j0, int bw,
-                             int *status, cudaStream_t st) {
-  if (nrows <= 0) return cudaSuccess;
-  if (bw < 1 || bw > 64) return cudaErrorInvalidValue;
-  if (bw <= 32) return chol_rows_b<T, 32>(W, ld, row0, nrows, j0, bw, status, st);
-  return chol_rows_b<T, 64>(W, ld, row0, nrows, j0, bw, status, st);
 }
 
 template <typename T, int MODE, int ROWS>
@@ -699,11 +576,6 @@ cudaError_t launch_copy_matrix(const Tin *A, int64_t lda, Tout *W, int64_t ldw, 
   return cudaGetLastError();
 }
 
-template cudaError_t launch_chol_diag<double, double>(double *, int64_t, int64_t, int, int *, cudaStream_t);
-template cudaError_t launch_chol_diag<float, float>(float *, int64_t, int64_t, int, int *, cudaStream_t);
-template cudaError_t launch_chol_diag<float, double>(float *, int64_t, int64_t, int, int *, cudaStream_t);
-template cudaError_t launch_chol_rows<double>(double *, int64_t, int64_t, int64_t, int64_t, int, int *, cudaStream_t);
-template cudaError_t launch_chol_rows<float>(float *, int64_t, int64_t, int64_t, int64_t, int, int *, cudaStream_t);
 template cudaError_t launch_chol_panel<double>(double *, int64_t, int64_t, int, int64_t, int *, unsigned long long *, cudaStream_t);
 template cudaError_t launch_chol_panel<float>(float *, int64_t, int64_t, int, int64_t, int *, unsigned long long *, cudaStream_t);
 template cudaError_t launch_lu_diag<double, double>(double *, int64_t, int64_t, int, int *, cudaStream_t);
