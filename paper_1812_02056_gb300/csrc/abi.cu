@@ -874,18 +874,26 @@ template <typename Tf>
 struct SolvePlan {
   Tf *dinv_lo = nullptr;  // inverses of the diagonal blocks of L
   Tf *dinv_up = nullptr;  // of L^T (Cholesky) or of the unit U (LU)
+  Tf *m_lo = nullptr;     // coupling blocks of the two sweeps
+  Tf *m_up = nullptr;
 };
 
 template <typename Tf>
 gb_status solve_prepare(gb_handle *h, bool is_lu, const Tf *F, int64_t ldf, int64_t n,
                         SolvePlan<Tf> &p, cudaStream_t st) {
   const size_t one = trsm_inv_bytes(n, sizeof(Tf));
-  gb_status r = ws_reserve(h, WS_DINV, 2 * one, st);
+  gb_status r = ws_reserve(h, WS_DINV, 4 * one, st);
   if (r != GB_OK) return r;
-  p.dinv_lo = (Tf *)h->ws[WS_DINV].ptr;
-  p.dinv_up = (Tf *)((char *)h->ws[WS_DINV].ptr + one);
+  char *base = (char *)h->ws[WS_DINV].ptr;
+  p.dinv_lo = (Tf *)base;
+  p.dinv_up = (Tf *)(base + one);
+  p.m_lo = (Tf *)(base + 2 * one);
+  p.m_up = (Tf *)(base + 3 * one);
+  const int up = is_lu ? TRSM_UNIT_UPPER : TRSM_LOWER_T;
   GB_CUDA_TRY(launch_diag_inv<Tf>(F, ldf, n, TRSM_LOWER, p.dinv_lo, st));
-  GB_CUDA_TRY(launch_diag_inv<Tf>(F, ldf, n, is_lu ? TRSM_UNIT_UPPER : TRSM_LOWER_T, p.dinv_up, st));
+  GB_CUDA_TRY(launch_diag_inv<Tf>(F, ldf, n, up, p.dinv_up, st));
+  GB_CUDA_TRY(launch_coupling<Tf>(F, ldf, p.dinv_lo, n, TRSM_LOWER, p.m_lo, st));
+  GB_CUDA_TRY(launch_coupling<Tf>(F, ldf, p.dinv_up, n, up, p.m_up, st));
   return GB_OK;
 }
 
@@ -894,11 +902,11 @@ gb_status tri_solve(gb_handle *h, bool is_lu, const Tf *F, int64_t ldf, const So
                     double *X, int64_t ldx, int64_t n, int64_t nrhs, cudaStream_t st) {
   unsigned e1 = ++h->sync_epoch;
   if (e1 == 0) e1 = ++h->sync_epoch;
-  GB_CUDA_TRY((launch_trsm_inv<Tf>(F, ldf, p.dinv_lo, X, ldx, n, nrhs, TRSM_LOWER, h->d_sync, e1,
-                                   h->d_err, h->spin_limit, st)));
+  GB_CUDA_TRY((launch_trsm_inv<Tf>(F, ldf, p.dinv_lo, p.m_lo, X, ldx, n, nrhs, TRSM_LOWER,
+                                   h->d_sync, e1, h->d_err, h->spin_limit, st)));
   unsigned e2 = ++h->sync_epoch;
   if (e2 == 0) e2 = ++h->sync_epoch;
-  GB_CUDA_TRY((launch_trsm_inv<Tf>(F, ldf, p.dinv_up, X, ldx, n, nrhs,
+  GB_CUDA_TRY((launch_trsm_inv<Tf>(F, ldf, p.dinv_up, p.m_up, X, ldx, n, nrhs,
                                    is_lu ? TRSM_UNIT_UPPER : TRSM_LOWER_T, h->d_sync, e2, h->d_err,
                                    h->spin_limit, st)));
   return GB_OK;

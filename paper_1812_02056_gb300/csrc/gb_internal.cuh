@@ -207,15 +207,20 @@ cudaError_t launch_trsm(const Tf *F, int64_t ldf, double *B, int64_t ldb, int64_
                         int64_t spin_limit, cudaStream_t st);
 enum { TRSM_LOWER = 0, TRSM_LOWER_T = 1, TRSM_UNIT_UPPER = 2 };
 // Solve through inverted diagonal blocks: launch_diag_inv fills Dinv
-// (trsm_inv_bytes), then launch_trsm_inv solves in place like launch_trsm.
+// (trsm_inv_bytes), launch_coupling the coupling blocks M (trsm_inv_bytes:
+// block p couples position p to position p - 1), then launch_trsm_inv
+// solves in place like launch_trsm.
 size_t trsm_inv_bytes(int64_t n, size_t esz);
 template <typename Tf>
 cudaError_t launch_diag_inv(const Tf *F, int64_t ldf, int64_t n, int kind, Tf *Dinv,
                             cudaStream_t st);
 template <typename Tf>
-cudaError_t launch_trsm_inv(const Tf *F, int64_t ldf, const Tf *Dinv, double *B, int64_t ldb,
-                            int64_t n, int64_t nrhs, int kind, int *sync, unsigned epoch, int *err,
-                            int64_t spin_limit, cudaStream_t st);
+cudaError_t launch_coupling(const Tf *F, int64_t ldf, const Tf *Dinv, int64_t n, int kind, Tf *M,
+                            cudaStream_t st);
+template <typename Tf>
+cudaError_t launch_trsm_inv(const Tf *F, int64_t ldf, const Tf *Dinv, const Tf *M, double *B,
+                            int64_t ldb, int64_t n, int64_t nrhs, int kind, int *sync,
+                            unsigned epoch, int *err, int64_t spin_limit, cudaStream_t st);
 // r = b - A x in FP64 (and the norms of r, x, b per column when `norms`);
 // small orders split the columns of A into slices whose partial products go
 // to `work` (residual_work_bytes; without it, one slice).

@@ -197,6 +197,40 @@ __global__ void __launch_bounds__(inv_block<Tc>())
   for (int i = 0; i < TB; ++i) D[i * TB + j] = (i < rows && j < rows) ? Ys[i][j] : Tc(0);
 }
 
+// Coupling blocks of the solve: for position p >= 1 (block b, previous
+// position's block bp), M_p = Dinv[b] op(F)[b rows, bp columns], so that
+// X_b = Dinv[b] (B_b - sum over earlier positions) - M_p X_bp puts a single
+// BS x BS product on the dependence chain.
+template <typename Tc>
+__global__ void __launch_bounds__(TRSM_THREADS)
+    coupling_kernel(const Tc *__restrict__ F, int64_t ldf, const Tc *__restrict__ Dinv, int64_t n,
+                    int kind, Tc *__restrict__ M) {
+  constexpr int BS = inv_block<Tc>();
+  __shared__ Tc Ds[BS][BS + 1];
+  __shared__ Tc Os[BS][BS + 1];
+  const int nb = (int)((n + BS - 1) / BS);
+  const int p = blockIdx.x + 1;
+  if (p >= nb) return;
+  const bool fwd = (kind == TRSM_LOWER);
+  const int b = fwd ? p : nb - 1 - p, bp = fwd ? p - 1 : nb - p;
+  const int64_t r0 = (int64_t)b * BS, c0 = (int64_t)bp * BS;
+  const int rows = (int)min64(BS, n - r0), cw = (int)min64(BS, n - c0);
+  const Tc *D = Dinv + (int64_t)b * BS * BS;
+  for (int idx = threadIdx.x; idx < BS * BS; idx += TRSM_THREADS) {
+    const int i = idx / BS, k = idx % BS;
+    Ds[i][k] = D[idx];
+    Os[i][k] = (i < rows && k < cw) ? op_elem(F, ldf, kind, r0 + i, c0 + k) : Tc(0);
+  }
+  __syncthreads();
+  Tc *Mo = M + (int64_t)p * BS * BS;
+  for (int idx = threadIdx.x; idx < BS * BS; idx += TRSM_THREADS) {
+    const int i = idx / BS, k = idx % BS;
+    Tc v = Tc(0);
+    for (int j = 0; j < BS; ++j) v = v + Ds[i][j] * Os[j][k];
+    Mo[idx] = v;
+  }
+}
+
 // Solve with inverted diagonal blocks.  CTAs take block rows (BS rows) in
 // dependence order from a ticket (position t: block t forward, block
 // nb - 1 - t backward).  `progress` counts the finished positions; blocks
@@ -224,9 +258,9 @@ struct TrsmCfg {
 
 template <typename Tf, typename Tc>
 __global__ void __launch_bounds__(TRSM_THREADS)
-    trsm_inv_kernel(const Tf *__restrict__ F, int64_t ldf, const Tc *__restrict__ Dinv, double *B,
-                    int64_t ldb, int64_t n, int64_t nrhs, int kind, int *ticket, int *progress,
-                    int *err, long long wait_ns) {
+    trsm_inv_kernel(const Tf *__restrict__ F, int64_t ldf, const Tc *__restrict__ Dinv,
+                    const Tc *__restrict__ Mc, double *B, int64_t ldb, int64_t n, int64_t nrhs,
+                    int kind, int *ticket, int *progress, int *err, long long wait_ns) {
   using C = TrsmCfg<Tc>;
   constexpr int BS = C::BS, KC = C::KC, NRC = C::NRC, OPT = C::OPT;
   static_assert(KC % BS == 0 && C::TPR * OPT == NRC, "layout");
@@ -262,17 +296,50 @@ __global__ void __launch_bounds__(TRSM_THREADS)
     c1 = min64((b0 + w) * BS, n);
   };
 
+  // every thread: wait until position p is finished; the number of finished
+  // positions, or -1 once a wait has expired (here or in another CTA)
+  auto wait_pos = [&](int p) {
+    if (tid == 0) {
+      int spins = 0, avail = ld_acquire(progress);
+      const long long t0 = (long long)globaltimer_ns();
+      while (avail <= p) {
+        if ((++spins & 255) == 0) {
+          if (ld_acquire(err) & DEV_ERR_TIMEOUT) {
+            s_abort = 1;
+            break;
+          }
+          if ((long long)globaltimer_ns() - t0 > wait_ns) {
+            atomicOr(err, DEV_ERR_TIMEOUT);
+            s_abort = 1;
+            break;
+          }
+        }
+        avail = ld_acquire(progress);
+      }
+      s_avail = avail;
+    }
+    __syncthreads();
+    return s_abort ? -1 : s_avail;
+  };
+
+  // positions 0 .. t - 2 go through the chunks; the previous position t - 1
+  // enters through the coupling block M_t = Dinv[b] op(F)[b, previous block]
+  const int tmain = t > 0 ? t - 1 : 0;
   for (int64_t rc0 = 0; rc0 < nrhs; rc0 += NRC) {
     const int cols = (int)min64(NRC, nrhs - rc0);
+    if (rc0 > 0 && t > 0) {  // the previous group left M_t in Ds
+      const Tc *D = Dinv + (int64_t)ib * BS * BS;
+      for (int idx = tid; idx < BS * BS; idx += TRSM_THREADS) Ds[(idx / BS) * (BS + 1) + idx % BS] = D[idx];
+    }
     Tc acc[OPT];
 #pragma unroll
     for (int q = 0; q < OPT; ++q)
       acc[q] = (tr < rows && tc + q < cols) ? (Tc)B[(r0 + tr) * ldb + rc0 + tc + q] : Tc(0);
     int done = 0;
-    while (done < t) {
+    while (done < tmain) {
       // op(F) for the next chunk of positions, loaded once, before waiting
       // for any of its X
-      const int wmax = min(KC / BS, t - done);
+      const int wmax = min(KC / BS, tmain - done);
       int64_t f0, f1;
       col_range(done, wmax, f0, f1);
       const int fw = (int)(f1 - f0);
@@ -283,29 +350,10 @@ __global__ void __launch_bounds__(TRSM_THREADS)
       int applied = 0;  // positions of this chunk applied so far
       while (applied < wmax) {
         const int p0 = done + applied;
-        if (tid == 0) {
-          int spins = 0, avail = ld_acquire(progress);
-          const long long t0 = (long long)globaltimer_ns();
-          while (avail <= p0) {
-            if ((++spins & 255) == 0) {
-              if (ld_acquire(err) & DEV_ERR_TIMEOUT) {
-                s_abort = 1;
-                break;
-              }
-              if ((long long)globaltimer_ns() - t0 > wait_ns) {
-                atomicOr(err, DEV_ERR_TIMEOUT);
-                s_abort = 1;
-                break;
-              }
-            }
-            avail = ld_acquire(progress);
-          }
-          s_avail = avail;
-        }
-        __syncthreads();
-        if (s_abort) return;
+        const int avail = wait_pos(p0);
+        if (avail < 0) return;
         // the finished positions p0 .. p0 + w - 1 of this chunk
-        const int w = min(wmax - applied, s_avail - p0);
+        const int w = min(wmax - applied, avail - p0);
         int64_t c0, c1;
         col_range(p0, w, c0, c1);
         const int kw = (int)(c1 - c0);
@@ -336,7 +384,7 @@ __global__ void __launch_bounds__(TRSM_THREADS)
       }
       done += wmax;
     }
-    // X_b = Dinv[b] * acc
+    // Y = Dinv[b] * acc, before the previous position is waited for
 #pragma unroll
     for (int q = 0; q < OPT; ++q) Xs[tr * (NRC + 1) + tc + q] = acc[q];
     __syncthreads();
@@ -348,6 +396,27 @@ __global__ void __launch_bounds__(TRSM_THREADS)
       const Tc d = Ds[tr * (BS + 1) + k];
 #pragma unroll
       for (int q = 0; q < OPT; ++q) out[q] = out[q] + d * Xs[k * (NRC + 1) + tc + q];
+    }
+    if (t > 0) {
+      // X_b = Y - M_t X_{t-1}: one product on the dependence chain
+      __syncthreads();  // Ds and Xs are read
+      const Tc *M = Mc + (int64_t)t * BS * BS;
+      for (int idx = tid; idx < BS * BS; idx += TRSM_THREADS) Ds[(idx / BS) * (BS + 1) + idx % BS] = M[idx];
+      if (wait_pos(t - 1) < 0) return;
+      int64_t c0, c1;
+      col_range(t - 1, 1, c0, c1);
+      const int kw = (int)(c1 - c0);
+      for (int idx = tid; idx < kw * NRC; idx += TRSM_THREADS) {
+        const int k = idx / NRC, c = idx % NRC;
+        Xs[k * (NRC + 1) + c] = c < cols ? (Tc)__ldcg(&B[(c0 + k) * ldb + rc0 + c]) : Tc(0);
+      }
+      __syncthreads();
+#pragma unroll 8
+      for (int k = 0; k < kw; ++k) {
+        const Tc m = Ds[tr * (BS + 1) + k];
+#pragma unroll
+        for (int q = 0; q < OPT; ++q) out[q] = out[q] - m * Xs[k * (NRC + 1) + tc + q];
+      }
     }
 #pragma unroll
     for (int q = 0; q < OPT; ++q)
@@ -581,9 +650,19 @@ cudaError_t launch_diag_inv(const Tf *F, int64_t ldf, int64_t n, int kind, Tf *D
 }
 
 template <typename Tf>
-cudaError_t launch_trsm_inv(const Tf *F, int64_t ldf, const Tf *Dinv, double *B, int64_t ldb,
-                            int64_t n, int64_t nrhs, int kind, int *sync, unsigned epoch, int *err,
-                            int64_t spin_limit, cudaStream_t st) {
+cudaError_t launch_coupling(const Tf *F, int64_t ldf, const Tf *Dinv, int64_t n, int kind, Tf *M,
+                            cudaStream_t st) {
+  const int64_t bs = inv_block<Tf>(), nb = (n + bs - 1) / bs;
+  if (nb <= 1) return cudaSuccess;
+  coupling_kernel<Tf><<<(unsigned)(nb - 1), TRSM_THREADS, 0, st>>>(F, ldf, Dinv, n, kind, M);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <typename Tf>
+cudaError_t launch_trsm_inv(const Tf *F, int64_t ldf, const Tf *Dinv, const Tf *M, double *B,
+                            int64_t ldb, int64_t n, int64_t nrhs, int kind, int *sync,
+                            unsigned epoch, int *err, int64_t spin_limit, cudaStream_t st) {
   if (n <= 0 || nrhs <= 0) return cudaSuccess;
   using C = TrsmCfg<Tf>;
   const int64_t nb = (n + C::BS - 1) / C::BS;
@@ -595,7 +674,7 @@ cudaError_t launch_trsm_inv(const Tf *F, int64_t ldf, const Tf *Dinv, double *B,
   if (e != cudaSuccess) return e;
   const long long wait_ns = (long long)spin_limit * 100LL;
   trsm_inv_kernel<Tf, Tf><<<(unsigned)nb, TRSM_THREADS, C::SMEM, st>>>(
-      F, ldf, Dinv, B, ldb, n, nrhs, kind, sync, sync + 1, err, wait_ns);
+      F, ldf, Dinv, M, B, ldb, n, nrhs, kind, sync, sync + 1, err, wait_ns);
   count_launch();
   return cudaGetLastError();
 }
@@ -712,12 +791,16 @@ template cudaError_t launch_diag_inv<double>(const double *, int64_t, int64_t, i
                                              cudaStream_t);
 template cudaError_t launch_diag_inv<float>(const float *, int64_t, int64_t, int, float *,
                                             cudaStream_t);
-template cudaError_t launch_trsm_inv<double>(const double *, int64_t, const double *, double *,
-                                             int64_t, int64_t, int64_t, int, int *, unsigned, int *,
-                                             int64_t, cudaStream_t);
-template cudaError_t launch_trsm_inv<float>(const float *, int64_t, const float *, double *, int64_t,
-                                            int64_t, int64_t, int, int *, unsigned, int *, int64_t,
-                                            cudaStream_t);
+template cudaError_t launch_coupling<double>(const double *, int64_t, const double *, int64_t, int,
+                                             double *, cudaStream_t);
+template cudaError_t launch_coupling<float>(const float *, int64_t, const float *, int64_t, int,
+                                            float *, cudaStream_t);
+template cudaError_t launch_trsm_inv<double>(const double *, int64_t, const double *, const double *,
+                                             double *, int64_t, int64_t, int64_t, int, int *,
+                                             unsigned, int *, int64_t, cudaStream_t);
+template cudaError_t launch_trsm_inv<float>(const float *, int64_t, const float *, const float *,
+                                            double *, int64_t, int64_t, int64_t, int, int *, unsigned,
+                                            int *, int64_t, cudaStream_t);
 template cudaError_t launch_backward_error<double>(int, const double *, int64_t, const double *,
                                                    int64_t, int64_t, double *, cudaStream_t);
 template cudaError_t launch_backward_error<float>(int, const double *, int64_t, const float *,
