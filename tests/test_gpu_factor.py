@@ -180,6 +180,24 @@ def test_chol_breakdown_reports_column(h):
     assert info > 0
 
 
+@pytest.mark.parametrize("dtype", ["f32", "mix_bf16", "mix_bf16x3"])
+def test_chol_breakdown_reports_column_fp32_working_matrix(h, dtype):
+    """The FP32 and mixed paths (one warp finishes each 16-column chunk of
+    the diagonal block) report the first non-positive pivot, inside and
+    across chunks and inner blocks, and a NaN anywhere."""
+    n = 300
+    for k in (0, 15, 16, 137, 299):
+        A = I.spd_gram(n, 1)
+        A[k, k] = -1e7
+        for s in [16, 64, 100, 300]:
+            _, info = _chol(h, A, s, dtype)
+            assert info == k + 1, (k, s)
+    B = I.spd_gram(40, 2)
+    B[25, 3] = B[3, 25] = np.nan
+    _, info = _chol(h, B, 8, dtype)
+    assert info > 0
+
+
 def test_chol_empty(h):
     from paper_1812_02056_gb300 import binding
     info = np.ones(1, dtype=np.int32)
