@@ -235,13 +235,15 @@ __global__ void __launch_bounds__(TRSM_THREADS)
 // dependence order from a ticket (position t: block t forward, block
 // nb - 1 - t backward).  `progress` counts the finished positions; blocks
 // finish in order, so progress = p means positions 0 .. p - 1 are solved.  A
-// CTA walks its row panel in chunks of up to KC columns: the op(F) part of a
-// chunk is loaded once, before any wait (it does not depend on X), as is the
-// CTA's Dinv block; then each wait applies as many of the chunk's blocks as
-// are finished when it looks (all of them far behind the wavefront, one per
-// wait when caught up), so a CTA that trails the wavefront re-reads neither
-// op(F) nor X.  Then X_b = Dinv[b] (B_b -
-// contributions), stored, and published.  Every wait is bounded by a
+// CTA walks its row panel, except the previous position's block, in chunks
+// of up to KC columns: the op(F) part of a chunk is loaded once, before any
+// wait (it does not depend on X), as is the CTA's Dinv block; then each wait
+// applies as many of the chunk's blocks as are finished when it looks (all
+// of them far behind the wavefront, one per wait when caught up), so a CTA
+// that trails the wavefront re-reads neither op(F) nor X.  Then
+// Y = Dinv[b] (B_b - contributions) before the previous position is waited
+// for, and after it X_b = Y - M_t X_prev with the coupling block M_t
+// (coupling_kernel), stored and published.  Every wait is bounded by a
 // %globaltimer deadline; on expiry the kernel raises DEV_ERR_TIMEOUT in the
 // error word, every other waiter sees it and returns, and the host reports
 // GB_ERR_TIMEOUT.
