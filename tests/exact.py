@@ -78,3 +78,57 @@ def cholesky_exact_decimal(A, digits=50):
             num = det(_sub(A, list(range(j)) + [i], range(j + 1)))
             L[i][j] = (Decimal(num.numerator) / Decimal(num.denominator)) / root
     return L
+
+
+def _fr(M):
+    """Exact binary values of a float matrix (numpy array or nested lists)."""
+    return [[Fraction(float(x)) for x in row] for row in M]
+
+
+def frob_ratio(D, A, digits=40):
+    """``||D||_F / ||A||_F`` (``||D||_F`` when ``A`` is None) for Fraction
+    matrices, with the square root of the exact rational taken in decimal."""
+    getcontext().prec = digits
+    num = sum(x * x for row in D for x in row)
+    den = Fraction(1) if A is None else sum(x * x for row in A for x in row)
+    if den == 0:
+        return 0.0
+    q = num / den
+    return float((Decimal(q.numerator) / Decimal(q.denominator)).sqrt())
+
+
+def chol_residual(A, L):
+    """``A - L L^T`` exactly, with ``L`` taken as its lower triangle."""
+    A, L = _fr(A), _fr(L)
+    n = len(A)
+    return [[A[i][j] - sum(L[i][k] * L[j][k] for k in range(min(i, j) + 1)) for j in range(n)]
+            for i in range(n)], A
+
+
+def lu_residual(A, L, U):
+    """``A - L U`` exactly, ``L`` its lower triangle, ``U`` its strict upper
+    triangle plus the unit diagonal (whatever ``U`` stores on and below it)."""
+    A, L, U = _fr(A), _fr(L), _fr(U)
+    n = len(A)
+
+    def u(k, j):
+        return Fraction(1) if k == j else U[k][j]
+
+    return [[A[i][j] - sum(L[i][k] * u(k, j) for k in range(min(i, j) + 1)) for j in range(n)]
+            for i in range(n)], A
+
+
+def qr_residual(A, Q, R):
+    """``A - Q R`` exactly, with all entries of ``Q`` and ``R`` as given."""
+    A, Q, R = _fr(A), _fr(Q), _fr(R)
+    n = len(A)
+    return [[A[i][j] - sum(Q[i][k] * R[k][j] for k in range(n)) for j in range(n)]
+            for i in range(n)], A
+
+
+def orthogonality_defect(Q):
+    """``Q^T Q - I`` exactly."""
+    Q = _fr(Q)
+    n = len(Q)
+    return [[sum(Q[k][i] * Q[k][j] for k in range(n)) - (1 if i == j else 0) for j in range(n)]
+            for i in range(n)]

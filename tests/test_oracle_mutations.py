@@ -3,7 +3,8 @@
 Each case plants one mistake (a dropped term, a wrong sign, a transposed
 operand, a wrong index or range, a missing step) in a copy of oracle.c,
 compiles the copy with the same flags, and checks that at least one pin --
-Pascal closed form, rational brute force, LAPACK, step agreement -- fails
+Pascal closed form, rational brute force, LAPACK, step agreement, the error
+measures against their exact values -- fails
 with it.  The planted copies live in a temporary directory; the committed
 oracle is untouched.
 """
@@ -16,7 +17,7 @@ import pytest
 
 import oracle
 from paper_1812_02056_gb300 import inputs as I
-from tests import exact
+from tests import exact, test_oracle_error_pins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "oracle.c")
 
@@ -59,6 +60,42 @@ MUTATIONS = {
     "qr_r_transposed": ("const double *qi = Qc + i * n;", "const double *qi = Qc + i;"),
     "lu_update_first_term_dropped": ("for (int64_t k = z; k < c; ++k) {\n              const double lik = L[i * ldl + k];\n              for (int64_t j = c; j < n; ++j) srow[j]",
                                      "for (int64_t k = z + 1; k < c; ++k) {\n              const double lik = L[i * ldl + k];\n              for (int64_t j = c; j < n; ++j) srow[j]"),
+    # error measures (the definitions that judge every factor)
+    "be_chol_no_sqrt": ("sqrtl(num / den) : 0.0;\n}\n\ndouble orc_lu_backward_error",
+                        "(num / den) : 0.0;\n}\n\ndouble orc_lu_backward_error"),
+    "be_chol_no_den": ("sqrtl(num / den) : 0.0;\n}\n\ndouble orc_lu_backward_error",
+                       "sqrtl(num) : 0.0;\n}\n\ndouble orc_lu_backward_error"),
+    "be_chol_lower_triangle_only": (
+        "for (int64_t j = 0; j < n; ++j) {\n      long double p = 0.0L;\n      const int64_t kmax = i < j ? i : j;\n      for (int64_t k = 0; k <= kmax; ++k)\n        p +=",
+        "for (int64_t j = 0; j <= i; ++j) {\n      long double p = 0.0L;\n      const int64_t kmax = i < j ? i : j;\n      for (int64_t k = 0; k <= kmax; ++k)\n        p +="),
+    "be_chol_diag_term_dropped": (
+        "for (int64_t k = 0; k <= kmax; ++k)\n        p += (long double)L[i * ldl + k] * (long double)L[j * ldl + k];",
+        "for (int64_t k = 0; k < kmax; ++k)\n        p += (long double)L[i * ldl + k] * (long double)L[j * ldl + k];"),
+    "be_chol_reads_upper": (
+        "for (int64_t k = 0; k <= kmax; ++k)\n        p += (long double)L[i * ldl + k] * (long double)L[j * ldl + k];",
+        "for (int64_t k = 0; k < n; ++k)\n        p += (long double)L[i * ldl + k] * (long double)L[j * ldl + k];"),
+    "be_lu_stored_diag_used": ("const long double u = (k == j) ? 1.0L : (long double)U[k * ldu + j];",
+                               "const long double u = (long double)U[k * ldu + j];"),
+    "be_lu_transposed": ("p += (long double)L[i * ldl + k] * u;", "p += (long double)L[k * ldl + i] * u;"),
+    "be_lu_no_sqrt": ("sqrtl(num / den) : 0.0;\n}\n\n/* ||A - Q R||_F",
+                      "(num / den) : 0.0;\n}\n\n/* ||A - Q R||_F"),
+    "be_lu_no_den": ("sqrtl(num / den) : 0.0;\n}\n\n/* ||A - Q R||_F",
+                     "sqrtl(num) : 0.0;\n}\n\n/* ||A - Q R||_F"),
+    "be_qr_no_sqrt": ("sqrtl(num / den) : 0.0;\n}\n\n/* ||Q^T Q - I||_F",
+                      "(num / den) : 0.0;\n}\n\n/* ||Q^T Q - I||_F"),
+    "be_qr_no_den": ("sqrtl(num / den) : 0.0;\n}\n\n/* ||Q^T Q - I||_F",
+                     "sqrtl(num) : 0.0;\n}\n\n/* ||Q^T Q - I||_F"),
+    "be_qr_transposed": ("acc += (long double)Q[i * ldq + k] * (long double)R[k * ldr + j];",
+                         "acc += (long double)Q[k * ldq + i] * (long double)R[k * ldr + j];"),
+    "be_qr_upper_r_only": ("acc += (long double)Q[i * ldq + k] * (long double)R[k * ldr + j];",
+                           "if (k <= j) acc += (long double)Q[i * ldq + k] * (long double)R[k * ldr + j];"),
+    "orth_no_sqrt": ("return (double)sqrtl(num);", "return (double)num;"),
+    "orth_no_identity": ("const long double d = acc - (i == j ? 1.0L : 0.0L);",
+                         "const long double d = acc;"),
+    "orth_transposed_operand": ("acc += (long double)Q[k * ldq + i] * (long double)Q[k * ldq + j];",
+                                "acc += (long double)Q[k * ldq + i] * (long double)Q[j * ldq + k];"),
+    "orth_upper_only": ("const long double d = acc - (i == j ? 1.0L : 0.0L);\n      num += d * d;",
+                        "const long double d = acc - (i == j ? 1.0L : 0.0L);\n      if (j >= i) num += d * d;"),
 }
 
 
@@ -131,7 +168,8 @@ def _pins_pass() -> bool:
         Qn, Rn, _ = oracle.qr(D, 40)
         if not (np.array_equal(Q1, Qn) and np.array_equal(R1, Rn)):
             return False
-        return True
+        # the error measures against their exact values
+        return test_oracle_error_pins.check_error_measures()
     except Exception:
         return False
 
