@@ -1,11 +1,12 @@
 // gb_chol_solve_noalloc: forward and back substitution with a Cholesky
 // factor for callers that cannot allocate device memory.
 //
-// Some callers cannot call cudaMalloc: code that runs while a stream is
-// being captured into a CUDA graph (an allocation there is not captured, and
-// cudaMalloc may synchronize the device), code inside a pool-budgeted or
-// real-time section where allocation is forbidden, or plugins that must not
-// touch the allocator at all.  The regular gb_chol_solve needs a handle, and
+// Some callers cannot call cudaMalloc: code that runs inside a memory budget
+// it does not own (a host application that hands this library a fixed
+// arena, or a pool that is already fully reserved), a latency-critical
+// section where an allocation (which may synchronize the whole device) is
+// not allowed, or a plugin loaded into another program that must not touch
+// that program's allocator.  The regular gb_chol_solve needs a handle, and
 // gb_create allocates the handle's scratch words (the ticket and per-block
 // flags that order the single-launch triangular solve).  This entry point
 // takes no handle: its scratch is the file-scope array below, which every
@@ -13,7 +14,10 @@
 //
 // Properties:
 //  * at most NOALLOC_MAX_N rows (NOALLOC_BLOCKS blocks of 32 rows);
-//  * device pointers only (staging host buffers would allocate);
+//  * device pointers on the current device only (staging host buffers would
+//    allocate; another GPU's memory is rejected);
+//  * the call waits for `stream`: it reads the breakdown word before the
+//    substitutions and the error word after them on the host;
 //  * every call shares the one array and it keeps the last call's contents:
 //    the ticket, the error word and the breakdown word are cleared by each
 //    call, and the per-block flags are compared against a fresh epoch, so
@@ -21,8 +25,9 @@
 //  * calls that overlap on the GPU (two streams, one device) race on the
 //    array and must not be issued;
 //  * the first call on a device looks up the array's device address
-//    (cudaGetSymbolAddress, with that device current); make that first call
-//    before any stream capture.
+//    (cudaGetSymbolAddress, with that device current): that set-up happens
+//    once per device, and the first call should come before any stream
+//    capture.
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -57,13 +62,16 @@ unsigned next_epoch(DeviceScratch &d) {
   return e;
 }
 
-bool is_device_pointer(const void *p) {
+// Device (or managed) memory that the kernels on device `dev` can address:
+// plain device memory must belong to `dev` itself.
+bool is_device_pointer(const void *p, int dev) {
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  if (at.type == cudaMemoryTypeManaged) return true;
+  return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 template <typename Tf>
@@ -111,11 +119,11 @@ extern "C" gb_status gb_chol_solve_noalloc(int64_t n, int64_t nrhs, gb_dtype fac
     return GB_ERR_UNSUPPORTED;
   }
   if (n == 0 || nrhs == 0) return GB_OK;
-  if (!is_device_pointer(L)) return -4;
-  if (!is_device_pointer(B)) return -6;
-  if (!is_device_pointer(X)) return -8;
   int dev = 0;
   GB_CUDA_TRY(cudaGetDevice(&dev));
+  if (!is_device_pointer(L, dev)) return -4;
+  if (!is_device_pointer(B, dev)) return -6;
+  if (!is_device_pointer(X, dev)) return -8;
   if (dev < 0 || dev >= MAX_DEVICES) return GB_ERR_UNSUPPORTED;
   DeviceScratch &d = g_scratch[dev];
   // once per device, with that device current: the array's device address
