@@ -158,7 +158,7 @@ typedef enum gb_option {
                                inner block one at a time (default 16, range
                                1..256; capped by s and by the panel's shared
                                memory, 200 KiB per CTA for ceil(n/8) rows).  */
-  GB_OPT_LEFT_LOOKING = 10  /* 1: gb_chol_factor with GB_MIX_BF16 / GB_MIX_F16
+  GB_OPT_LEFT_LOOKING = 10, /* 1: gb_chol_factor with GB_MIX_BF16 / GB_MIX_F16
                                (tensor-core update on, s a multiple of 64,
                                s < n, n a multiple of 8) accumulates the
                                update of each s-block column from all earlier
@@ -168,6 +168,16 @@ typedef enum gb_option {
                                every s columns: the same sums, grouped by
                                tile; FP32 traffic of the working matrix once
                                per block column.  Default 0.                 */
+  GB_OPT_TEST_WITHHOLD = 11 /* failure-detection test hook, 0 (default) off:
+                               v >= 1 makes block v - 1 (in sweep order) of
+                               the forward triangular sweep of gb_chol_solve
+                               and gb_lu_solve skip publishing its
+                               completion, so the block after it waits until
+                               GB_OPT_SPIN_LIMIT runs out, raises the timeout
+                               word and returns; the call then reports
+                               GB_ERR_TIMEOUT and clears the word.  Nothing
+                               faults or hangs; the next call on the handle
+                               starts from fresh sync words.                  */
 } gb_option;
 
 gb_status gb_set_option(gb_handle *h, gb_option opt, int64_t value);
@@ -327,24 +337,28 @@ gb_status gb_rank_update(gb_handle *h, gb_dtype dt, int lower, int y_is_kxn, int
  * allocate device memory.  The paper has no counterpart: it is a plain
  * solve (no refinement) that needs no handle.
  *
- * Who needs it: code that runs while a stream is being captured into a CUDA
- * graph, inside a budgeted memory pool or a real-time section, or in a
- * plugin that must not call cudaMalloc -- gb_create allocates a handle's
- * scratch, this call does not.  Its scratch (the ticket and per-block flags
- * that order the single-launch solve, an error word and a breakdown word)
- * is a file-scope __device__ array that every GPU loading the library holds
- * until exit.
+ * Who needs it: callers that may not call cudaMalloc -- code working inside
+ * a memory budget it does not own (a fixed arena handed over by the host
+ * application, a pool that is already fully reserved), a latency-critical
+ * section where an allocation (which can synchronize the device) is not
+ * allowed, or a plugin that must not touch its host program's allocator.
+ * gb_create allocates a handle's scratch; this call takes no handle.  Its
+ * scratch (the ticket and per-block flags that order the single-launch
+ * solve, an error word and a breakdown word) is a file-scope __device__
+ * array of 4099 ints that every GPU loading the library holds until exit.
  *
  *  n <= 131072 (larger n returns GB_ERR_UNSUPPORTED); nrhs >= 0.
- *  L, B, X     device pointers (host pointers are rejected: staging them
+ *  L, B, X     device pointers on the current device (host pointers and
+ *              other GPUs' memory are rejected with -4, -6 or -8: staging
  *              would allocate); layouts as gb_chol_solve; X may alias B.
  *  factor_dt   as gb_chol_solve (L double for GB_F64, float otherwise).
- * Runs on the current device and waits for `stream` (to read the breakdown
- * and error words).  Every call shares the one array and leaves its
- * contents behind; each call clears what must start at zero.  Calls that
- * overlap on the GPU race on the array: do not issue them concurrently.  The
- * first call on a device looks up the array's address with that device
- * current; make that first call before any stream capture.
+ * Runs on the current device and waits for `stream`: the breakdown and
+ * error words are read on the host.  Every call shares the one array and
+ * leaves its contents behind; each call clears what must start at zero.
+ * Calls that overlap on the GPU race on the array: do not issue them
+ * concurrently.  The first call on a device looks up the array's address
+ * with that device current (set-up done once per device); make that first
+ * call before any stream capture.
  * Returns GB_ERR_BREAKDOWN for a zero or non-finite diagonal entry of L and
  * GB_ERR_TIMEOUT if a bounded device wait expired.
  */
@@ -454,6 +468,31 @@ uint64_t gb_kernel_launches(void);
  * and report the achieved rate in flop/s (2 per FMA).  Synchronous.
  */
 gb_status gb_measure_fma_peak(gb_handle *h, gb_dtype dt, double *flops_per_s);
+
+/*
+ * gb_measure_peak -- the arithmetic rooflines of this GPU's pipes, measured
+ * by register- or shared-memory-only loops over every SM of the handle's
+ * device, in flop/s (no counterpart in the paper: they are the denominators
+ * of the roofline fractions the benchmark reports).  Synchronous.
+ *   GB_PEAK_DFMA, GB_PEAK_FFMA  as gb_measure_fma_peak (FP64 / FP32 FMA)
+ *   GB_PEAK_DMMA     f64 tensor MMA, mma.sync m8n8k4 (512 flop per warp op)
+ *   GB_PEAK_TC_BF16  tcgen05.mma kind::f16, BF16 operands, FP32 accumulate,
+ *                    M = 128, N = 256, one CTA per SM, operands in shared
+ *                    memory (no memory traffic): dense tensor-pipe peak
+ *   GB_PEAK_TC_F16   the same with FP16 operands
+ *   GB_PEAK_TC_TF32  tcgen05.mma kind::tf32 (K = 8 per instruction)
+ * Returns GB_ERR_UNSUPPORTED for the tcgen05 kinds on a device without
+ * them, and GB_ERR_TIMEOUT if the loop's bounded completion wait ran out.
+ */
+typedef enum gb_peak {
+  GB_PEAK_DFMA = 0,
+  GB_PEAK_FFMA = 1,
+  GB_PEAK_DMMA = 2,
+  GB_PEAK_TC_BF16 = 3,
+  GB_PEAK_TC_F16 = 4,
+  GB_PEAK_TC_TF32 = 5
+} gb_peak;
+gb_status gb_measure_peak(gb_handle *h, gb_peak kind, double *flops_per_s);
 
 /*
  * gb_backward_error -- ||A - L L^T||_F / ||A||_F (is_lu = 0) or
