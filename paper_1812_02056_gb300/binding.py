@@ -39,6 +39,8 @@ GB_OPT_LOOKAHEAD = 7
 GB_OPT_STRASSEN = 8
 GB_OPT_QR_INNER_STEP = 9
 GB_OPT_LEFT_LOOKING = 10
+GB_OPT_TEST_WITHHOLD = 11
+PEAKS = {"dfma": 0, "ffma": 1, "dmma": 2, "tc_bf16": 3, "tc_f16": 4, "tc_tf32": 5}
 
 
 class GbError(RuntimeError):
@@ -116,6 +118,7 @@ SIGNATURES = {
     "gb_profile_read": (_I32, [_P, _P]),
     "gb_kernel_launches": (ctypes.c_uint64, []),
     "gb_measure_fma_peak": (_I32, [_P, _I32, ctypes.POINTER(_D)]),
+    "gb_measure_peak": (_I32, [_P, _I32, ctypes.POINTER(_D)]),
 }
 
 PHASES = ["copy", "diag", "panel", "inner", "update"]
@@ -243,6 +246,12 @@ class Handle:
         p = into if into is not None else Profile()
         check(self.lib.gb_profile_read(self.h, ctypes.byref(p)), "gb_profile_read")
         return p
+
+    def measure_peak(self, kind: str) -> float:
+        """Measured pipe peak in flop/s: dfma, ffma, dmma, tc_bf16, tc_f16, tc_tf32."""
+        v = ctypes.c_double()
+        check(self.lib.gb_measure_peak(self.h, PEAKS[kind], ctypes.byref(v)), "gb_measure_peak")
+        return v.value
 
     def measure_fma_peak(self, dtype: str = "f64") -> float:
         v = ctypes.c_double()

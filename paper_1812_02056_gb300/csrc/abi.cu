@@ -903,7 +903,8 @@ gb_status tri_solve(gb_handle *h, bool is_lu, const Tf *F, int64_t ldf, const So
   unsigned e1 = ++h->sync_epoch;
   if (e1 == 0) e1 = ++h->sync_epoch;
   GB_CUDA_TRY((launch_trsm_inv<Tf>(F, ldf, p.dinv_lo, p.m_lo, X, ldx, n, nrhs, TRSM_LOWER,
-                                   h->d_sync, e1, h->d_err, h->spin_limit, st)));
+                                   h->d_sync, e1, h->d_err, h->spin_limit, st,
+                                   h->test_withhold - 1)));
   unsigned e2 = ++h->sync_epoch;
   if (e2 == 0) e2 = ++h->sync_epoch;
   GB_CUDA_TRY((launch_trsm_inv<Tf>(F, ldf, p.dinv_up, p.m_up, X, ldx, n, nrhs,
@@ -969,7 +970,13 @@ gb_status solve_common(bool is_lu, gb_handle *h, int64_t n, int64_t nrhs, const 
                                 h->sm_count, st));
     GB_CUDA_TRY(cudaMemcpyAsync(hn.data(), norms, sizeof(double) * hn.size(),
                                 cudaMemcpyDeviceToHost, st));
+    int errw = 0;  // an expired device wait ends the refinement at once
+    GB_CUDA_TRY(cudaMemcpyAsync(&errw, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     GB_CUDA_TRY(cudaStreamSynchronize(st));
+    if (errw) {
+      eta = INFINITY;
+      break;
+    }
     const double anorm = hn[0];
     eta = 0.0;
     for (int64_t c = 0; c < nrhs; ++c) {
@@ -1181,6 +1188,10 @@ gb_status gb_set_option(gb_handle *h, gb_option opt, int64_t v) {
       h->qr_inner = (int)v;
       return GB_OK;
     case GB_OPT_LEFT_LOOKING: h->left_looking = v ? 1 : 0; return GB_OK;
+    case GB_OPT_TEST_WITHHOLD:
+      if (v < 0 || v > (int64_t)1 << 30) return -3;
+      h->test_withhold = (int)v;
+      return GB_OK;
     default: return -2;
   }
 }
@@ -1199,6 +1210,7 @@ gb_status gb_get_option(gb_handle *h, gb_option opt, int64_t *v) {
     case GB_OPT_STRASSEN: *v = h->strassen; return GB_OK;
     case GB_OPT_QR_INNER_STEP: *v = h->qr_inner; return GB_OK;
     case GB_OPT_LEFT_LOOKING: *v = h->left_looking; return GB_OK;
+    case GB_OPT_TEST_WITHHOLD: *v = h->test_withhold; return GB_OK;
     default: return -2;
   }
 }

@@ -56,6 +56,7 @@ struct gb_handle {
   int tc_update = 2;
   int qr_inner = 16;          // inner step of the QR panel (GB_OPT_QR_INNER_STEP)
   int left_looking = 0;       // GB_OPT_LEFT_LOOKING
+  int test_withhold = 0;      // GB_OPT_TEST_WITHHOLD (test hook, 0 = off)
   // device copies of host buffers come from this pool, which keeps its
   // memory between calls (allocating and mapping it again each call costs
   // more than the copies)
@@ -199,6 +200,8 @@ cudaError_t launch_pack16(const float *X, int64_t ldx, int64_t rows, int64_t K, 
 size_t tc_pack_bytes(int64_t M, int64_t N, int64_t K, bool nn, int split);
 cudaError_t launch_update_tc(const TcUpdateArgs &a, cudaStream_t st);
 bool tc_supported(int device);
+// tensor-pipe peak loop: kind 0 BF16, 1 FP16 (kind::f16), 2 TF32 (kind::tf32)
+cudaError_t measure_tc_peak(int kind, int sm_count, double *flops_per_s);
 
 // Solves (solve.cu)
 template <typename Tf, typename Tc>
@@ -220,7 +223,8 @@ cudaError_t launch_coupling(const Tf *F, int64_t ldf, const Tf *Dinv, int64_t n,
 template <typename Tf>
 cudaError_t launch_trsm_inv(const Tf *F, int64_t ldf, const Tf *Dinv, const Tf *M, double *B,
                             int64_t ldb, int64_t n, int64_t nrhs, int kind, int *sync,
-                            unsigned epoch, int *err, int64_t spin_limit, cudaStream_t st);
+                            unsigned epoch, int *err, int64_t spin_limit, cudaStream_t st,
+                            int withhold = -1);
 // r = b - A x in FP64 (and the norms of r, x, b per column when `norms`);
 // small orders split the columns of A into slices whose partial products go
 // to `work` (residual_work_bytes; without it, one slice).

@@ -19,6 +19,7 @@ namespace {
 constexpr int TB = 32;       // rows per block
 constexpr int NRC = 32;      // right-hand sides per chunk
 constexpr int TRSM_THREADS = 256;
+constexpr int TRSM_MAX_GROUPS = 4;  // right-hand-side groups of 16 per trsm_inv launch
 
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
   unsigned long long t;
@@ -258,11 +259,20 @@ struct TrsmCfg {
       sizeof(Tc) * ((size_t)BS * (KC + 1) + (size_t)KC * (NRC + 1) + (size_t)BS * (BS + 1));
 };
 
-template <typename Tf, typename Tc>
-__global__ void __launch_bounds__(TRSM_THREADS)
+// Resident CTAs per SM the registers must allow: FP32 blocks are held back
+// to two by their shared memory anyway; FP64 blocks with one group keep
+// six resident (their shared memory allows it), more groups two.
+template <typename Tc, int G>
+constexpr int trsm_min_blocks() {
+  return (sizeof(Tc) == 8 && G == 1) ? 6 : 2;
+}
+
+template <typename Tf, typename Tc, int TRSM_GROUPS>
+__global__ void __launch_bounds__(TRSM_THREADS, trsm_min_blocks<Tc, TRSM_GROUPS>())
     trsm_inv_kernel(const Tf *__restrict__ F, int64_t ldf, const Tc *__restrict__ Dinv,
                     const Tc *__restrict__ Mc, double *B, int64_t ldb, int64_t n, int64_t nrhs,
-                    int kind, int *ticket, int *progress, int *err, long long wait_ns) {
+                    int kind, int *ticket, int *progress, int *err, long long wait_ns,
+                    int withhold) {
   using C = TrsmCfg<Tc>;
   constexpr int BS = C::BS, KC = C::KC, NRC = C::NRC, OPT = C::OPT;
   static_assert(KC % BS == 0 && C::TPR * OPT == NRC, "layout");
@@ -325,45 +335,55 @@ __global__ void __launch_bounds__(TRSM_THREADS)
   };
 
   // positions 0 .. t - 2 go through the chunks; the previous position t - 1
-  // enters through the coupling block M_t = Dinv[b] op(F)[b, previous block]
+  // enters through the coupling block M_t = Dinv[b] op(F)[b, previous block].
+  // All right-hand-side groups (NRC columns each, at most TRSM_GROUPS) are
+  // carried together: each chunk of finished positions is applied to every
+  // group before the next wait, so only one pass over the row panel lies on
+  // the chain between this position and the next.
   const int tmain = t > 0 ? t - 1 : 0;
-  for (int64_t rc0 = 0; rc0 < nrhs; rc0 += NRC) {
-    const int cols = (int)min64(NRC, nrhs - rc0);
-    if (rc0 > 0 && t > 0) {  // the previous group left M_t in Ds
-      const Tc *D = Dinv + (int64_t)ib * BS * BS;
-      for (int idx = tid; idx < BS * BS; idx += TRSM_THREADS) Ds[(idx / BS) * (BS + 1) + idx % BS] = D[idx];
-    }
-    Tc acc[OPT];
+  const int ng = (int)((nrhs + NRC - 1) / NRC);  // <= TRSM_GROUPS (the launcher slices)
+  Tc acc[TRSM_GROUPS][OPT];
 #pragma unroll
-    for (int q = 0; q < OPT; ++q)
-      acc[q] = (tr < rows && tc + q < cols) ? (Tc)B[(r0 + tr) * ldb + rc0 + tc + q] : Tc(0);
-    int done = 0;
-    while (done < tmain) {
-      // op(F) for the next chunk of positions, loaded once, before waiting
-      // for any of its X
-      const int wmax = min(KC / BS, tmain - done);
-      int64_t f0, f1;
-      col_range(done, wmax, f0, f1);
-      const int fw = (int)(f1 - f0);
-      for (int idx = tid; idx < BS * KC; idx += TRSM_THREADS) {
-        const int i = idx / KC, k = idx % KC;
-        Fs[i * (KC + 1) + k] = (i < rows && k < fw) ? (Tc)op_elem(F, ldf, kind, r0 + i, f0 + k) : Tc(0);
-      }
-      int applied = 0;  // positions of this chunk applied so far
-      while (applied < wmax) {
-        const int p0 = done + applied;
-        const int avail = wait_pos(p0);
-        if (avail < 0) return;
-        // the finished positions p0 .. p0 + w - 1 of this chunk
-        const int w = min(wmax - applied, avail - p0);
-        int64_t c0, c1;
-        col_range(p0, w, c0, c1);
-        const int kw = (int)(c1 - c0);
-        // only the kw rows the products below read
-        for (int idx = tid; idx < kw * NRC; idx += TRSM_THREADS) {
-          const int k = idx / NRC, c = idx % NRC;
-          Xs[k * (NRC + 1) + c] = c < cols ? (Tc)__ldcg(&B[(c0 + k) * ldb + rc0 + c]) : Tc(0);
-        }
+  for (int g = 0; g < TRSM_GROUPS; ++g)
+#pragma unroll
+    for (int q = 0; q < OPT; ++q) {
+      const int64_t c = (int64_t)g * NRC + tc + q;
+      acc[g][q] = (g < ng && tr < rows && c < nrhs) ? (Tc)B[(r0 + tr) * ldb + c] : Tc(0);
+    }
+  // X rows [c0, c0 + kw) of group g into Xs
+  auto load_x = [&](int g, int64_t c0, int kw) {
+    const int64_t cb = (int64_t)g * NRC;
+    for (int idx = tid; idx < kw * NRC; idx += TRSM_THREADS) {
+      const int k = idx / NRC, c = idx % NRC;
+      Xs[k * (NRC + 1) + c] = cb + c < nrhs ? (Tc)__ldcg(&B[(c0 + k) * ldb + cb + c]) : Tc(0);
+    }
+  };
+  int done = 0;
+  while (done < tmain) {
+    // op(F) for the next chunk of positions, loaded once, before waiting
+    // for any of its X
+    const int wmax = min(KC / BS, tmain - done);
+    int64_t f0, f1;
+    col_range(done, wmax, f0, f1);
+    const int fw = (int)(f1 - f0);
+    for (int idx = tid; idx < BS * KC; idx += TRSM_THREADS) {
+      const int i = idx / KC, k = idx % KC;
+      Fs[i * (KC + 1) + k] = (i < rows && k < fw) ? (Tc)op_elem(F, ldf, kind, r0 + i, f0 + k) : Tc(0);
+    }
+    int applied = 0;  // positions of this chunk applied so far
+    while (applied < wmax) {
+      const int p0 = done + applied;
+      const int avail = wait_pos(p0);
+      if (avail < 0) return;
+      // the finished positions p0 .. p0 + w - 1 of this chunk
+      const int w = min(wmax - applied, avail - p0);
+      int64_t c0, c1;
+      col_range(p0, w, c0, c1);
+      const int kw = (int)(c1 - c0);
+#pragma unroll
+      for (int g = 0; g < TRSM_GROUPS; ++g) {
+        if (g >= ng) continue;  // uniform
+        load_x(g, c0, kw);  // only the kw rows the products below read
         __syncthreads();
         // blocks in position order (backward: descending), columns ascending
         // inside a block: the same order for any chunking, so results do not
@@ -378,54 +398,66 @@ __global__ void __launch_bounds__(TRSM_THREADS)
             const Tc f = Fr[k];
             const Tc *xk = Xb + k * (NRC + 1);
 #pragma unroll
-            for (int q = 0; q < OPT; ++q) acc[q] = acc[q] - f * xk[q];
+            for (int q = 0; q < OPT; ++q) acc[g][q] = acc[g][q] - f * xk[q];
           }
         }
         __syncthreads();
-        applied += w;
       }
-      done += wmax;
+      applied += w;
     }
-    // Y = Dinv[b] * acc, before the previous position is waited for
+    done += wmax;
+  }
+  // Y = Dinv[b] * acc per group, before the previous position is waited for
+  Tc out[TRSM_GROUPS][OPT];
 #pragma unroll
-    for (int q = 0; q < OPT; ++q) Xs[tr * (NRC + 1) + tc + q] = acc[q];
+  for (int g = 0; g < TRSM_GROUPS; ++g) {
+#pragma unroll
+    for (int q = 0; q < OPT; ++q) out[g][q] = Tc(0);
+    if (g >= ng) continue;  // uniform
+#pragma unroll
+    for (int q = 0; q < OPT; ++q) Xs[tr * (NRC + 1) + tc + q] = acc[g][q];
     __syncthreads();
-    Tc out[OPT];
-#pragma unroll
-    for (int q = 0; q < OPT; ++q) out[q] = Tc(0);
 #pragma unroll 8
     for (int k = 0; k < BS; ++k) {
       const Tc d = Ds[tr * (BS + 1) + k];
 #pragma unroll
-      for (int q = 0; q < OPT; ++q) out[q] = out[q] + d * Xs[k * (NRC + 1) + tc + q];
+      for (int q = 0; q < OPT; ++q) out[g][q] = out[g][q] + d * Xs[k * (NRC + 1) + tc + q];
     }
-    if (t > 0) {
-      // X_b = Y - M_t X_{t-1}: one product on the dependence chain
-      __syncthreads();  // Ds and Xs are read
-      const Tc *M = Mc + (int64_t)t * BS * BS;
-      for (int idx = tid; idx < BS * BS; idx += TRSM_THREADS) Ds[(idx / BS) * (BS + 1) + idx % BS] = M[idx];
-      if (wait_pos(t - 1) < 0) return;
-      int64_t c0, c1;
-      col_range(t - 1, 1, c0, c1);
-      const int kw = (int)(c1 - c0);
-      for (int idx = tid; idx < kw * NRC; idx += TRSM_THREADS) {
-        const int k = idx / NRC, c = idx % NRC;
-        Xs[k * (NRC + 1) + c] = c < cols ? (Tc)__ldcg(&B[(c0 + k) * ldb + rc0 + c]) : Tc(0);
-      }
+    __syncthreads();  // Xs is rewritten by the next group
+  }
+  if (t > 0) {
+    // X_b = Y - M_t X_{t-1}: one product per group on the dependence chain
+    const Tc *M = Mc + (int64_t)t * BS * BS;
+    for (int idx = tid; idx < BS * BS; idx += TRSM_THREADS) Ds[(idx / BS) * (BS + 1) + idx % BS] = M[idx];
+    if (wait_pos(t - 1) < 0) return;
+    int64_t c0, c1;
+    col_range(t - 1, 1, c0, c1);
+    const int kw = (int)(c1 - c0);
+#pragma unroll
+    for (int g = 0; g < TRSM_GROUPS; ++g) {
+      if (g >= ng) continue;  // uniform
+      load_x(g, c0, kw);
       __syncthreads();
 #pragma unroll 8
       for (int k = 0; k < kw; ++k) {
         const Tc m = Ds[tr * (BS + 1) + k];
 #pragma unroll
-        for (int q = 0; q < OPT; ++q) out[q] = out[q] - m * Xs[k * (NRC + 1) + tc + q];
+        for (int q = 0; q < OPT; ++q) out[g][q] = out[g][q] - m * Xs[k * (NRC + 1) + tc + q];
       }
+      __syncthreads();
     }
-#pragma unroll
-    for (int q = 0; q < OPT; ++q)
-      if (tr < rows && tc + q < cols) B[(r0 + tr) * ldb + rc0 + tc + q] = (double)out[q];
-    __syncthreads();
   }
-  if (tid == 0) {
+#pragma unroll
+  for (int g = 0; g < TRSM_GROUPS; ++g)
+#pragma unroll
+    for (int q = 0; q < OPT; ++q) {
+      const int64_t c = (int64_t)g * NRC + tc + q;
+      if (g < ng && tr < rows && c < nrhs) B[(r0 + tr) * ldb + c] = (double)out[g][q];
+    }
+  __syncthreads();  // every row of X_b is stored before thread 0 publishes it
+  // (test hook: position `withhold` never publishes, so the waits for it
+  // run out; -1 in every normal call)
+  if (tid == 0 && t != withhold) {
     __threadfence();
     st_release(progress, t + 1);  // every position before t is finished: progress was t
   }
@@ -664,21 +696,47 @@ cudaError_t launch_coupling(const Tf *F, int64_t ldf, const Tf *Dinv, int64_t n,
 template <typename Tf>
 cudaError_t launch_trsm_inv(const Tf *F, int64_t ldf, const Tf *Dinv, const Tf *M, double *B,
                             int64_t ldb, int64_t n, int64_t nrhs, int kind, int *sync,
-                            unsigned epoch, int *err, int64_t spin_limit, cudaStream_t st) {
+                            unsigned epoch, int *err, int64_t spin_limit, cudaStream_t st,
+                            int withhold) {
   if (n <= 0 || nrhs <= 0) return cudaSuccess;
   using C = TrsmCfg<Tf>;
   const int64_t nb = (n + C::BS - 1) / C::BS;
   (void)epoch;
-  static const cudaError_t attr = cudaFuncSetAttribute(
-      trsm_inv_kernel<Tf, Tf>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+  static const cudaError_t attr = [] {
+    cudaError_t a = cudaFuncSetAttribute(trsm_inv_kernel<Tf, Tf, 1>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    if (a == cudaSuccess)
+      a = cudaFuncSetAttribute(trsm_inv_kernel<Tf, Tf, 2>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    if (a == cudaSuccess)
+      a = cudaFuncSetAttribute(trsm_inv_kernel<Tf, Tf, TRSM_MAX_GROUPS>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    return a;
+  }();
   if (attr != cudaSuccess) return attr;
-  cudaError_t e = cudaMemsetAsync(sync, 0, 2 * sizeof(int), st);  // ticket, progress
-  if (e != cudaSuccess) return e;
   const long long wait_ns = (long long)spin_limit * 100LL;
-  trsm_inv_kernel<Tf, Tf><<<(unsigned)nb, TRSM_THREADS, C::SMEM, st>>>(
-      F, ldf, Dinv, M, B, ldb, n, nrhs, kind, sync, sync + 1, err, wait_ns);
-  count_launch();
-  return cudaGetLastError();
+  // one launch per slab of up to TRSM_GROUPS * NRC right-hand sides, each a
+  // complete sweep with fresh sync words (stream order separates the slabs)
+  constexpr int64_t SLAB = (int64_t)TRSM_MAX_GROUPS * C::NRC;
+  for (int64_t c0 = 0; c0 < nrhs; c0 += SLAB) {
+    cudaError_t e = cudaMemsetAsync(sync, 0, 2 * sizeof(int), st);  // ticket, progress
+    if (e != cudaSuccess) return e;
+    const int64_t w = min64(SLAB, nrhs - c0);
+    const int hold = withhold < nb ? withhold : -1;
+    if (w <= C::NRC)
+      trsm_inv_kernel<Tf, Tf, 1><<<(unsigned)nb, TRSM_THREADS, C::SMEM, st>>>(
+          F, ldf, Dinv, M, B + c0, ldb, n, w, kind, sync, sync + 1, err, wait_ns, hold);
+    else if (w <= 2 * C::NRC)
+      trsm_inv_kernel<Tf, Tf, 2><<<(unsigned)nb, TRSM_THREADS, C::SMEM, st>>>(
+          F, ldf, Dinv, M, B + c0, ldb, n, w, kind, sync, sync + 1, err, wait_ns, hold);
+    else
+      trsm_inv_kernel<Tf, Tf, TRSM_MAX_GROUPS><<<(unsigned)nb, TRSM_THREADS, C::SMEM, st>>>(
+          F, ldf, Dinv, M, B + c0, ldb, n, w, kind, sync, sync + 1, err, wait_ns, hold);
+    count_launch();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 // r = b - (P[0] + P[1] + ... ) with the slices summed in order; the norms as
@@ -799,10 +857,10 @@ template cudaError_t launch_coupling<float>(const float *, int64_t, const float 
                                             float *, cudaStream_t);
 template cudaError_t launch_trsm_inv<double>(const double *, int64_t, const double *, const double *,
                                              double *, int64_t, int64_t, int64_t, int, int *,
-                                             unsigned, int *, int64_t, cudaStream_t);
+                                             unsigned, int *, int64_t, cudaStream_t, int);
 template cudaError_t launch_trsm_inv<float>(const float *, int64_t, const float *, const float *,
                                             double *, int64_t, int64_t, int64_t, int, int *, unsigned,
-                                            int *, int64_t, cudaStream_t);
+                                            int *, int64_t, cudaStream_t, int);
 template cudaError_t launch_backward_error<double>(int, const double *, int64_t, const double *,
                                                    int64_t, int64_t, double *, cudaStream_t);
 template cudaError_t launch_backward_error<float>(int, const double *, int64_t, const float *,
