@@ -48,9 +48,15 @@ int64_t served_step(int64_t n, gb_dtype dt) {
 // Device bytes a job holds while it runs: the FP64 copy of A (refinement or
 // host input), the factor, right-hand sides and solution, the refinement
 // residual and the packed tensor-core operands.
+// Leading dimension of a job's factor buffer: a multiple of 64 elements, so
+// that every row starts on a 256-byte boundary and the tensor-core update's
+// epilogue can reduce into it with TMA (its row pitch must be a multiple of
+// 16 bytes); the factor's layout is the job's own business.
+int64_t factor_ld(int64_t n) { return (n + 63) / 64 * 64; }
+
 size_t footprint(const gb_request &r) {
   const size_t n = (size_t)r.n, k = (size_t)r.nrhs;
-  const size_t fac = (r.dtype == GB_F64 ? 8 : 4) * n * n;
+  const size_t fac = (r.dtype == GB_F64 ? 8 : 4) * n * (size_t)factor_ld(r.n);
   const size_t s = (size_t)served_step(r.n, r.dtype);
   const size_t planes = r.dtype == GB_MIX_BF16X3 ? 6 : 1;
   const size_t pack = (r.dtype >= GB_MIX_BF16) ? 2 * n * ((s + 63) / 64 * 64) * 2 * planes : 0;
@@ -118,7 +124,8 @@ void run_job(gb_server *S, gb_server::Slot &slot, gb_server::Job &J) {
   if (!a_dev && cudaMallocAsync((void **)&dA, 8 * (size_t)n * n, st) != cudaSuccess) fail(GB_ERR_NOMEM);
   if (!b_dev && cudaMallocAsync((void **)&dB, 8 * (size_t)n * k, st) != cudaSuccess) fail(GB_ERR_NOMEM);
   if (!x_dev && cudaMallocAsync((void **)&dX, 8 * (size_t)n * k, st) != cudaSuccess) fail(GB_ERR_NOMEM);
-  if (cudaMallocAsync(&dL, (r.dtype == GB_F64 ? 8 : 4) * (size_t)n * n, st) != cudaSuccess)
+  const int64_t ldl = factor_ld(n);
+  if (cudaMallocAsync(&dL, (r.dtype == GB_F64 ? 8 : 4) * (size_t)n * ldl, st) != cudaSuccess)
     fail(GB_ERR_NOMEM);
   const double *A = a_dev ? r.A : dA;
   const double *B = b_dev ? r.B : dB;
@@ -135,11 +142,11 @@ void run_job(gb_server *S, gb_server::Slot &slot, gb_server::Job &J) {
     if (r.dtype == GB_F32) {
       // GB_F32 factors read float input: cast A's lower triangle into the
       // factor buffer and factor it in place
-      const cudaError_t ce = launch_copy_matrix<double, float>(A, lda, (float *)dL, n, n, true, st);
-      e = ce == cudaSuccess ? gb_chol_factor(h, n, s, r.dtype, dL, n, dL, n, dinfo, st)
+      const cudaError_t ce = launch_copy_matrix<double, float>(A, lda, (float *)dL, ldl, n, true, st);
+      e = ce == cudaSuccess ? gb_chol_factor(h, n, s, r.dtype, dL, ldl, dL, ldl, dinfo, st)
                             : GB_ERR_CUDA;
     } else {
-      e = gb_chol_factor(h, n, s, r.dtype, A, lda, dL, n, dinfo, st);
+      e = gb_chol_factor(h, n, s, r.dtype, A, lda, dL, ldl, dinfo, st);
     }
     if (e != GB_OK) fail(e);
   }
@@ -151,7 +158,7 @@ void run_job(gb_server *S, gb_server::Slot &slot, gb_server::Job &J) {
   gb_solve_stats stats{0, 0, 0.0};
   if (st_all == GB_OK && info == 0) {
     gb_refine_opts opts{r.tol > 0 ? r.tol : 1e-14, r.max_iter > 0 ? r.max_iter : 30};
-    gb_status e = gb_chol_solve(h, n, k, r.dtype, dL, n, refine ? A : nullptr, lda, B, ldb, X,
+    gb_status e = gb_chol_solve(h, n, k, r.dtype, dL, ldl, refine ? A : nullptr, lda, B, ldb, X,
                                 ldx, &opts, &stats, st);
     if (e != GB_OK) fail(e);
     if (!x_dev && (e == GB_OK || e == GB_ERR_NOT_CONVERGED) &&
