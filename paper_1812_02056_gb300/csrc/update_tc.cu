@@ -853,6 +853,68 @@ cudaError_t launch_kernel(const TcKernelArgs &k, int64_t valid, int dev, cudaStr
                             k.use_tma_store, k.vec_ok);
 }
 
+
+// ------------------------------------------------ tensor-pipe peak loop
+// One CTA per SM issues back-to-back dense MMAs M = 128, N = 256 on
+// K-major tiles already in shared memory (zeros: the rate does not depend on
+// the values), accumulating into one TMEM accumulator, and waits (bounded)
+// for their completion.  kind 0: kind::f16 with BF16 operands, 1: kind::f16
+// with FP16 operands (K = 16 per instruction), 2: kind::tf32 (K = 8).  Each
+// 128-byte row step of the tiles is one instruction's K.
+constexpr uint32_t PEAK_A = BM * 128, PEAK_B = BN * 128;  // one 128-byte K step each
+constexpr size_t PEAK_SMEM = PEAK_A + PEAK_B + 1024;
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(da), "l"(db), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__global__ void __launch_bounds__(128, 1)
+    tc_peak_kernel(int kind, int iters, uint32_t idesc, long long wait_ns, int *err) {
+  extern __shared__ __align__(1024) unsigned char peak_raw[];
+  __shared__ uint32_t s_tmem;
+  __shared__ __align__(8) uint64_t s_done;
+  __shared__ int s_abort;
+  const uint32_t base = (smem_u32(peak_raw) + 1023u) & ~1023u;
+  unsigned char *gen = peak_raw + (base - smem_u32(peak_raw));
+  for (uint32_t i = threadIdx.x * 16; i < PEAK_A + PEAK_B; i += 128 * 16)
+    *reinterpret_cast<uint4 *>(gen + i) = make_uint4(0, 0, 0, 0);
+  if (threadIdx.x == 0) {
+    mbar_init(&s_done, 1);
+    s_abort = 0;
+  }
+  fence_proxy_async_smem();  // the zeros are read by the tensor pipe
+  if (threadIdx.x < 32) tmem_alloc<1>(&s_tmem, 256);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  if (threadIdx.x == 0) {
+    const uint32_t a0 = base, b0 = base + PEAK_A;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        const uint64_t da = sw128_desc(a0 + kk * 32), db = sw128_desc(b0 + kk * 32);
+        const uint32_t acc = (it | kk) != 0;
+        if (kind == 2) mma_tf32(tmem, da, db, idesc, acc);
+        else mma_f16<1>(tmem, da, db, idesc, acc);
+      }
+    }
+    mma_commit(&s_done);
+  }
+  __syncwarp();
+  mbar_wait(&s_done, 0, (unsigned long long)wait_ns, err, &s_abort);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (threadIdx.x < 32) tmem_dealloc<1>(tmem, 256);
+}
+
 }  // namespace
 
 bool tc_supported(int device) {
@@ -963,6 +1025,50 @@ cudaError_t launch_update_tc(const TcUpdateArgs &a, cudaStream_t st) {
                 : launch_kernel<false, 1>(k, valid, dev, st);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
+}
+
+// Tensor-pipe throughput (see tc_peak_kernel): flop/s over every SM.
+cudaError_t measure_tc_peak(int kind, int sm_count, double *flops_per_s) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (!tc_supported(dev)) return cudaErrorNotSupported;
+  if (kind < 0 || kind > 2) return cudaErrorInvalidValue;
+  static const cudaError_t attr = cudaFuncSetAttribute(
+      tc_peak_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PEAK_SMEM);
+  if (attr != cudaSuccess) return attr;
+  // A and B formats: BF16 1, FP16 0 (kind::f16), TF32 2 (kind::tf32)
+  const uint32_t ab = kind == 0 ? 1u : (kind == 1 ? 0u : 2u);
+  const uint32_t idesc = (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(BN >> 3) << 17) |
+                         ((uint32_t)(BM >> 4) << 24);
+  const int iters = kind == 2 ? 10000 : 20000;
+  const double k_instr = kind == 2 ? 8.0 : 16.0;
+  int *err = nullptr;
+  if ((e = cudaMalloc(&err, sizeof(int))) != cudaSuccess) return e;
+  cudaEvent_t a = nullptr, b = nullptr;
+  float ms = 0.f;
+  int herr = 0;
+  const long long wait_ns = 1000000000LL;  // 1 s: the loop takes ~10 ms
+  if ((e = cudaMemset(err, 0, sizeof(int))) == cudaSuccess &&
+      (e = cudaEventCreate(&a)) == cudaSuccess && (e = cudaEventCreate(&b)) == cudaSuccess) {
+    tc_peak_kernel<<<sm_count, 128, PEAK_SMEM>>>(kind, iters / 20, idesc, wait_ns, err);  // warm-up
+    count_launch();
+    cudaEventRecord(a);
+    tc_peak_kernel<<<sm_count, 128, PEAK_SMEM>>>(kind, iters, idesc, wait_ns, err);
+    count_launch();
+    cudaEventRecord(b);
+    if ((e = cudaEventSynchronize(b)) == cudaSuccess && (e = cudaGetLastError()) == cudaSuccess &&
+        (e = cudaEventElapsedTime(&ms, a, b)) == cudaSuccess)
+      e = cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost);
+  }
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  cudaFree(err);
+  if (e != cudaSuccess) return e;
+  if (herr) return cudaErrorLaunchTimeout;
+  const double flops = (double)sm_count * iters * 4.0 * 2.0 * BM * BN * k_instr;
+  *flops_per_s = flops / (ms * 1e-3);
+  return cudaSuccess;
 }
 
 }  // namespace gb
