@@ -168,7 +168,7 @@ typedef enum gb_option {
                                every s columns: the same sums, grouped by
                                tile; FP32 traffic of the working matrix once
                                per block column.  Default 0.                 */
-  GB_OPT_TEST_WITHHOLD = 11 /* failure-detection test hook, 0 (default) off:
+  GB_OPT_TEST_WITHHOLD = 11, /* failure-detection test hook, 0 (default) off:
                                v >= 1 makes block v - 1 (in sweep order) of
                                the forward triangular sweep of gb_chol_solve
                                and gb_lu_solve skip publishing its
@@ -178,6 +178,11 @@ typedef enum gb_option {
                                GB_ERR_TIMEOUT and clears the word.  Nothing
                                faults or hangs; the next call on the handle
                                starts from fresh sync words.                  */
+  GB_OPT_INNER_CUDA_CORES = 12 /* 1: gb_chol_factor with a mixed dtype runs
+                               the updates inside each s-block (K <= inner
+                               step) in FP32 on the CUDA cores instead of the
+                               tensor cores; the delayed rank-s updates stay
+                               on the tensor cores.  Default 0.              */
 } gb_option;
 
 gb_status gb_set_option(gb_handle *h, gb_option opt, int64_t value);

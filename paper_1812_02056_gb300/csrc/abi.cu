@@ -376,7 +376,10 @@ gb_status chol_blocked_on(gb_handle *h, int64_t n, int64_t s, T *W, int64_t ld, 
         PhaseTimer t(h, st, GB_PHASE_INNER, update_flops(n - r0, pe - r0, bw, true),
                      update_bytes(n - r0, pe - r0, bw, true, e));
         const T *R = W + r0 * ld + j0;
-        gb_status r = chol_update<T>(h, dt, W + r0 * ld + r0, R, R, ld, n - r0, pe - r0, bw,
+        // mixed dtypes: the skinny inner products (K <= 64) on the tensor
+        // cores, or in FP32 on the CUDA cores (GB_OPT_INNER_CUDA_CORES)
+        const gb_dtype di = (is_mixed(dt) && h->inner_cuda_cores) ? GB_F32 : dt;
+        gb_status r = chol_update<T>(h, di, W + r0 * ld + r0, R, R, ld, n - r0, pe - r0, bw,
                                      status, WS_PANEL, st);
         if (r != GB_OK) return r;
       }
@@ -477,7 +480,8 @@ gb_status chol_left_on(gb_handle *h, int64_t n, int64_t s, T *W, int64_t ld, int
         PhaseTimer t(h, st, GB_PHASE_INNER, update_flops(n - r0, pe - r0, bw, true),
                      update_bytes(n - r0, pe - r0, bw, true, 4));
         const T *R = W + r0 * ld + j0;
-        r = chol_update<T>(h, dt, W + r0 * ld + r0, R, R, ld, n - r0, pe - r0, bw, status,
+        const gb_dtype di = (is_mixed(dt) && h->inner_cuda_cores) ? GB_F32 : dt;
+        r = chol_update<T>(h, di, W + r0 * ld + r0, R, R, ld, n - r0, pe - r0, bw, status,
                            WS_PANEL, st);
         if (r != GB_OK) return r;
       }
@@ -1192,6 +1196,7 @@ gb_status gb_set_option(gb_handle *h, gb_option opt, int64_t v) {
       if (v < 0 || v > (int64_t)1 << 30) return -3;
       h->test_withhold = (int)v;
       return GB_OK;
+    case GB_OPT_INNER_CUDA_CORES: h->inner_cuda_cores = v ? 1 : 0; return GB_OK;
     default: return -2;
   }
 }
@@ -1211,6 +1216,7 @@ gb_status gb_get_option(gb_handle *h, gb_option opt, int64_t *v) {
     case GB_OPT_QR_INNER_STEP: *v = h->qr_inner; return GB_OK;
     case GB_OPT_LEFT_LOOKING: *v = h->left_looking; return GB_OK;
     case GB_OPT_TEST_WITHHOLD: *v = h->test_withhold; return GB_OK;
+    case GB_OPT_INNER_CUDA_CORES: *v = h->inner_cuda_cores; return GB_OK;
     default: return -2;
   }
 }

@@ -57,6 +57,7 @@ struct gb_handle {
   int qr_inner = 16;          // inner step of the QR panel (GB_OPT_QR_INNER_STEP)
   int left_looking = 0;       // GB_OPT_LEFT_LOOKING
   int test_withhold = 0;      // GB_OPT_TEST_WITHHOLD (test hook, 0 = off)
+  int inner_cuda_cores = 0;   // GB_OPT_INNER_CUDA_CORES
   // device copies of host buffers come from this pool, which keeps its
   // memory between calls (allocating and mapping it again each call costs
   // more than the copies)
