@@ -259,12 +259,191 @@ struct TrsmCfg {
       sizeof(Tc) * ((size_t)BS * (KC + 1) + (size_t)KC * (NRC + 1) + (size_t)BS * (BS + 1));
 };
 
-// Resident CTAs per SM the registers must allow: FP32 blocks are held back
-// to two by their shared memory anyway; FP64 blocks with one group keep
-// six resident (their shared memory allows it), more groups two.
+// One group of at most NRC right-hand sides: the same steps as
+// trsm_inv_kernel with TRSM_GROUPS = 1, in the form that keeps the register
+// count low (40 instead of 109 for FP32), which measured faster for the
+// common solve with 16 right-hand sides.
+template <typename Tf, typename Tc>
+__global__ void __launch_bounds__(TRSM_THREADS)
+    trsm_inv1_kernel(const Tf *__restrict__ F, int64_t ldf, const Tc *__restrict__ Dinv,
+                    const Tc *__restrict__ Mc, double *B, int64_t ldb, int64_t n, int64_t nrhs,
+                    int kind, int *ticket, int *progress, int *err, long long wait_ns,
+                    int withhold) {
+  using C = TrsmCfg<Tc>;
+  constexpr int BS = C::BS, KC = C::KC, NRC = C::NRC, OPT = C::OPT;
+  static_assert(KC % BS == 0 && C::TPR * OPT == NRC, "layout");
+  extern __shared__ __align__(16) unsigned char trsm_smem[];
+  Tc *Fs = reinterpret_cast<Tc *>(trsm_smem);   // [BS][KC + 1]
+  Tc *Xs = Fs + (size_t)BS * (KC + 1);           // [KC][NRC + 1]
+  Tc *Ds = Xs + (size_t)KC * (NRC + 1);          // [BS][BS + 1]
+  __shared__ int s_t, s_avail, s_abort;
+  const int tid = threadIdx.x;
+  const int nb = (int)((n + BS - 1) / BS);
+  const bool fwd = (kind == TRSM_LOWER);
+  if (tid == 0) {
+    s_t = atomicAdd(ticket, 1);
+    s_abort = 0;
+  }
+  __syncthreads();
+  const int t = s_t;
+  if (t < 0 || t >= nb) return;
+  const int ib = fwd ? t : nb - 1 - t;
+  const int64_t r0 = (int64_t)ib * BS;
+  const int rows = (int)min64(BS, n - r0);
+  const int tr = tid / C::TPR, tc = (tid % C::TPR) * OPT;
+  {
+    const Tc *D = Dinv + (int64_t)ib * BS * BS;
+    for (int idx = tid; idx < BS * BS; idx += TRSM_THREADS) Ds[(idx / BS) * (BS + 1) + idx % BS] = D[idx];
+  }
+
+  // columns of op(F) for positions [p0, p0 + w): forward blocks p0 .. p0+w-1,
+  // backward blocks nb-p0-w .. nb-p0-1 (both as one ascending column range)
+  auto col_range = [&](int p0, int w, int64_t &c0, int64_t &c1) {
+    const int64_t b0 = fwd ? p0 : nb - p0 - w;
+    c0 = b0 * BS;
+    c1 = min64((b0 + w) * BS, n);
+  };
+
+  // every thread: wait until position p is finished; the number of finished
+  // positions, or -1 once a wait has expired (here or in another CTA)
+  auto wait_pos = [&](int p) {
+    if (tid == 0) {
+      int spins = 0, avail = ld_acquire(progress);
+      const long long t0 = (long long)globaltimer_ns();
+      while (avail <= p) {
+        if ((++spins & 255) == 0) {
+          if (ld_acquire(err) & DEV_ERR_TIMEOUT) {
+            s_abort = 1;
+            break;
+          }
+          if ((long long)globaltimer_ns() - t0 > wait_ns) {
+            atomicOr(err, DEV_ERR_TIMEOUT);
+            s_abort = 1;
+            break;
+          }
+        }
+        avail = ld_acquire(progress);
+      }
+      s_avail = avail;
+    }
+    __syncthreads();
+    return s_abort ? -1 : s_avail;
+  };
+
+  // positions 0 .. t - 2 go through the chunks; the previous position t - 1
+  // enters through the coupling block M_t = Dinv[b] op(F)[b, previous block]
+  const int tmain = t > 0 ? t - 1 : 0;
+  for (int64_t rc0 = 0; rc0 < nrhs; rc0 += NRC) {
+    const int cols = (int)min64(NRC, nrhs - rc0);
+    if (rc0 > 0 && t > 0) {  // the previous group left M_t in Ds
+      const Tc *D = Dinv + (int64_t)ib * BS * BS;
+      for (int idx = tid; idx < BS * BS; idx += TRSM_THREADS) Ds[(idx / BS) * (BS + 1) + idx % BS] = D[idx];
+    }
+    Tc acc[OPT];
+#pragma unroll
+    for (int q = 0; q < OPT; ++q)
+      acc[q] = (tr < rows && tc + q < cols) ? (Tc)B[(r0 + tr) * ldb + rc0 + tc + q] : Tc(0);
+    int done = 0;
+    while (done < tmain) {
+      // op(F) for the next chunk of positions, loaded once, before waiting
+      // for any of its X
+      const int wmax = min(KC / BS, tmain - done);
+      int64_t f0, f1;
+      col_range(done, wmax, f0, f1);
+      const int fw = (int)(f1 - f0);
+      for (int idx = tid; idx < BS * KC; idx += TRSM_THREADS) {
+        const int i = idx / KC, k = idx % KC;
+        Fs[i * (KC + 1) + k] = (i < rows && k < fw) ? (Tc)op_elem(F, ldf, kind, r0 + i, f0 + k) : Tc(0);
+      }
+      int applied = 0;  // positions of this chunk applied so far
+      while (applied < wmax) {
+        const int p0 = done + applied;
+        const int avail = wait_pos(p0);
+        if (avail < 0) return;
+        // the finished positions p0 .. p0 + w - 1 of this chunk
+        const int w = min(wmax - applied, avail - p0);
+        int64_t c0, c1;
+        col_range(p0, w, c0, c1);
+        const int kw = (int)(c1 - c0);
+        // only the kw rows the products below read
+        for (int idx = tid; idx < kw * NRC; idx += TRSM_THREADS) {
+          const int k = idx / NRC, c = idx % NRC;
+          Xs[k * (NRC + 1) + c] = c < cols ? (Tc)__ldcg(&B[(c0 + k) * ldb + rc0 + c]) : Tc(0);
+        }
+        __syncthreads();
+        // blocks in position order (backward: descending), columns ascending
+        // inside a block: the same order for any chunking, so results do not
+        // depend on how far the other blocks had got
+        for (int pb = 0; pb < w; ++pb) {
+          const int64_t b0 = fwd ? (int64_t)(p0 + pb) : (int64_t)(nb - 1 - p0 - pb);
+          const int64_t bc0 = b0 * BS;
+          const int bw = (int)min64(BS, n - bc0);
+          const Tc *Fr = Fs + tr * (KC + 1) + (bc0 - f0);
+          const Tc *Xb = Xs + (bc0 - c0) * (NRC + 1) + tc;
+          for (int k = 0; k < bw; ++k) {
+            const Tc f = Fr[k];
+            const Tc *xk = Xb + k * (NRC + 1);
+#pragma unroll
+            for (int q = 0; q < OPT; ++q) acc[q] = acc[q] - f * xk[q];
+          }
+        }
+        __syncthreads();
+        applied += w;
+      }
+      done += wmax;
+    }
+    // Y = Dinv[b] * acc, before the previous position is waited for
+#pragma unroll
+    for (int q = 0; q < OPT; ++q) Xs[tr * (NRC + 1) + tc + q] = acc[q];
+    __syncthreads();
+    Tc out[OPT];
+#pragma unroll
+    for (int q = 0; q < OPT; ++q) out[q] = Tc(0);
+#pragma unroll 8
+    for (int k = 0; k < BS; ++k) {
+      const Tc d = Ds[tr * (BS + 1) + k];
+#pragma unroll
+      for (int q = 0; q < OPT; ++q) out[q] = out[q] + d * Xs[k * (NRC + 1) + tc + q];
+    }
+    if (t > 0) {
+      // X_b = Y - M_t X_{t-1}: one product on the dependence chain
+      __syncthreads();  // Ds and Xs are read
+      const Tc *M = Mc + (int64_t)t * BS * BS;
+      for (int idx = tid; idx < BS * BS; idx += TRSM_THREADS) Ds[(idx / BS) * (BS + 1) + idx % BS] = M[idx];
+      if (wait_pos(t - 1) < 0) return;
+      int64_t c0, c1;
+      col_range(t - 1, 1, c0, c1);
+      const int kw = (int)(c1 - c0);
+      for (int idx = tid; idx < kw * NRC; idx += TRSM_THREADS) {
+        const int k = idx / NRC, c = idx % NRC;
+        Xs[k * (NRC + 1) + c] = c < cols ? (Tc)__ldcg(&B[(c0 + k) * ldb + rc0 + c]) : Tc(0);
+      }
+      __syncthreads();
+#pragma unroll 8
+      for (int k = 0; k < kw; ++k) {
+        const Tc m = Ds[tr * (BS + 1) + k];
+#pragma unroll
+        for (int q = 0; q < OPT; ++q) out[q] = out[q] - m * Xs[k * (NRC + 1) + tc + q];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < OPT; ++q)
+      if (tr < rows && tc + q < cols) B[(r0 + tr) * ldb + rc0 + tc + q] = (double)out[q];
+    __syncthreads();
+  }
+  if (tid == 0 && t != withhold) {  // (test hook: see trsm_inv_kernel)
+    __threadfence();
+    st_release(progress, t + 1);  // every position before t is finished: progress was t
+  }
+}
+
+// Resident CTAs per SM the registers must allow: FP64 blocks with one group
+// keep six resident (their shared memory allows it); FP32 with one group is
+// left to the compiler (its shared memory holds it to two CTAs anyway); more
+// groups need two.
 template <typename Tc, int G>
 constexpr int trsm_min_blocks() {
-  return (sizeof(Tc) == 8 && G == 1) ? 6 : 2;
+  return G == 1 ? (sizeof(Tc) == 8 ? 6 : 1) : 2;
 }
 
 template <typename Tf, typename Tc, int TRSM_GROUPS>
@@ -703,7 +882,7 @@ cudaError_t launch_trsm_inv(const Tf *F, int64_t ldf, const Tf *Dinv, const Tf *
   const int64_t nb = (n + C::BS - 1) / C::BS;
   (void)epoch;
   static const cudaError_t attr = [] {
-    cudaError_t a = cudaFuncSetAttribute(trsm_inv_kernel<Tf, Tf, 1>,
+    cudaError_t a = cudaFuncSetAttribute(trsm_inv1_kernel<Tf, Tf>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
     if (a == cudaSuccess)
       a = cudaFuncSetAttribute(trsm_inv_kernel<Tf, Tf, 2>,
@@ -724,7 +903,7 @@ cudaError_t launch_trsm_inv(const Tf *F, int64_t ldf, const Tf *Dinv, const Tf *
     const int64_t w = min64(SLAB, nrhs - c0);
     const int hold = withhold < nb ? withhold : -1;
     if (w <= C::NRC)
-      trsm_inv_kernel<Tf, Tf, 1><<<(unsigned)nb, TRSM_THREADS, C::SMEM, st>>>(
+      trsm_inv1_kernel<Tf, Tf><<<(unsigned)nb, TRSM_THREADS, C::SMEM, st>>>(
           F, ldf, Dinv, M, B + c0, ldb, n, w, kind, sync, sync + 1, err, wait_ns, hold);
     else if (w <= 2 * C::NRC)
       trsm_inv_kernel<Tf, Tf, 2><<<(unsigned)nb, TRSM_THREADS, C::SMEM, st>>>(
