@@ -178,7 +178,7 @@ typedef enum gb_option {
                                GB_ERR_TIMEOUT and clears the word.  Nothing
                                faults or hangs; the next call on the handle
                                starts from fresh sync words.                  */
-  GB_OPT_INNER_CUDA_CORES = 12 /* 1: gb_chol_factor with a mixed dtype runs
+  GB_OPT_INNER_CUDA_CORES = 12, /* 1: gb_chol_factor with a mixed dtype runs
                                the updates inside each s-block (K <= inner
                                step) in FP32 on the CUDA cores instead of the
                                tensor cores; the delayed rank-s updates stay
@@ -486,6 +486,9 @@ gb_status gb_measure_fma_peak(gb_handle *h, gb_dtype dt, double *flops_per_s);
  *                    memory (no memory traffic): dense tensor-pipe peak
  *   GB_PEAK_TC_F16   the same with FP16 operands
  *   GB_PEAK_TC_TF32  tcgen05.mma kind::tf32 (K = 8 per instruction)
+ *   GB_PEAK_DFMA_DMMA  FP64 FMAs and f64 MMAs interleaved in one loop, equal
+ *                    flops of each: above both single rates only if the
+ *                    two run on separate units
  * Returns GB_ERR_UNSUPPORTED for the tcgen05 kinds on a device without
  * them, and GB_ERR_TIMEOUT if the loop's bounded completion wait ran out.
  */
@@ -495,7 +498,8 @@ typedef enum gb_peak {
   GB_PEAK_DMMA = 2,
   GB_PEAK_TC_BF16 = 3,
   GB_PEAK_TC_F16 = 4,
-  GB_PEAK_TC_TF32 = 5
+  GB_PEAK_TC_TF32 = 5,
+  GB_PEAK_DFMA_DMMA = 6
 } gb_peak;
 gb_status gb_measure_peak(gb_handle *h, gb_peak kind, double *flops_per_s);
 

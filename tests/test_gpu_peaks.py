@@ -11,7 +11,7 @@ torch = pytest.importorskip("torch")
 
 RANGES_TFLOPS = {"dfma": (0.6, 1.4), "ffma": (40.0, 90.0), "dmma": (0.05, 1.4),
                  "tc_bf16": (900.0, 2600.0), "tc_f16": (900.0, 2600.0),
-                 "tc_tf32": (400.0, 1300.0)}
+                 "tc_tf32": (400.0, 1300.0), "dfma_dmma": (0.5, 2.8)}
 
 
 @pytest.fixture(scope="module")
@@ -33,4 +33,4 @@ def test_peak_in_range(h, kind):
 def test_bad_kind_rejected(h):
     import ctypes
     v = ctypes.c_double()
-    assert h.lib.gb_measure_peak(h.h, 6, ctypes.byref(v)) == -2
+    assert h.lib.gb_measure_peak(h.h, 7, ctypes.byref(v)) == -2
