@@ -168,8 +168,10 @@ __global__ void __launch_bounds__(inv_block<Tc>())
     diag_inv_kernel(const Tf *__restrict__ F, int64_t ldf, int64_t n, int kind,
                     Tc *__restrict__ Dinv) {
   constexpr int TB = inv_block<Tc>();
-  __shared__ Tc Bs[TB][TB + 1];
-  __shared__ Tc Ys[TB][TB + 1];  // column j of the inverse, built by thread j
+  // Bs: the block, Ys: column j of the inverse, built by thread j ([TB][TB + 1] each)
+  extern __shared__ __align__(16) unsigned char inv_smem[];
+  Tc (*Bs)[TB + 1] = reinterpret_cast<Tc (*)[TB + 1]>(inv_smem);
+  Tc (*Ys)[TB + 1] = Bs + TB;
   const int b = blockIdx.x, j = threadIdx.x;
   const int64_t r0 = (int64_t)b * TB;
   const int rows = (int)min64(TB, n - r0);
@@ -207,8 +209,9 @@ __global__ void __launch_bounds__(TRSM_THREADS)
     coupling_kernel(const Tc *__restrict__ F, int64_t ldf, const Tc *__restrict__ Dinv, int64_t n,
                     int kind, Tc *__restrict__ M) {
   constexpr int BS = inv_block<Tc>();
-  __shared__ Tc Ds[BS][BS + 1];
-  __shared__ Tc Os[BS][BS + 1];
+  extern __shared__ __align__(16) unsigned char cpl_smem[];  // Ds, Os: [BS][BS + 1] each
+  Tc (*Ds)[BS + 1] = reinterpret_cast<Tc (*)[BS + 1]>(cpl_smem);
+  Tc (*Os)[BS + 1] = Ds + BS;
   const int nb = (int)((n + BS - 1) / BS);
   const int p = blockIdx.x + 1;
   if (p >= nb) return;
@@ -856,8 +859,12 @@ cudaError_t launch_diag_inv(const Tf *F, int64_t ldf, int64_t n, int kind, Tf *D
                             cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   constexpr int BS = inv_block<Tf>();
+  constexpr size_t smem = 2 * sizeof(Tf) * BS * (BS + 1);
+  static const cudaError_t attr = cudaFuncSetAttribute(
+      diag_inv_kernel<Tf, Tf>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (attr != cudaSuccess) return attr;
   const int64_t nb = (n + BS - 1) / BS;
-  diag_inv_kernel<Tf, Tf><<<(unsigned)nb, BS, 0, st>>>(F, ldf, n, kind, Dinv);
+  diag_inv_kernel<Tf, Tf><<<(unsigned)nb, BS, smem, st>>>(F, ldf, n, kind, Dinv);
   count_launch();
   return cudaGetLastError();
 }
@@ -867,7 +874,11 @@ cudaError_t launch_coupling(const Tf *F, int64_t ldf, const Tf *Dinv, int64_t n,
                             cudaStream_t st) {
   const int64_t bs = inv_block<Tf>(), nb = (n + bs - 1) / bs;
   if (nb <= 1) return cudaSuccess;
-  coupling_kernel<Tf><<<(unsigned)(nb - 1), TRSM_THREADS, 0, st>>>(F, ldf, Dinv, n, kind, M);
+  constexpr size_t smem = 2 * sizeof(Tf) * inv_block<Tf>() * (inv_block<Tf>() + 1);
+  static const cudaError_t attr = cudaFuncSetAttribute(
+      coupling_kernel<Tf>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (attr != cudaSuccess) return attr;
+  coupling_kernel<Tf><<<(unsigned)(nb - 1), TRSM_THREADS, smem, st>>>(F, ldf, Dinv, n, kind, M);
   count_launch();
   return cudaGetLastError();
 }
