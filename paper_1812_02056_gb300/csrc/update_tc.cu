@@ -353,7 +353,7 @@ __global__ void __launch_bounds__(Cfg<CL>::THREADS, 1)
                      const __grid_constant__ CUtensorMap map_c, float *__restrict__ C, int64_t ldc,
                      int64_t M, int64_t N, int nk, int64_t diag, int64_t total, uint32_t idesc,
                      const int *status, int *err, long long wait_ns, int use_tma_store,
-                     int vec_ok) {
+                     int vec_ok, int kbs, uint32_t bstripe) {
   static_assert(CL == 1 || CL == 2, "one CTA or a CTA pair");
   constexpr int STAGES = Cfg<CL>::STAGES;
   constexpr uint32_t B_STAGE = Cfg<CL>::B_STAGE;
@@ -429,6 +429,9 @@ __global__ void __launch_bounds__(Cfg<CL>::THREADS, 1)
       while (ok && it.next(m0, n0)) {
         for (int kb = 0; kb < nk; ++kb, ++g) {
           const uint32_t s = g % STAGES, ph = (g / STAGES) & 1u;
+          // B's k-block: stripe table entry of this term, same offset inside it
+          const int t = kb / kbs;
+          const int kbb = (int)((bstripe >> (4 * t)) & 15u) * kbs + (kb - t * kbs);
           if (g >= (uint32_t)STAGES && !mbar_wait(&empty[s], ph ^ 1u, deadline, err, abort_flag)) {
             ok = false;
             break;
@@ -436,13 +439,13 @@ __global__ void __launch_bounds__(Cfg<CL>::THREADS, 1)
           if (CL == 1) {
             mbar_expect_tx(&full[s], A_STAGE + B_STAGE);
             tma_load_2d(sA + s * A_STAGE, &map_a, &full[s], kb * BK, (int)m0);
-            tma_load_2d(sB + s * B_STAGE, &map_b, &full[s], kb * BK, (int)n0);
+            tma_load_2d(sB + s * B_STAGE, &map_b, &full[s], kbb * BK, (int)n0);
           } else {
             // the even CTA's barrier counts the bytes of both CTAs
             if (rank == 0) mbar_expect_tx(&full[s], CL * (A_STAGE + B_STAGE));
             const uint32_t bar = full0 + s * 8u;
             tma_load_2d_pair(sA + s * A_STAGE, &map_a, bar, kb * BK, (int)m0);
-            tma_load_2d_pair(sB + s * B_STAGE, &map_b, bar, kb * BK,
+            tma_load_2d_pair(sB + s * B_STAGE, &map_b, bar, kbb * BK,
                              (int)(n0 + rank * (BN / 2)));
           }
         }
@@ -469,6 +472,9 @@ __global__ void __launch_bounds__(Cfg<CL>::THREADS, 1)
         const uint32_t d = tmem + buf * (TMEM_COLS / 2);
         for (int kb = 0; kb < nk; ++kb, ++g) {
           const uint32_t s = g % STAGES, ph = (g / STAGES) & 1u;
+          // B's k-block: stripe table entry of this term, same offset inside it
+          const int t = kb / kbs;
+          const int kbb = (int)((bstripe >> (4 * t)) & 15u) * kbs + (kb - t * kbs);
           if (!mbar_wait(&full[s], ph, deadline, err, abort_flag)) {
             ok = false;
             break;
@@ -759,6 +765,18 @@ uint32_t code_of(const int *planes, int terms) {
 constexpr int X3_PLANES[6] = {2, 1, 0, 1, 0, 0};
 constexpr int Y3_PLANES[6] = {0, 1, 2, 0, 1, 0};
 
+// For Y packed as X (the same rows): term t's B stripe is the first X
+// stripe that holds plane Y3_PLANES[t].
+uint32_t stripes_of_y_in_x() {
+  uint32_t code = 0;
+  for (int t = 0; t < 6; ++t) {
+    int st = 0;
+    while (X3_PLANES[st] != Y3_PLANES[t]) ++st;
+    code |= (uint32_t)st << (4 * t);
+  }
+  return code;
+}
+
 template <typename T16>
 void launch_pack_rows(const float *X, int64_t ldx, int64_t rows, int64_t K, int64_t Kp, int terms,
                       uint32_t code, T16 *out, int64_t ldo, cudaStream_t st) {
@@ -806,6 +824,8 @@ struct TcKernelArgs {
   int *err;
   long long wait_ns;
   int use_tma_store, vec_ok;
+  int kbs;           // k-blocks per term stripe (Kp / BK)
+  uint32_t bstripe;  // B's stripe for term t in bits 4t..4t+3
 };
 
 // Launch over `valid` tile groups: clusters of CL CTAs, as many groups as can
@@ -850,7 +870,7 @@ cudaError_t launch_kernel(const TcKernelArgs &k, int64_t valid, int dev, cudaStr
   count_launch();
   return cudaLaunchKernelEx(&cfg, kern, k.map_a, k.map_b, k.map_c, k.C, k.ldc, k.M, k.N, k.nk,
                             k.diag, k.total, k.idesc, k.status, k.err, k.wait_ns,
-                            k.use_tma_store, k.vec_ok);
+                            k.use_tma_store, k.vec_ok, k.kbs, k.bstripe);
 }
 
 
@@ -960,6 +980,7 @@ cudaError_t launch_update_tc(const TcUpdateArgs &a, cudaStream_t st) {
   if (Ke / BK > INT32_MAX) return cudaErrorInvalidValue;
   const void *xp, *yp;
   int64_t xstride = Ke, ystride = Ke;
+  uint32_t bstripe = 0x543210u;  // B's term t from its own stripe t
   if (a.xpack) {
     // operands already resident as 16-bit rows (one plane, K a multiple of
     // 64, rows 16-byte aligned): no packing
@@ -973,7 +994,12 @@ cudaError_t launch_update_tc(const TcUpdateArgs &a, cudaStream_t st) {
     ystride = a.ldyp;
   } else {
     if (tc_pack_bytes(a.M, a.N, a.K, a.nn, a.split) > a.pack_bytes) return cudaErrorInvalidValue;
-    const bool same = !a.nn && terms == 1 && a.X == a.Y && a.ldx == a.ldy && a.M == a.N;
+    // Y's rows are the first N rows of X (the Cholesky updates: the same
+    // panel, the trailing columns a prefix of the trailing rows): X's packed
+    // rows serve as Y's too -- with three planes through the stripe table,
+    // since X's stripes hold the planes in another order than Y's
+    const bool same = !a.nn && a.X == a.Y && a.ldx == a.ldy && a.N <= a.M;
+    if (same && terms > 1) bstripe = stripes_of_y_in_x();
     uint8_t *base = reinterpret_cast<uint8_t *>(a.pack);
     void *xw = base;
     void *yw = same ? base : base + (size_t)round_up(a.M, 8) * Ke * 2;
@@ -1016,7 +1042,8 @@ cudaError_t launch_update_tc(const TcUpdateArgs &a, cudaStream_t st) {
       !make_operand_map(&map_b, yp, a.N, Ke, BN / CL, a.f16, ystride))
     return cudaErrorInvalidValue;
   const TcKernelArgs k{map_a, map_b, map_c, a.C, a.ldc, a.M, a.N, (int)(Ke / BK), a.diag,
-                       valid, idesc, a.status, a.err, wait_ns, use_tma_store, vec_ok};
+                       valid, idesc, a.status, a.err, wait_ns, use_tma_store, vec_ok,
+                       (int)(Kp / BK), bstripe};
   cudaError_t e;
   if (a.lower)
     e = CL == 2 ? launch_kernel<true, 2>(k, valid, dev, st) : launch_kernel<true, 1>(k, valid, dev, st);
