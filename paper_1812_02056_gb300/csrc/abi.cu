@@ -359,9 +359,17 @@ gb_status chol_blocked_on(gb_handle *h, int64_t n, int64_t s, T *W, int64_t ld, 
     if (r != GB_OK) return r;
   }
   bool rest_pending = false;
+  // host input arriving in column slabs (h->cin): wait for slab k on `on`
+  auto slab_ready = [&](int64_t col, cudaStream_t on) -> gb_status {
+    if (!h->cin.active || col >= n) return GB_OK;
+    GB_CUDA_TRY(cudaStreamWaitEvent(on, h->ev_in[(size_t)(col / h->cin.s)], 0));
+    return GB_OK;
+  };
   for (int64_t z = 0; z < n; z += s) {
     const int64_t sb = std::min(s, n - z);
     const int64_t pe = z + sb;  // end of this s-block
+    gb_status rw = slab_ready(z, st);  // the s-block's columns have arrived
+    if (rw != GB_OK) return rw;
     for (int64_t j0 = z; j0 < pe; j0 += b) {
       const int bw = (int)std::min(b, pe - j0);
       const int64_t r0 = j0 + bw;
@@ -384,14 +392,41 @@ gb_status chol_blocked_on(gb_handle *h, int64_t n, int64_t s, T *W, int64_t ld, 
         if (r != GB_OK) return r;
       }
     }
+    if (h->cout.active) {
+      // columns [z, pe) are final (rows above z are zero): copy them out
+      GB_CUDA_TRY(cudaEventRecord(h->ev_cpy, st));
+      GB_CUDA_TRY(cudaStreamWaitEvent(h->cpy, h->ev_cpy, 0));
+      const auto &c = h->cout;
+      GB_CUDA_TRY(cudaMemcpy2DAsync((char *)c.host + z * c.esz, c.ldh * c.esz,
+                                    (const char *)c.dev + z * c.esz, c.ldd * c.esz, sb * c.esz, n,
+                                    cudaMemcpyDeviceToHost, h->cpy));
+    }
     if (pe >= n) break;
     // delayed rank-sb update A[pe.., pe..] -= R R^T, R = L[pe.., z..pe)
     const int64_t m = n - pe;
     const T *R = W + pe * ld + z;
+    // first block with host input still arriving: the trailing update in
+    // strips of one slab each (the lower part of columns [c, c + s), rows
+    // from c), each after its slab; every element still receives the same
+    // K-sum.  Later blocks find every slab in place.
+    const bool strips = h->cin.active && z == 0;
+    auto strip_update = [&](int64_t q, int slot, cudaStream_t on) -> gb_status {
+      for (int64_t c = q; c < n; c += s) {
+        gb_status r = slab_ready(c, on);
+        if (r != GB_OK) return r;
+        const int64_t w = std::min(s, n - c);
+        const T *Rc = W + c * ld + z;
+        r = chol_update<T>(h, dt, W + c * ld + c, Rc, Rc, ld, n - c, w, sb, status, slot, on);
+        if (r != GB_OK) return r;
+      }
+      return GB_OK;
+    };
     if (!la) {
       PhaseTimer t(h, st, GB_PHASE_UPDATE, update_flops(m, m, sb, true),
                    update_bytes(m, m, sb, true, e));
-      gb_status r = chol_update<T>(h, dt, W + pe * ld + pe, R, R, ld, m, m, sb, status, WS_PANEL, st);
+      gb_status r = strips ? strip_update(pe, WS_PANEL, st)
+                           : chol_update<T>(h, dt, W + pe * ld + pe, R, R, ld, m, m, sb, status,
+                                            WS_PANEL, st);
       if (r != GB_OK) return r;
       continue;
     }
@@ -401,7 +436,9 @@ gb_status chol_blocked_on(gb_handle *h, int64_t n, int64_t s, T *W, int64_t ld, 
     {
       PhaseTimer t(h, st, GB_PHASE_UPDATE, update_flops(m, nb, sb, true),
                    update_bytes(m, nb, sb, true, e));
-      gb_status r = chol_update<T>(h, dt, W + pe * ld + pe, R, R, ld, m, nb, sb, status, WS_PANEL, st);
+      gb_status r = slab_ready(pe, st);  // the next block's columns have arrived
+      if (r == GB_OK)
+        r = chol_update<T>(h, dt, W + pe * ld + pe, R, R, ld, m, nb, sb, status, WS_PANEL, st);
       if (r != GB_OK) return r;
     }
     const int64_t q = pe + nb;  // the rest: rows and columns from q on
@@ -411,8 +448,9 @@ gb_status chol_blocked_on(gb_handle *h, int64_t n, int64_t s, T *W, int64_t ld, 
       const T *Rq = W + q * ld + z;
       PhaseTimer t(h, h->aux, GB_PHASE_UPDATE, update_flops(n - q, n - q, sb, true),
                    update_bytes(n - q, n - q, sb, true, e));
-      gb_status r = chol_update<T>(h, dt, W + q * ld + q, Rq, Rq, ld, n - q, n - q, sb, status,
-                                   WS_PANEL2, h->aux);
+      gb_status r = strips ? strip_update(q, WS_PANEL2, h->aux)
+                           : chol_update<T>(h, dt, W + q * ld + q, Rq, Rq, ld, n - q, n - q, sb,
+                                            status, WS_PANEL2, h->aux);
       if (r != GB_OK) return r;
       GB_CUDA_TRY(cudaEventRecord(h->ev_rest, h->aux));
       rest_pending = true;
@@ -776,6 +814,49 @@ gb_status qr_common(gb_handle *h, int64_t n, int64_t s, gb_dtype dt, const void 
   return GB_OK;
 }
 
+// Host input for the right-looking Cholesky: on the copy stream, for each
+// column slab [q, q + s): its rows from q down go to the staging buffer, are
+// cast into the working matrix (zero above the slab's diagonal) and the rows
+// above q are zeroed; ev_in[k] marks slab k ready.  Only the lower triangle
+// crosses the link.  The factorization waits for each slab where it first
+// reads or updates it.
+gb_status slab_copy_in(gb_handle *h, gb_dtype dt, const void *A, int64_t lda, void *Ad,
+                       int64_t ldad, void *W, int64_t ldw, int64_t n, int64_t s, cudaStream_t st) {
+  const int64_t ns = (n + s - 1) / s;
+  while ((int64_t)h->ev_in.size() < ns) {
+    cudaEvent_t e = nullptr;
+    GB_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    h->ev_in.push_back(e);
+  }
+  const size_t ein = elem_size_input(dt), ef = elem_size_factor(dt);
+  GB_CUDA_TRY(cudaEventRecord(h->ev_cpy, st));  // after the staging allocations
+  GB_CUDA_TRY(cudaStreamWaitEvent(h->cpy, h->ev_cpy, 0));
+  for (int64_t k = 0; k < ns; ++k) {
+    const int64_t q = k * s, w = std::min(s, n - q);
+    const char *src = (const char *)A + ((size_t)q * lda + q) * ein;
+    char *dst = (char *)Ad + ((size_t)q * ldad + q) * ein;
+    GB_CUDA_TRY(cudaMemcpy2DAsync(dst, ldad * ein, src, lda * ein, w * ein, n - q,
+                                  cudaMemcpyHostToDevice, h->cpy));
+    cudaError_t e;
+    if (dt == GB_F64)
+      e = launch_copy_slab<double, double>((const double *)dst, ldad, (double *)W + q * ldw + q, ldw,
+                                           n - q, w, true, h->cpy);
+    else if (dt == GB_F32)
+      e = launch_copy_slab<float, float>((const float *)dst, ldad, (float *)W + q * ldw + q, ldw,
+                                         n - q, w, true, h->cpy);
+    else
+      e = launch_copy_slab<double, float>((const double *)dst, ldad, (float *)W + q * ldw + q, ldw,
+                                          n - q, w, true, h->cpy);
+    GB_CUDA_TRY(e);
+    if (q > 0)
+      GB_CUDA_TRY(cudaMemset2DAsync((char *)W + q * ef, ldw * ef, 0, w * ef, q, h->cpy));
+    GB_CUDA_TRY(cudaEventRecord(h->ev_in[(size_t)k], h->cpy));
+  }
+  h->cin.active = true;
+  h->cin.s = s;
+  return GB_OK;
+}
+
 gb_status factor_common(bool is_lu, gb_handle *h, int64_t n, int64_t s, gb_dtype dt,
                         const void *A, int64_t lda, void *L, int64_t ldl, int *info,
                         void *stream) {
@@ -818,24 +899,52 @@ gb_status factor_common(bool is_lu, gb_handle *h, int64_t n, int64_t s, gb_dtype
   if (r != GB_OK) return r;
   if (n == 0) return iw.finish(st);
 
+  // host input, Cholesky, right-looking loop, not in place: A goes in by
+  // column slabs while the factorization starts (slab_copy_in)
+  const bool left_mixed = !is_lu && is_mixed(dt) && h->left_looking && h->tc_update &&
+                          split_of(dt) == 1 && s % 64 == 0 && s < n && n % 8 == 0;
+  const bool stream_in = !is_lu && !left_mixed && !alias && !is_device_ptr(A) && h->cpy;
   Staged sa, sl;
   if (alias) {
     if ((r = sl.take(L, n, n, ldl, ef, true, true, st, h->stage_pool)) != GB_OK) return r;
     sa.dev = sl.dev;
     sa.ldd = sl.ldd;
   } else {
-    if ((r = sa.take(A, n, n, lda, ein, true, false, st, h->stage_pool)) != GB_OK) return r;
+    if ((r = sa.take(A, n, n, lda, ein, !stream_in, false, st, h->stage_pool)) != GB_OK) return r;
     if ((r = sl.take(L, n, n, ldl, ef, false, true, st, h->stage_pool)) != GB_OK) return r;
   }
   const int64_t ld = sl.ldd;
   const bool lower_only = !is_lu;
+  // host output, Cholesky, right-looking loop: stream the finished block
+  // columns out during the factorization instead of copying L at the end
+  struct CopyGuard {  // on any return: the staging buffers are freed on `st` after the copies
+    gb_handle *h;
+    cudaStream_t st;
+    ~CopyGuard() {
+      const bool copying = h->cin.active || h->cout.active;
+      h->cin.active = false;
+      h->cout.active = false;
+      if (!copying) return;
+      cudaEventRecord(h->ev_cpy, h->cpy);
+      cudaStreamWaitEvent(st, h->ev_cpy, 0);
+    }
+  } copy_guard{h, st};
+  if (!is_lu && !left_mixed && sl.host_dst && h->cpy) {
+    h->cout = {true, sl.host_dst, ldl, sl.dev, ld, n, ef};
+    GB_CUDA_TRY(cudaEventRecord(h->ev_cpy, st));  // the copy stream starts after the set-up
+    GB_CUDA_TRY(cudaStreamWaitEvent(h->cpy, h->ev_cpy, 0));
+  }
   std::unique_ptr<PhaseTimer> tcopy(new PhaseTimer(h, st, GB_PHASE_COPY, 0.0,
                                                    (double)n * n * (double)(ein + ef)));
+  if (stream_in) {
+    if ((r = slab_copy_in(h, dt, A, lda, sa.dev, sa.ldd, sl.dev, ld, n, s, st)) != GB_OK) return r;
+  }
   switch (dt) {
     case GB_F64: {
       double *W = (double *)sl.dev;
-      GB_CUDA_TRY((launch_copy_matrix<double, double>((const double *)sa.dev, sa.ldd, W, ld, n,
-                                                      lower_only, st)));
+      if (!stream_in)
+        GB_CUDA_TRY((launch_copy_matrix<double, double>((const double *)sa.dev, sa.ldd, W, ld, n,
+                                                        lower_only, st)));
       tcopy.reset();
       r = is_lu ? lu_blocked<double, double>(h, n, s, W, ld, iw.dev, dt, st)
                 : chol_blocked<double, double>(h, n, s, W, ld, iw.dev, dt, st);
@@ -843,8 +952,9 @@ gb_status factor_common(bool is_lu, gb_handle *h, int64_t n, int64_t s, gb_dtype
     }
     case GB_F32: {
       float *W = (float *)sl.dev;
-      GB_CUDA_TRY((launch_copy_matrix<float, float>((const float *)sa.dev, sa.ldd, W, ld, n,
-                                                    lower_only, st)));
+      if (!stream_in)
+        GB_CUDA_TRY((launch_copy_matrix<float, float>((const float *)sa.dev, sa.ldd, W, ld, n,
+                                                      lower_only, st)));
       tcopy.reset();
       r = is_lu ? lu_blocked<float, float>(h, n, s, W, ld, iw.dev, dt, st)
                 : chol_blocked<float, float>(h, n, s, W, ld, iw.dev, dt, st);
@@ -852,11 +962,11 @@ gb_status factor_common(bool is_lu, gb_handle *h, int64_t n, int64_t s, gb_dtype
     }
     default: {  // mixed: FP64 in, FP32 working matrix, FP64 diagonal blocks
       float *W = (float *)sl.dev;
-      GB_CUDA_TRY((launch_copy_matrix<double, float>((const double *)sa.dev, sa.ldd, W, ld, n,
-                                                     lower_only, st)));
+      if (!stream_in)
+        GB_CUDA_TRY((launch_copy_matrix<double, float>((const double *)sa.dev, sa.ldd, W, ld, n,
+                                                       lower_only, st)));
       tcopy.reset();
-      const bool left = !is_lu && h->left_looking && h->tc_update && split_of(dt) == 1 &&
-                        s % 64 == 0 && s < n && n % 8 == 0;
+      const bool left = left_mixed;
       r = is_lu  ? lu_blocked<float, double>(h, n, s, W, ld, iw.dev, dt, st)
           : left ? chol_left_on<float, double>(h, n, s, W, ld, iw.dev, dt, st)
                  : chol_blocked<float, double>(h, n, s, W, ld, iw.dev, dt, st);
@@ -864,6 +974,12 @@ gb_status factor_common(bool is_lu, gb_handle *h, int64_t n, int64_t s, gb_dtype
     }
   }
   if (r != GB_OK) return r;
+  if (h->cout.active) {  // every block column went out on the copy stream
+    h->cout.active = false;
+    sl.host_dst = nullptr;
+    GB_CUDA_TRY(cudaEventRecord(h->ev_cpy, h->cpy));
+    GB_CUDA_TRY(cudaStreamWaitEvent(st, h->ev_cpy, 0));
+  }
   if ((r = sl.finish()) != GB_OK) return r;
   if ((r = iw.finish(st)) != GB_OK) return r;
   if (sl.on_host() || sa.on_host()) GB_CUDA_TRY(cudaStreamSynchronize(st));
@@ -1119,7 +1235,9 @@ gb_status gb_create(gb_handle **out, int device) {
          cudaEventCreateWithFlags(&h->ev_next, cudaEventDisableTiming) == cudaSuccess &&
          cudaEventCreateWithFlags(&h->ev_rest, cudaEventDisableTiming) == cudaSuccess &&
          cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
-         cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) == cudaSuccess;
+         cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) == cudaSuccess &&
+         cudaStreamCreateWithFlags(&h->cpy, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&h->ev_cpy, cudaEventDisableTiming) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     gb_destroy(h);
@@ -1160,6 +1278,9 @@ gb_status gb_destroy(gb_handle *h) {
   if (h->ev_rest) cudaEventDestroy(h->ev_rest);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->ev_cpy) cudaEventDestroy(h->ev_cpy);
+  for (cudaEvent_t e : h->ev_in) cudaEventDestroy(e);
+  if (h->cpy) cudaStreamDestroy(h->cpy);
   if (h->hi) cudaStreamDestroy(h->hi);
   if (h->aux) cudaStreamDestroy(h->aux);
   if (h->stage_pool) cudaMemPoolDestroy(h->stage_pool);

@@ -85,6 +85,26 @@ struct gb_handle {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaEvent_t ev_next = nullptr;      // next block's columns updated (main stream)
   cudaEvent_t ev_rest = nullptr;      // rest of the update done (aux stream)
+  // Host-buffer Cholesky: each finished block column is copied to the host
+  // on `cpy` while the factorization goes on (set by factor_common)
+  cudaStream_t cpy = nullptr;
+  cudaEvent_t ev_cpy = nullptr;
+  // Host-input Cholesky: A arrives in column slabs of s columns (rows from
+  // the slab's first column down), each cast into W on `cpy`; slab k is
+  // ready when ev_in[k] completes (set by factor_common)
+  struct CopyIn {
+    bool active = false;
+    int64_t s = 0;
+  } cin;
+  std::vector<cudaEvent_t> ev_in;
+  struct CopyOut {
+    bool active = false;
+    void *host = nullptr;
+    int64_t ldh = 0;
+    const void *dev = nullptr;
+    int64_t ldd = 0, n = 0;
+    size_t esz = 0;
+  } cout;
   struct ProfRec {
     int phase;
     cudaEvent_t start, stop;
@@ -163,6 +183,11 @@ cudaError_t launch_update_strassen(T *C, int64_t ldc, const T *X, int64_t ldx, c
 template <typename Tin, typename Tout>
 cudaError_t launch_copy_matrix(const Tin *A, int64_t lda, Tout *W, int64_t ldw, int64_t n,
                                bool lower_only, cudaStream_t st);
+// rows x cols block (A's and W's pointers at its top-left corner), zero above
+// the block's own diagonal with lower_only
+template <typename Tin, typename Tout>
+cudaError_t launch_copy_slab(const Tin *A, int64_t lda, Tout *W, int64_t ldw, int64_t rows,
+                             int64_t cols, bool lower_only, cudaStream_t st);
 
 // tcgen05 mixed update (update_tc.cu).  Packs the panel to 16-bit operands and
 // runs the tensor-core kernel.  Returns cudaErrorNotSupported if the device

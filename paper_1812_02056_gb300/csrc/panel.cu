@@ -479,6 +479,19 @@ __global__ void copy_matrix_kernel(const Tin *__restrict__ A, int64_t lda, Tout 
   }
 }
 
+// rows x cols block of A into W, cast; with lower_only the entries above the
+// block's own diagonal (j > i) are zero
+template <typename Tin, typename Tout>
+__global__ void copy_slab_kernel(const Tin *__restrict__ A, int64_t lda, Tout *__restrict__ W,
+                                 int64_t ldw, int64_t rows, int64_t cols, int lower_only) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= cols) return;
+  for (int64_t i = blockIdx.y; i < rows; i += gridDim.y) {
+    Tout v = (!lower_only || j <= i) ? (Tout)A[i * lda + j] : Tout(0);
+    W[i * ldw + j] = v;
+  }
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ launchers
@@ -575,6 +588,22 @@ cudaError_t launch_copy_matrix(const Tin *A, int64_t lda, Tout *W, int64_t ldw, 
   count_launch();
   return cudaGetLastError();
 }
+
+template <typename Tin, typename Tout>
+cudaError_t launch_copy_slab(const Tin *A, int64_t lda, Tout *W, int64_t ldw, int64_t rows,
+                             int64_t cols, bool lower_only, cudaStream_t st) {
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  const dim3 block(256), grid((unsigned)((cols + 255) / 256), (unsigned)std::min<int64_t>(rows, 4096));
+  copy_slab_kernel<Tin, Tout><<<grid, block, 0, st>>>(A, lda, W, ldw, rows, cols, lower_only ? 1 : 0);
+  count_launch();
+  return cudaGetLastError();
+}
+template cudaError_t launch_copy_slab<double, double>(const double *, int64_t, double *, int64_t,
+                                                      int64_t, int64_t, bool, cudaStream_t);
+template cudaError_t launch_copy_slab<float, float>(const float *, int64_t, float *, int64_t,
+                                                    int64_t, int64_t, bool, cudaStream_t);
+template cudaError_t launch_copy_slab<double, float>(const double *, int64_t, float *, int64_t,
+                                                     int64_t, int64_t, bool, cudaStream_t);
 
 template cudaError_t launch_chol_panel<double>(double *, int64_t, int64_t, int, int64_t, int *, unsigned long long *, cudaStream_t);
 template cudaError_t launch_chol_panel<float>(float *, int64_t, int64_t, int, int64_t, int *, unsigned long long *, cudaStream_t);

@@ -165,6 +165,42 @@ def test_chol_host_buffers_match_device(h):
     assert np.array_equal(L, Ld)
 
 
+@pytest.mark.parametrize("dtype", ["f64", "f32", "mix_bf16", "mix_bf16x3"])
+@pytest.mark.parametrize("n,s", [(257, 64), (300, 200), (1000, 256), (1000, 1000), (2000, 128)])
+def test_chol_host_buffers_streamed_by_column_blocks(h, dtype, n, s):
+    """Host buffers: A goes in by column slabs (lower triangle only) while the
+    factorization starts, with the first trailing update in strips that wait
+    for their slab, and the finished block columns go out while it goes on.
+    The host L (padded pitch, filled with NaN) must hold the device-buffer
+    factor bit for bit, zeros above the diagonal, and untouched padding."""
+    from paper_1812_02056_gb300 import binding
+    dt = binding.DTYPES[dtype]
+    A = I.spd_gram(n, 17 + n)
+    Ain = A.astype(np.float32) if dtype == "f32" else A
+    fdt = np.float64 if dtype == "f64" else np.float32
+    ldl = n + 3
+    Lh = np.full((n, ldl), np.nan, dtype=fdt)
+    info = np.zeros(1, dtype=np.int32)
+    st = h.gb_chol_factor(n, s, dt, Ain, n, Lh, ldl, info)
+    assert st == 0 and info[0] == 0
+    Ad = torch.from_numpy(Ain).to(DEV)
+    Ld = torch.empty((n, n), dtype=torch.float64 if dtype == "f64" else torch.float32, device=DEV)
+    infod = torch.zeros(1, dtype=torch.int32, device=DEV)
+    assert h.gb_chol_factor(n, s, dt, Ad, n, Ld, n, infod) == 0
+    torch.cuda.synchronize()
+    assert np.array_equal(Lh[:, :n], Ld.cpu().numpy())
+    assert np.all(np.triu(Lh[:, :n], 1) == 0.0)
+    assert np.all(np.isnan(Lh[:, n:]))
+    # host input, device output (NaN in A's upper triangle is never read)
+    Au = Ain.copy()
+    Au[np.triu_indices(n, 1)] = np.nan
+    L2 = torch.full((n, n), float("nan"), dtype=Ld.dtype, device=DEV)
+    assert h.gb_chol_factor(n, s, dt, Au, n, L2, n, infod) == 0
+    torch.cuda.synchronize()
+    assert int(infod.item()) == 0
+    assert torch.equal(L2, Ld)
+
+
 def test_chol_breakdown_reports_column(h):
     n = 100
     A = I.spd_gram(n, 1)
