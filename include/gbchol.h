@@ -183,6 +183,24 @@ typedef enum gb_option {
                                step) in FP32 on the CUDA cores instead of the
                                tensor cores; the delayed rank-s updates stay
                                on the tensor cores.  Default 0.              */
+  GB_OPT_INNER_RECURSIVE = 13, /* 1: inside each s-block of gb_chol_factor,
+                               a column range wider than two inner steps is
+                               split in halves (multiples of the inner step):
+                               the left half is finished first, the right
+                               half then receives the whole left half in one
+                               product, then is finished the same way; 0: each
+                               inner block updates all the s-block's remaining
+                               columns.  The same sums, fewer and larger
+                               products.  2 (default): 1 for GB_F64 and the
+                               mixed dtypes, 0 for GB_F32.                   */
+  GB_OPT_INNER_LOOKAHEAD = 14 /* 1: inside each s-block of gb_chol_factor,
+                               each inner product goes first to the next
+                               inner block's columns (on the stream of the
+                               column steps) and to the rest of the range on
+                               a third stream, alongside the next column
+                               steps.  The same sums in the same order per
+                               element.  0 off, 2 (default): 1 for GB_F64
+                               only.                                         */
 } gb_option;
 
 gb_status gb_set_option(gb_handle *h, gb_option opt, int64_t value);
@@ -605,7 +623,9 @@ gb_status gb_batched_tune(gb_handle *h, gb_dtype dt, int64_t n_max, int *steps_o
  * the factorization of the n x n test matrix n I + ones in dtype dt for
  * s in {32, 64, 128, 256, 512, 1024} (below n) and inner steps {16, 32, 64}
  * (QR: {8, 16, 32}, the column-step width GB_OPT_QR_INNER_STEP), and keeps
- * the fastest pair in the handle for every order in [2^k, 2^(k+1)) with
+ * the fastest pair (a larger step replaces a smaller one only when it is at
+ * least 3% faster: the smaller step is at least as accurate) in the handle
+ * for every order in [2^k, 2^(k+1)) with
  * k = floor(log2 n).  Later calls with s = 0 in that range use the pair (the
  * inner step for that call only); without a tuned entry s = 0 keeps its
  * fixed default.  s_out and b_out (optional) receive the pair.  This is the

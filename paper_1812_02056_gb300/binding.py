@@ -41,6 +41,8 @@ GB_OPT_QR_INNER_STEP = 9
 GB_OPT_LEFT_LOOKING = 10
 GB_OPT_TEST_WITHHOLD = 11
 GB_OPT_INNER_CUDA_CORES = 12
+GB_OPT_INNER_RECURSIVE = 13
+GB_OPT_INNER_LOOKAHEAD = 14
 PEAKS = {"dfma": 0, "ffma": 1, "dmma": 2, "tc_bf16": 3, "tc_f16": 4, "tc_tf32": 5,
          "dfma_dmma": 6}
 

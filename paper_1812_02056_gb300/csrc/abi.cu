@@ -358,6 +358,11 @@ gb_status chol_blocked_on(gb_handle *h, int64_t n, int64_t s, T *W, int64_t ld, 
     if (r == GB_OK) r = ws_reserve(h, WS_PANEL2, pb, h->aux);
     if (r != GB_OK) return r;
   }
+  if (h->inner_lookahead == 1 && h->aux2 && is_mixed(dt) && h->tc_update) {
+    const size_t pb = tc_pack_bytes(n, n, std::min(s, n), false, split_of(dt));
+    gb_status r = ws_reserve(h, WS_INNER, pb, h->aux2);
+    if (r != GB_OK) return r;
+  }
   bool rest_pending = false;
   // host input arriving in column slabs (h->cin): wait for slab k on `on`
   auto slab_ready = [&](int64_t col, cudaStream_t on) -> gb_status {
@@ -370,27 +375,86 @@ gb_status chol_blocked_on(gb_handle *h, int64_t n, int64_t s, T *W, int64_t ld, 
     const int64_t pe = z + sb;  // end of this s-block
     gb_status rw = slab_ready(z, st);  // the s-block's columns have arrived
     if (rw != GB_OK) return rw;
-    for (int64_t j0 = z; j0 < pe; j0 += b) {
-      const int bw = (int)std::min(b, pe - j0);
-      const int64_t r0 = j0 + bw;
+    // mixed dtypes: the products inside the s-block on the tensor cores, or
+    // in FP32 on the CUDA cores (GB_OPT_INNER_CUDA_CORES)
+    const gb_dtype di = (is_mixed(dt) && h->inner_cuda_cores) ? GB_F32 : dt;
+    // Columns [c, hi) (rows from c down) receive the product of columns
+    // [k0, k0 + K) (rows from c down).  With GB_OPT_INNER_LOOKAHEAD the next
+    // inner block's columns receive it first, on the column-step stream, and
+    // the rest of the range on aux2 while the next column steps run; every
+    // later write to the range from `st` waits for that rest first.
+    // 2 (default): FP64 only (n = 8192: 1061.8 -> 1063.5 GFLOP/s; the mixed
+    // dtypes measured slower, their tensor-core rest competing with the
+    // column steps for SMs)
+    const bool ila = h->aux2 && (h->inner_lookahead == 1 ||
+                                 (h->inner_lookahead == 2 && dt == GB_F64));
+    bool inner_pending = false;
+    auto give = [&](int64_t c, int64_t hi, int64_t k0, int64_t K) -> gb_status {
+      const int64_t nb = ila ? std::min(b, hi - c) : hi - c;
+      if (inner_pending) GB_CUDA_TRY(cudaStreamWaitEvent(st, h->ev_ir, 0));
       {
-        // diagonal block and the rows below it
-        PhaseTimer t(h, st, GB_PHASE_PANEL,
-                     (double)bw * bw * bw / 3.0 + (double)(n - r0) * bw * bw,
-                     (double)bw * bw * e + 2.0 * (double)(n - r0) * bw * e);
-        GB_CUDA_TRY(launch_chol_panel<T>(W, ld, j0, bw, n - r0, status, h->d_arrivals, st));
-      }
-      if (r0 < pe) {  // the s-block's remaining columns receive this inner block
-        PhaseTimer t(h, st, GB_PHASE_INNER, update_flops(n - r0, pe - r0, bw, true),
-                     update_bytes(n - r0, pe - r0, bw, true, e));
-        const T *R = W + r0 * ld + j0;
-        // mixed dtypes: the skinny inner products (K <= 64) on the tensor
-        // cores, or in FP32 on the CUDA cores (GB_OPT_INNER_CUDA_CORES)
-        const gb_dtype di = (is_mixed(dt) && h->inner_cuda_cores) ? GB_F32 : dt;
-        gb_status r = chol_update<T>(h, di, W + r0 * ld + r0, R, R, ld, n - r0, pe - r0, bw,
-                                     status, WS_PANEL, st);
+        PhaseTimer t(h, st, GB_PHASE_INNER, update_flops(n - c, nb, K, true),
+                     update_bytes(n - c, nb, K, true, e));
+        const T *R = W + c * ld + k0;
+        gb_status r = chol_update<T>(h, di, W + c * ld + c, R, R, ld, n - c, nb, K, status,
+                                     WS_PANEL, st);
         if (r != GB_OK) return r;
       }
+      const int64_t c2 = c + nb;
+      if (c2 >= hi) return GB_OK;
+      GB_CUDA_TRY(cudaEventRecord(h->ev_ip, st));
+      GB_CUDA_TRY(cudaStreamWaitEvent(h->aux2, h->ev_ip, 0));
+      {
+        PhaseTimer t(h, h->aux2, GB_PHASE_INNER, update_flops(n - c2, hi - c2, K, true),
+                     update_bytes(n - c2, hi - c2, K, true, e));
+        const T *R = W + c2 * ld + k0;
+        gb_status r = chol_update<T>(h, di, W + c2 * ld + c2, R, R, ld, n - c2, hi - c2, K, status,
+                                     WS_INNER, h->aux2);
+        if (r != GB_OK) return r;
+      }
+      GB_CUDA_TRY(cudaEventRecord(h->ev_ir, h->aux2));
+      inner_pending = true;
+      return GB_OK;
+    };
+    // columns [lo, hi) of the s-block, all rows from lo down, given every
+    // earlier column's contribution: inner blocks of b columns, each giving
+    // its product to the range's remaining columns; with GB_OPT_INNER_RECURSIVE
+    // a range wider than two inner blocks is split in halves (multiples of
+    // b), the right half receiving the whole left half in one product.
+    auto flat = [&](int64_t lo, int64_t hi) -> gb_status {
+      for (int64_t j0 = lo; j0 < hi; j0 += b) {
+        const int bw = (int)std::min(b, hi - j0);
+        const int64_t r0 = j0 + bw;
+        {
+          // diagonal block and the rows below it
+          PhaseTimer t(h, st, GB_PHASE_PANEL,
+                       (double)bw * bw * bw / 3.0 + (double)(n - r0) * bw * bw,
+                       (double)bw * bw * e + 2.0 * (double)(n - r0) * bw * e);
+          GB_CUDA_TRY(launch_chol_panel<T>(W, ld, j0, bw, n - r0, status, h->d_arrivals, st));
+        }
+        if (r0 < hi) {  // the range's remaining columns receive this inner block
+          gb_status r = give(r0, hi, j0, bw);
+          if (r != GB_OK) return r;
+        }
+      }
+      return GB_OK;
+    };
+    // 2 (default): halves except for the FP32 dtype, whose CUDA-core inner
+    // updates measured faster flat (n = 8192: 10.23 against 10.40 ms)
+    const bool halves = h->inner_recursive == 1 || (h->inner_recursive == 2 && dt != GB_F32);
+    auto range = [&](auto &&self, int64_t lo, int64_t hi) -> gb_status {
+      if (!halves || hi - lo <= 2 * b) return flat(lo, hi);
+      const int64_t mid = lo + ((hi - lo) / 2 + b - 1) / b * b;
+      gb_status r = self(self, lo, mid);
+      if (r == GB_OK) r = give(mid, hi, lo, mid - lo);
+      if (r != GB_OK) return r;
+      return self(self, mid, hi);
+    };
+    {
+      gb_status r = range(range, z, pe);
+      if (r != GB_OK) return r;
+      // the block column is final: later readers of it on `st` see every write
+      if (inner_pending) GB_CUDA_TRY(cudaStreamWaitEvent(st, h->ev_ir, 0));
     }
     if (h->cout.active) {
       // columns [z, pe) are final (rows above z are zero): copy them out
@@ -1237,7 +1301,10 @@ gb_status gb_create(gb_handle **out, int device) {
          cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
          cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) == cudaSuccess &&
          cudaStreamCreateWithFlags(&h->cpy, cudaStreamNonBlocking) == cudaSuccess &&
-         cudaEventCreateWithFlags(&h->ev_cpy, cudaEventDisableTiming) == cudaSuccess;
+         cudaEventCreateWithFlags(&h->ev_cpy, cudaEventDisableTiming) == cudaSuccess &&
+         cudaStreamCreateWithPriority(&h->aux2, cudaStreamNonBlocking, prio_hi) == cudaSuccess &&
+         cudaEventCreateWithFlags(&h->ev_ip, cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&h->ev_ir, cudaEventDisableTiming) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     gb_destroy(h);
@@ -1279,6 +1346,9 @@ gb_status gb_destroy(gb_handle *h) {
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
   if (h->ev_cpy) cudaEventDestroy(h->ev_cpy);
+  if (h->ev_ip) cudaEventDestroy(h->ev_ip);
+  if (h->ev_ir) cudaEventDestroy(h->ev_ir);
+  if (h->aux2) cudaStreamDestroy(h->aux2);
   for (cudaEvent_t e : h->ev_in) cudaEventDestroy(e);
   if (h->cpy) cudaStreamDestroy(h->cpy);
   if (h->hi) cudaStreamDestroy(h->hi);
@@ -1318,6 +1388,14 @@ gb_status gb_set_option(gb_handle *h, gb_option opt, int64_t v) {
       h->test_withhold = (int)v;
       return GB_OK;
     case GB_OPT_INNER_CUDA_CORES: h->inner_cuda_cores = v ? 1 : 0; return GB_OK;
+    case GB_OPT_INNER_RECURSIVE:
+      if (v < 0 || v > 2) return -3;
+      h->inner_recursive = (int)v;
+      return GB_OK;
+    case GB_OPT_INNER_LOOKAHEAD:
+      if (v < 0 || v > 2) return -3;
+      h->inner_lookahead = (int)v;
+      return GB_OK;
     default: return -2;
   }
 }
@@ -1338,6 +1416,8 @@ gb_status gb_get_option(gb_handle *h, gb_option opt, int64_t *v) {
     case GB_OPT_LEFT_LOOKING: *v = h->left_looking; return GB_OK;
     case GB_OPT_TEST_WITHHOLD: *v = h->test_withhold; return GB_OK;
     case GB_OPT_INNER_CUDA_CORES: *v = h->inner_cuda_cores; return GB_OK;
+    case GB_OPT_INNER_RECURSIVE: *v = h->inner_recursive; return GB_OK;
+    case GB_OPT_INNER_LOOKAHEAD: *v = h->inner_lookahead; return GB_OK;
     default: return -2;
   }
 }
@@ -1768,7 +1848,11 @@ extern "C" gb_status gb_tune_step(gb_handle *h, int kind, gb_dtype dt, int64_t n
       int host_info = 0;
       if (r == GB_OK && cudaMemcpy(&host_info, info, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
         r = GB_ERR_CUDA;
-      if (r == GB_OK && host_info == 0 && ms < best) {
+      // steps ascend: a larger step must be 3% faster to replace a smaller
+      // one (the smaller step is at least as accurate, and for the mixed
+      // dtypes a less accurate factor can cost a refinement step)
+      const float need = (best_s == 0 || best_s == s) ? best : 0.97f * best;
+      if (r == GB_OK && host_info == 0 && ms < need) {
         best = ms;
         best_s = s;
         best_b = b;

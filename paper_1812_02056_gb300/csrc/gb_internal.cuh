@@ -58,6 +58,10 @@ struct gb_handle {
   int left_looking = 0;       // GB_OPT_LEFT_LOOKING
   int test_withhold = 0;      // GB_OPT_TEST_WITHHOLD (test hook, 0 = off)
   int inner_cuda_cores = 0;   // GB_OPT_INNER_CUDA_CORES
+  int inner_recursive = 2;    // GB_OPT_INNER_RECURSIVE
+  int inner_lookahead = 2;    // GB_OPT_INNER_LOOKAHEAD
+  cudaStream_t aux2 = nullptr;  // high priority: the inner updates' rest (inner look-ahead)
+  cudaEvent_t ev_ip = nullptr, ev_ir = nullptr;  // inner block's columns final / inner rest done
   // device copies of host buffers come from this pool, which keeps its
   // memory between calls (allocating and mapping it again each call costs
   // more than the copies)
@@ -74,7 +78,7 @@ struct gb_handle {
   unsigned long long *d_arrivals = nullptr;  // arrival counter of the fused panel kernel
   double *d_scalars = nullptr;  // small FP64 reduction outputs
   unsigned sync_epoch = 0;
-  gb::Workspace ws[10];      // named workspaces, see WS_* below
+  gb::Workspace ws[11];      // named workspaces, see WS_* below
   std::mutex mu;
   // GB_OPT_PROFILE: event pairs recorded around launches, read later
   int profile = 0;
@@ -132,7 +136,7 @@ struct gb_handle {
 namespace gb {
 
 enum { WS_STAGE = 0, WS_PANEL = 1, WS_SOLVE = 2, WS_MISC = 3, WS_DINV = 4, WS_PANEL2 = 5,
-       WS_STRAS = 6, WS_STRAS2 = 7, WS_QR = 8, WS_LEFT = 9 };
+       WS_STRAS = 6, WS_STRAS2 = 7, WS_QR = 8, WS_LEFT = 9, WS_INNER = 10 };
 constexpr int SYNC_WORDS = 1 << 16;
 
 // Make sure workspace `slot` holds >= bytes; waits for `stream` before

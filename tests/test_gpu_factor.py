@@ -319,3 +319,54 @@ def test_lu_inner_step(h, inner):
         h.set_option(binding.GB_OPT_INNER_STEP, 64)
     L, U = lu_split(LU)
     assert info == 0 and guarded_rel_err(L, Lo) <= 1e-10 and guarded_rel_err(U, Uo) <= 1e-10
+
+
+@pytest.mark.parametrize("rec", [0, 1])
+@pytest.mark.parametrize("n,s", [(1000, 512), (777, 300), (2048, 1024)])
+def test_inner_halves_and_flat_match_oracle(h, rec, n, s):
+    """GB_OPT_INNER_RECURSIVE: an s-block's columns finished in halves (the
+    right half receiving the whole left half in one product) or inner block
+    by inner block: FP64 against the oracle at the suite's tolerance, and the
+    mixed factor of an integer L0 L0^T exactly L0 either way."""
+    from paper_1812_02056_gb300 import binding
+    prev = h.get_option(binding.GB_OPT_INNER_RECURSIVE)
+    assert prev == 2  # the default
+    h.set_option(binding.GB_OPT_INNER_RECURSIVE, rec)
+    try:
+        A = I.spd_gram(n, 500 + n)
+        L, info = _chol(h, A, s)
+        assert info == 0
+        Lo, _ = oracle.chol(A, s)
+        assert guarded_rel_err(L, Lo) <= 1e-10
+        L0 = I.unit_lower_integer(n, 600 + n, -1, 1)
+        for dt in ("mix_bf16", "mix_bf16x3"):
+            Lm, info = _chol(h, L0 @ L0.T, s, dt)
+            assert info == 0 and np.array_equal(Lm, L0)
+    finally:
+        h.set_option(binding.GB_OPT_INNER_RECURSIVE, prev)
+    assert h.lib.gb_set_option(h.h, binding.GB_OPT_INNER_RECURSIVE, 3) == -3
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "mix_bf16", "mix_bf16x3"])
+@pytest.mark.parametrize("n,s", [(2000, 512), (1500, 256), (700, 1024)])
+def test_inner_lookahead_same_bits(h, dtype, n, s):
+    """GB_OPT_INNER_LOOKAHEAD splits each product inside an s-block into the
+    next inner block's columns and the rest of the range, on two streams:
+    every element receives the same sums in the same order, so the factor is
+    the same bits with and without it (and matches the oracle)."""
+    from paper_1812_02056_gb300 import binding
+    A = I.spd_gram(n, 900 + n)
+    assert h.get_option(binding.GB_OPT_INNER_LOOKAHEAD) == 2  # the default: FP64 only
+    try:
+        h.set_option(binding.GB_OPT_INNER_LOOKAHEAD, 0)
+        L0, info0 = _chol(h, A, s, dtype)
+        h.set_option(binding.GB_OPT_INNER_LOOKAHEAD, 1)
+        L1, info1 = _chol(h, A, s, dtype)
+    finally:
+        h.set_option(binding.GB_OPT_INNER_LOOKAHEAD, 2)
+    assert h.lib.gb_set_option(h.h, binding.GB_OPT_INNER_LOOKAHEAD, 3) == -3
+    assert info0 == 0 and info1 == 0
+    assert np.array_equal(L0, L1)
+    if dtype == "f64":
+        Lo, _ = oracle.chol(A, s)
+        assert guarded_rel_err(L1, Lo) <= 1e-10
