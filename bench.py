@@ -373,11 +373,13 @@ def run_ours(args):
             dst.copy_(src, non_blocking=True)
             torch.cuda.synchronize()
             link[name] = (time.perf_counter() - c0) * 1e3
-        # the library sends A's lower triangle only, in column slabs of s
-        # columns (rows from the slab's first column down), and L whole
-        h2d = sum((n - q) * min(s, n - q) for q in range(0, n, s)) * esz
+        # the library moves the lower triangle only, in column slabs of s
+        # columns (rows from the slab's first column down), both ways; the
+        # zeros above are written on the host
+        tri = sum((n - q) * min(s, n - q) for q in range(0, n, s))
         e2e = {"value": world * esteps * flops / el / 1e9, "unit": UNIT,
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": n * n * L.element_size() + 4,
+               "h2d_bytes_per_step": tri * esz,
+               "d2h_bytes_per_step": tri * L.element_size() + 4,
                "steps": esteps, "ms_per_step": el / esteps * 1e3,
                "link_full_matrix_copy_ms": link}
         del Ah, Lh

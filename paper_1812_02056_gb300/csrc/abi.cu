@@ -460,10 +460,12 @@ gb_status chol_blocked_on(gb_handle *h, int64_t n, int64_t s, T *W, int64_t ld, 
       // columns [z, pe) are final (rows above z are zero): copy them out
       GB_CUDA_TRY(cudaEventRecord(h->ev_cpy, st));
       GB_CUDA_TRY(cudaStreamWaitEvent(h->cpy, h->ev_cpy, 0));
+      // rows from z down (the zeros above the block column are written on
+      // the host by factor_common)
       const auto &c = h->cout;
-      GB_CUDA_TRY(cudaMemcpy2DAsync((char *)c.host + z * c.esz, c.ldh * c.esz,
-                                    (const char *)c.dev + z * c.esz, c.ldd * c.esz, sb * c.esz, n,
-                                    cudaMemcpyDeviceToHost, h->cpy));
+      GB_CUDA_TRY(cudaMemcpy2DAsync((char *)c.host + (z * c.ldh + z) * c.esz, c.ldh * c.esz,
+                                    (const char *)c.dev + (z * c.ldd + z) * c.esz, c.ldd * c.esz,
+                                    sb * c.esz, n - z, cudaMemcpyDeviceToHost, h->cpy));
     }
     if (pe >= n) break;
     // delayed rank-sb update A[pe.., pe..] -= R R^T, R = L[pe.., z..pe)
@@ -1038,6 +1040,16 @@ gb_status factor_common(bool is_lu, gb_handle *h, int64_t n, int64_t s, gb_dtype
     }
   }
   if (r != GB_OK) return r;
+  if (h->cout.active) {
+    // while the device works: the zeros above each row's block column, in
+    // the host buffer (the copy stream sends only rows from each block
+    // column's first row down)
+    const auto &c = h->cout;
+    for (int64_t i = 0; i < n; ++i) {
+      const int64_t j0 = (i / s + 1) * s;
+      if (j0 < n) memset((char *)c.host + (i * c.ldh + j0) * c.esz, 0, (size_t)(n - j0) * c.esz);
+    }
+  }
   if (h->cout.active) {  // every block column went out on the copy stream
     h->cout.active = false;
     sl.host_dst = nullptr;
