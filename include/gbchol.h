@@ -193,7 +193,7 @@ typedef enum gb_option {
                                columns.  The same sums, fewer and larger
                                products.  2 (default): 1 for GB_F64 and the
                                mixed dtypes, 0 for GB_F32.                   */
-  GB_OPT_INNER_LOOKAHEAD = 14 /* 1: inside each s-block of gb_chol_factor,
+  GB_OPT_INNER_LOOKAHEAD = 14, /* 1: inside each s-block of gb_chol_factor,
                                each inner product goes first to the next
                                inner block's columns (on the stream of the
                                column steps) and to the rest of the range on
@@ -201,6 +201,12 @@ typedef enum gb_option {
                                steps.  The same sums in the same order per
                                element.  0 off, 2 (default): 1 for GB_F64
                                only.                                         */
+  GB_OPT_EARLY_REST = 15      /* 1: with look-ahead, the rest of each s-block's
+                               delayed update (the columns after the next
+                               s-block) starts as soon as the s-block is
+                               factored, alongside the update of the next
+                               s-block's columns; 0: after that update.  The
+                               same sums.  2 (default): 1 for GB_F64 only.   */
 } gb_option;
 
 gb_status gb_set_option(gb_handle *h, gb_option opt, int64_t value);

@@ -497,6 +497,17 @@ gb_status chol_blocked_on(gb_handle *h, int64_t n, int64_t s, T *W, int64_t ld, 
       continue;
     }
     const int64_t nb = std::min(s, n - pe);  // width of the next s-block
+    const int64_t q = pe + nb;  // the rest: rows and columns from q on
+    // GB_OPT_EARLY_REST: the rest of this update needs only this block's
+    // columns, not the next block's update: start it first, alongside that
+    // update.  2 (default): FP64 only (n = 8192, s = 256: 172.2 -> 170.1 ms;
+    // the FP32 and mixed dtypes measured 4-8% slower, the narrow update on
+    // the critical path sharing the SMs with the rest)
+    const bool early = q < n && (h->early_rest == 1 || (h->early_rest == 2 && dt == GB_F64));
+    if (early) {
+      GB_CUDA_TRY(cudaEventRecord(h->ev_next, st));
+      GB_CUDA_TRY(cudaStreamWaitEvent(h->aux, h->ev_next, 0));
+    }
     // the previous rest-update wrote the next block's columns: wait for it
     if (rest_pending) GB_CUDA_TRY(cudaStreamWaitEvent(st, h->ev_rest, 0));
     {
@@ -507,10 +518,11 @@ gb_status chol_blocked_on(gb_handle *h, int64_t n, int64_t s, T *W, int64_t ld, 
         r = chol_update<T>(h, dt, W + pe * ld + pe, R, R, ld, m, nb, sb, status, WS_PANEL, st);
       if (r != GB_OK) return r;
     }
-    const int64_t q = pe + nb;  // the rest: rows and columns from q on
     if (q < n) {
-      GB_CUDA_TRY(cudaEventRecord(h->ev_next, st));
-      GB_CUDA_TRY(cudaStreamWaitEvent(h->aux, h->ev_next, 0));
+      if (!early) {
+        GB_CUDA_TRY(cudaEventRecord(h->ev_next, st));
+        GB_CUDA_TRY(cudaStreamWaitEvent(h->aux, h->ev_next, 0));
+      }
       const T *Rq = W + q * ld + z;
       PhaseTimer t(h, h->aux, GB_PHASE_UPDATE, update_flops(n - q, n - q, sb, true),
                    update_bytes(n - q, n - q, sb, true, e));
@@ -1408,6 +1420,10 @@ gb_status gb_set_option(gb_handle *h, gb_option opt, int64_t v) {
       if (v < 0 || v > 2) return -3;
       h->inner_lookahead = (int)v;
       return GB_OK;
+    case GB_OPT_EARLY_REST:
+      if (v < 0 || v > 2) return -3;
+      h->early_rest = (int)v;
+      return GB_OK;
     default: return -2;
   }
 }
@@ -1430,6 +1446,7 @@ gb_status gb_get_option(gb_handle *h, gb_option opt, int64_t *v) {
     case GB_OPT_INNER_CUDA_CORES: *v = h->inner_cuda_cores; return GB_OK;
     case GB_OPT_INNER_RECURSIVE: *v = h->inner_recursive; return GB_OK;
     case GB_OPT_INNER_LOOKAHEAD: *v = h->inner_lookahead; return GB_OK;
+    case GB_OPT_EARLY_REST: *v = h->early_rest; return GB_OK;
     default: return -2;
   }
 }

@@ -60,6 +60,7 @@ struct gb_handle {
   int inner_cuda_cores = 0;   // GB_OPT_INNER_CUDA_CORES
   int inner_recursive = 2;    // GB_OPT_INNER_RECURSIVE
   int inner_lookahead = 2;    // GB_OPT_INNER_LOOKAHEAD
+  int early_rest = 2;         // GB_OPT_EARLY_REST
   cudaStream_t aux2 = nullptr;  // high priority: the inner updates' rest (inner look-ahead)
   cudaEvent_t ev_ip = nullptr, ev_ir = nullptr;  // inner block's columns final / inner rest done
   // device copies of host buffers come from this pool, which keeps its

@@ -79,3 +79,28 @@ def test_library_and_oracle_are_independent(lib):
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "oracle.c" not in text, f
+
+
+def header_constants():
+    """Every `GB_NAME = value` enumerator and `#define GB_NAME (value)` of the
+    header, comments removed."""
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    consts = {k: int(v) for k, v in re.findall(r"\b(GB_[A-Z0-9_]+)\s*=\s*(-?\d+)", text)}
+    consts.update({k: int(v) for k, v in
+                   re.findall(r"#define\s+(GB_[A-Z0-9_]+)\s+\(?(-?\d+)\)?", text)})
+    return consts
+
+
+def test_binding_constants_match_the_header():
+    from paper_1812_02056_gb300 import binding
+    consts = header_constants()
+    opts = {k: v for k, v in consts.items() if k.startswith(("GB_OPT_", "GB_ERR_"))}
+    assert len([k for k in opts if k.startswith("GB_OPT_")]) >= 15
+    for k, v in opts.items():
+        assert getattr(binding, k) == v, k
+    for name in ("GB_F64", "GB_F32", "GB_MIX_BF16", "GB_MIX_F16", "GB_MIX_BF16X3"):
+        assert getattr(binding, name) == consts[name], name
+    peaks = {k: v for k, v in consts.items() if k.startswith("GB_PEAK_")}
+    assert sorted(binding.PEAKS.values()) == sorted(peaks.values())
+    for kind, v in binding.PEAKS.items():
+        assert consts["GB_PEAK_" + kind.upper()] == v, kind

@@ -370,3 +370,28 @@ def test_inner_lookahead_same_bits(h, dtype, n, s):
     if dtype == "f64":
         Lo, _ = oracle.chol(A, s)
         assert guarded_rel_err(L1, Lo) <= 1e-10
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "mix_bf16x3"])
+@pytest.mark.parametrize("n,s", [(2000, 512), (1500, 256), (1100, 128)])
+def test_early_rest_same_bits(h, dtype, n, s):
+    """GB_OPT_EARLY_REST starts the rest of each delayed update (the columns
+    after the next s-block) before the next s-block's own update: the two
+    write disjoint columns and read only finished ones, so the factor is the
+    same bits either way (and matches the oracle)."""
+    from paper_1812_02056_gb300 import binding
+    A = I.spd_gram(n, 1300 + n)
+    assert h.get_option(binding.GB_OPT_EARLY_REST) == 2  # the default: FP64 only
+    try:
+        h.set_option(binding.GB_OPT_EARLY_REST, 0)
+        L0, info0 = _chol(h, A, s, dtype)
+        h.set_option(binding.GB_OPT_EARLY_REST, 1)
+        L1, info1 = _chol(h, A, s, dtype)
+    finally:
+        h.set_option(binding.GB_OPT_EARLY_REST, 2)
+    assert h.lib.gb_set_option(h.h, binding.GB_OPT_EARLY_REST, 3) == -3
+    assert info0 == 0 and info1 == 0
+    assert np.array_equal(L0, L1)
+    if dtype == "f64":
+        Lo, _ = oracle.chol(A, s)
+        assert guarded_rel_err(L1, Lo) <= 1e-10
