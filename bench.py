@@ -623,6 +623,27 @@ def run_mixed(args):
                "factor_gflops": n ** 3 / 3 / (fm * 1e-3) / 1e9,
                "factor_phase_ms": {k: round(v["ms"], 3) for k, v in prof.items()},
                "factor_phase_launches": {k: v["launches"] for k, v in prof.items()}}
+        if name != "f64":
+            # the residual's method (GB_OPT_RESIDUAL), and the same solve with
+            # the FP64 residual on the CUDA cores for comparison
+            mode = h.get_option(binding.GB_OPT_RESIDUAL)
+            digits = mode == 1 or (mode == 2 and n >= 2048)
+            res["residual"] = "tensor-core digit products" if digits else "fp64 cuda cores"
+            h.set_option(binding.GB_OPT_RESIDUAL, 0)
+            X0 = torch.empty_like(B)
+            torch.cuda.synchronize()
+            e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+            e1.record(stream)
+            st0, stats0 = h.gb_chol_solve(n, nrhs, dt, L, n, A, n, B, nrhs, X0, nrhs, 1e-14, 50,
+                                          stream)
+            e2.record(stream)
+            torch.cuda.synchronize()
+            h.set_option(binding.GB_OPT_RESIDUAL, mode)
+            res["with_fp64_residual"] = {"solve_ms": e1.elapsed_time(e2),
+                                         "time_to_solution_ms": fm + e1.elapsed_time(e2),
+                                         "status": st0, "ir_iterations": stats0.iterations,
+                                         "eta": stats0.eta}
+            del X0
         Xh = X.double()
         R = B - A @ Xh
         den = A.abs().sum(1).max() * Xh.abs().max(0).values + B.abs().max(0).values

@@ -201,12 +201,28 @@ typedef enum gb_option {
                                steps.  The same sums in the same order per
                                element.  0 off, 2 (default): 1 for GB_F64
                                only.                                         */
-  GB_OPT_EARLY_REST = 15      /* 1: with look-ahead, the rest of each s-block's
+  GB_OPT_EARLY_REST = 15,     /* 1: with look-ahead, the rest of each s-block's
                                delayed update (the columns after the next
                                s-block) starts as soon as the s-block is
                                factored, alongside the update of the next
                                s-block's columns; 0: after that update.  The
                                same sums.  2 (default): 1 for GB_F64 only.   */
+  GB_OPT_RESIDUAL = 16        /* method of the FP64 residual r = B - A X of
+                               refinement and gb_residual.  0: FP64
+                               multiply-adds on the CUDA cores.  1: exact
+                               digit products on the tensor cores: each row
+                               of A and column of X is scaled by a power of
+                               two and cut into 11 digits of 5 bits (BF16
+                               planes; a truncation below 2^-55 of the row's
+                               or column's largest magnitude), the 76 digit
+                               pairs that matter are multiplied with exact
+                               FP32 accumulation, and the pair sums are
+                               combined in FP64; per term the error is below
+                               one FP64 rounding of the row's largest
+                               product.  Needs 22 n^2 bytes of workspace (the
+                               digits of A, made once per solve call); 0 is
+                               used when that cannot be had.  2 (default): 1
+                               for n >= 2048, else 0.                        */
 } gb_option;
 
 gb_status gb_set_option(gb_handle *h, gb_option opt, int64_t value);
@@ -335,6 +351,20 @@ gb_status gb_lu_solve(gb_handle *h, int64_t n, int64_t nrhs, gb_dtype factor_dt,
                       int64_t ldlu, const double *A, int64_t lda, const double *B, int64_t ldb,
                       double *X, int64_t ldx, const gb_refine_opts *opts, gb_solve_stats *stats,
                       void *stream);
+
+/*
+ * gb_residual -- R = B - A X in FP64 accuracy, the residual step of
+ * iterative refinement that gb_chol_solve and gb_lu_solve run when given
+ * A, by the method GB_OPT_RESIDUAL selects.  A n x n (lda), X and B
+ * n x nrhs (ldx, ldb), R n x nrhs (ldr); all double, row-major, device
+ * pointers; nrhs <= 1365.  With `eta` non-NULL writes
+ * max_c ||r_c||_inf / (||A||_inf ||x_c||_inf + ||b_c||_inf) there (Inf when
+ * anything is not finite).  Waits for the stream.  Returns GB_ERR_TIMEOUT
+ * if a bounded device wait of the tensor-core method expired.
+ */
+gb_status gb_residual(gb_handle *h, int64_t n, int64_t nrhs, const double *A, int64_t lda,
+                      const double *X, int64_t ldx, const double *B, int64_t ldb, double *R,
+                      int64_t ldr, double *eta, void *stream);
 
 /* --------------------------------------------------- the rank-s update */
 /*

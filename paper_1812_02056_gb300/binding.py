@@ -44,6 +44,7 @@ GB_OPT_INNER_CUDA_CORES = 12
 GB_OPT_INNER_RECURSIVE = 13
 GB_OPT_INNER_LOOKAHEAD = 14
 GB_OPT_EARLY_REST = 15
+GB_OPT_RESIDUAL = 16
 PEAKS = {"dfma": 0, "ffma": 1, "dmma": 2, "tc_bf16": 3, "tc_f16": 4, "tc_tf32": 5,
          "dfma_dmma": 6}
 
@@ -104,6 +105,8 @@ SIGNATURES = {
                            ctypes.POINTER(RefineOpts), ctypes.POINTER(SolveStats), _P]),
     "gb_backward_error": (_I32, [_P, _I32, _I64, _I32, _P, _I64, _P, _I64,
                                  ctypes.POINTER(_D), _P]),
+    "gb_residual": (_I32, [_P, _I64, _I64, _P, _I64, _P, _I64, _P, _I64, _P, _I64,
+                           ctypes.POINTER(_D), _P]),
     "gb_chol_factor_batched": (_I32, [_P, _I64, _P, _P, _P, _P, _P, _I32, _I64, _P, _P]),
     "gb_batched_plan": (_I32, [_P, _I64, _P, _P, _P, _P, _P, _I32, _I64, _P]),
     "gb_lu_factor_batched": (_I32, [_P, _I64, _P, _P, _P, _P, _P, _I32, _I64, _P, _P]),
@@ -308,6 +311,14 @@ class Handle:
         check(self.lib.gb_backward_error(self.h, int(is_lu), n, dt, _ptr(A), lda, _ptr(F), ldf,
                                          ctypes.byref(out), _stream_ptr(stream)),
               "gb_backward_error")
+        return out.value
+
+    def gb_residual(self, n, nrhs, A, lda, X, ldx, B, ldb, R, ldr, stream=None) -> float:
+        """R = B - A X (device buffers); returns the normwise backward error."""
+        out = ctypes.c_double()
+        check(self.lib.gb_residual(self.h, n, nrhs, _ptr(A), lda, _ptr(X), ldx, _ptr(B), ldb,
+                                   _ptr(R), ldr, ctypes.byref(out), _stream_ptr(stream)),
+              "gb_residual")
         return out.value
 
     def gb_chol_factor_batched(self, count, n_arr, a_arr, lda_arr, l_arr, ldl_arr, dt, s, info,

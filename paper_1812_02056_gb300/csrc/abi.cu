@@ -1133,6 +1133,58 @@ gb_status read_device_error(gb_handle *h, cudaStream_t st) {
   return GB_OK;
 }
 
+// The residual r = b - A x of refinement (GB_OPT_RESIDUAL): digit products
+// on the tensor cores (residual_tc.cu) when chosen and its workspace can be
+// had, else FP64 on the CUDA cores.  Both compute ||A||_inf into
+// h->d_scalars[0] here, and per call the norms of r, x and b into
+// h->d_scalars[1..3 nrhs].
+bool split_residual(const gb_handle *h, int64_t n) {
+  if (h->residual == 0 || n <= 0) return false;
+  if (h->residual == 2 && n < SPLIT_RESIDUAL_MIN_N) return false;
+  return tc_supported(h->device);
+}
+
+struct ResidualPlan {
+  double *R = nullptr;       // n x nrhs (row-major, ld nrhs)
+  void *work = nullptr;      // partial sums (FP64) or the digits of x (split)
+  size_t work_bytes = 0;
+  const void *awork = nullptr;  // the digits of A and row scales (split)
+};
+
+gb_status residual_prepare(gb_handle *h, const double *A, int64_t lda, int64_t n, int64_t nrhs,
+                           ResidualPlan &rp, cudaStream_t st) {
+  if ((size_t)(1 + 3 * nrhs) > 4096) return GB_ERR_UNSUPPORTED;
+  if (split_residual(h, n) && ws_reserve(h, WS_SPLIT, split_a_bytes(n), st) == GB_OK)
+    rp.awork = h->ws[WS_SPLIT].ptr;
+  const size_t rbytes = ((size_t)n * nrhs * 8 + 255) / 256 * 256;
+  rp.work_bytes = rp.awork ? split_x_bytes(n, nrhs, h->sm_count)
+                           : residual_work_bytes(n, nrhs, h->sm_count);
+  gb_status r = ws_reserve(h, WS_SOLVE, rbytes + rp.work_bytes, st);
+  if (r != GB_OK) return r;
+  rp.R = (double *)h->ws[WS_SOLVE].ptr;
+  rp.work = rp.work_bytes ? (char *)h->ws[WS_SOLVE].ptr + rbytes : nullptr;
+  double *norms = h->d_scalars;
+  if (rp.awork) GB_CUDA_TRY(launch_split_a(A, lda, n, const_cast<void *>(rp.awork), norms, st));
+  else GB_CUDA_TRY(launch_inf_norm_rows(A, lda, n, norms, st));
+  return GB_OK;
+}
+
+gb_status residual_run(gb_handle *h, const ResidualPlan &rp, const double *A, int64_t lda,
+                       const double *X, int64_t ldx, const double *B, int64_t ldb, int64_t n,
+                       int64_t nrhs, cudaStream_t st) {
+  double *norms = h->d_scalars + 1;
+  if (rp.awork) {
+    // a launch takes milliseconds; one second bounds every single wait
+    const long long wait_ns = std::min<long long>((long long)h->spin_limit * 100LL, 1000000000LL);
+    GB_CUDA_TRY(launch_residual_split(rp.awork, n, X, ldx, B, ldb, rp.R, nrhs, nrhs, norms,
+                                      rp.work, h->sm_count, h->d_err, wait_ns, st));
+  } else {
+    GB_CUDA_TRY(launch_residual(A, lda, X, ldx, B, ldb, rp.R, nrhs, n, nrhs, norms,
+                                (double *)rp.work, rp.work_bytes, h->sm_count, st));
+  }
+  return GB_OK;
+}
+
 template <typename Tf>
 gb_status solve_common(bool is_lu, gb_handle *h, int64_t n, int64_t nrhs, const Tf *F,
                        int64_t ldf, const double *A, int64_t lda, const double *B, int64_t ldb,
@@ -1162,20 +1214,15 @@ gb_status solve_common(bool is_lu, gb_handle *h, int64_t n, int64_t nrhs, const 
   if (!A) return read_device_error(h, st);
 
   // iterative refinement in FP64
-  const size_t rbytes = (size_t)n * nrhs * 8;
-  const size_t pbytes = residual_work_bytes(n, nrhs, h->sm_count);
-  if ((r = ws_reserve(h, WS_SOLVE, rbytes + pbytes, st)) != GB_OK) return r;
-  double *R = (double *)h->ws[WS_SOLVE].ptr;
-  double *P = pbytes ? R + (size_t)n * nrhs : nullptr;
+  ResidualPlan rp;
+  if ((r = residual_prepare(h, A, lda, n, nrhs, rp, st)) != GB_OK) return r;
+  double *R = rp.R;
   double *norms = h->d_scalars;  // [0]: ||A||_inf; [1..]: 3 * nrhs norms
-  if ((size_t)(1 + 3 * nrhs) > 4096) return GB_ERR_UNSUPPORTED;
-  GB_CUDA_TRY(launch_inf_norm_rows(A, lda, n, norms, st));
   std::vector<double> hn(1 + 3 * nrhs);
   int it = 0;
   double eta = 0.0;
   for (;;) {
-    GB_CUDA_TRY(launch_residual(A, lda, X, ldx, B, ldb, R, nrhs, n, nrhs, norms + 1, P, pbytes,
-                                h->sm_count, st));
+    if ((r = residual_run(h, rp, A, lda, X, ldx, B, ldb, n, nrhs, st)) != GB_OK) return r;
     GB_CUDA_TRY(cudaMemcpyAsync(hn.data(), norms, sizeof(double) * hn.size(),
                                 cudaMemcpyDeviceToHost, st));
     int errw = 0;  // an expired device wait ends the refinement at once
@@ -1424,6 +1471,10 @@ gb_status gb_set_option(gb_handle *h, gb_option opt, int64_t v) {
       if (v < 0 || v > 2) return -3;
       h->early_rest = (int)v;
       return GB_OK;
+    case GB_OPT_RESIDUAL:
+      if (v < 0 || v > 2) return -3;
+      h->residual = (int)v;
+      return GB_OK;
     default: return -2;
   }
 }
@@ -1447,6 +1498,7 @@ gb_status gb_get_option(gb_handle *h, gb_option opt, int64_t *v) {
     case GB_OPT_INNER_RECURSIVE: *v = h->inner_recursive; return GB_OK;
     case GB_OPT_INNER_LOOKAHEAD: *v = h->inner_lookahead; return GB_OK;
     case GB_OPT_EARLY_REST: *v = h->early_rest; return GB_OK;
+    case GB_OPT_RESIDUAL: *v = h->residual; return GB_OK;
     default: return -2;
   }
 }
@@ -1510,6 +1562,49 @@ gb_status gb_backward_error(gb_handle *h, int is_lu, int64_t n, gb_dtype factor_
   GB_CUDA_TRY(cudaMemcpyAsync(acc, h->d_scalars, sizeof acc, cudaMemcpyDeviceToHost, st));
   GB_CUDA_TRY(cudaStreamSynchronize(st));
   *out = acc[1] > 0 ? std::sqrt(acc[0] / acc[1]) : 0.0;
+  return GB_OK;
+}
+
+gb_status gb_residual(gb_handle *h, int64_t n, int64_t nrhs, const double *A, int64_t lda,
+                      const double *X, int64_t ldx, const double *B, int64_t ldb, double *R,
+                      int64_t ldr, double *eta, void *stream) {
+  if (!h) return -1;
+  if (n < 0) return -2;
+  if (nrhs < 0 || nrhs > 1365) return -3;
+  if (n > 0 && (!A || !is_device_ptr(A))) return -4;
+  if (lda < std::max<int64_t>(1, n)) return -5;
+  const bool work = n > 0 && nrhs > 0;
+  if (work && (!X || !is_device_ptr(X))) return -6;
+  if (ldx < std::max<int64_t>(1, nrhs)) return -7;
+  if (work && (!B || !is_device_ptr(B))) return -8;
+  if (ldb < std::max<int64_t>(1, nrhs)) return -9;
+  if (work && (!R || !is_device_ptr(R))) return -10;
+  if (ldr < std::max<int64_t>(1, nrhs)) return -11;
+  DeviceGuard g(h->device);
+  std::lock_guard<std::mutex> lk(h->mu);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (eta) *eta = 0.0;
+  if (!work) return GB_OK;
+  ResidualPlan rp;
+  gb_status r = residual_prepare(h, A, lda, n, nrhs, rp, st);
+  if (r != GB_OK) return r;
+  if ((r = residual_run(h, rp, A, lda, X, ldx, B, ldb, n, nrhs, st)) != GB_OK) return r;
+  GB_CUDA_TRY(cudaMemcpy2DAsync(R, ldr * 8, rp.R, nrhs * 8, nrhs * 8, n, cudaMemcpyDeviceToDevice,
+                                st));
+  std::vector<double> hn(1 + 3 * nrhs);
+  GB_CUDA_TRY(cudaMemcpyAsync(hn.data(), h->d_scalars, sizeof(double) * hn.size(),
+                              cudaMemcpyDeviceToHost, st));
+  if ((r = read_device_error(h, st)) != GB_OK) return r;
+  if (eta) {
+    double e = 0.0;
+    for (int64_t c = 0; c < nrhs; ++c) {
+      const double den = hn[0] * hn[1 + nrhs + c] + hn[1 + 2 * nrhs + c];
+      double ec = den > 0 ? hn[1 + c] / den : (hn[1 + c] > 0 ? INFINITY : 0.0);
+      if (!std::isfinite(ec) || !std::isfinite(den)) ec = INFINITY;
+      e = std::max(e, ec);
+    }
+    *eta = e;
+  }
   return GB_OK;
 }
 

@@ -61,6 +61,7 @@ struct gb_handle {
   int inner_recursive = 2;    // GB_OPT_INNER_RECURSIVE
   int inner_lookahead = 2;    // GB_OPT_INNER_LOOKAHEAD
   int early_rest = 2;         // GB_OPT_EARLY_REST
+  int residual = 2;           // GB_OPT_RESIDUAL
   cudaStream_t aux2 = nullptr;  // high priority: the inner updates' rest (inner look-ahead)
   cudaEvent_t ev_ip = nullptr, ev_ir = nullptr;  // inner block's columns final / inner rest done
   // device copies of host buffers come from this pool, which keeps its
@@ -79,7 +80,7 @@ struct gb_handle {
   unsigned long long *d_arrivals = nullptr;  // arrival counter of the fused panel kernel
   double *d_scalars = nullptr;  // small FP64 reduction outputs
   unsigned sync_epoch = 0;
-  gb::Workspace ws[11];      // named workspaces, see WS_* below
+  gb::Workspace ws[12];      // named workspaces, see WS_* below
   std::mutex mu;
   // GB_OPT_PROFILE: event pairs recorded around launches, read later
   int profile = 0;
@@ -137,7 +138,8 @@ struct gb_handle {
 namespace gb {
 
 enum { WS_STAGE = 0, WS_PANEL = 1, WS_SOLVE = 2, WS_MISC = 3, WS_DINV = 4, WS_PANEL2 = 5,
-       WS_STRAS = 6, WS_STRAS2 = 7, WS_QR = 8, WS_LEFT = 9, WS_INNER = 10 };
+       WS_STRAS = 6, WS_STRAS2 = 7, WS_QR = 8, WS_LEFT = 9, WS_INNER = 10,
+       WS_SPLIT = 11 };
 constexpr int SYNC_WORDS = 1 << 16;
 
 // Make sure workspace `slot` holds >= bytes; waits for `stream` before
@@ -266,6 +268,21 @@ cudaError_t launch_residual(const double *A, int64_t lda, const double *X, int64
 size_t residual_work_bytes(int64_t n, int64_t nrhs, int sm_count);
 cudaError_t launch_inf_norm_rows(const double *A, int64_t lda, int64_t n, double *out,
                                  cudaStream_t st);
+// The same residual from exact digit products on the tensor cores
+// (residual_tc.cu): launch_split_a writes A's digit planes and row scales to
+// `work` (split_a_bytes) and ||A||_inf to *anorm; launch_residual_split then
+// computes r = b - A x with the norms of r, x and b (as launch_residual),
+// using `xwork` (split_x_bytes) for the digits of x and partial sums.
+// GB_OPT_RESIDUAL 2 (default): the digit products from this order up
+constexpr int64_t SPLIT_RESIDUAL_MIN_N = 2048;
+size_t split_a_bytes(int64_t n);
+size_t split_x_bytes(int64_t n, int64_t nrhs, int sm_count);
+cudaError_t launch_split_a(const double *A, int64_t lda, int64_t n, void *work, double *anorm,
+                           cudaStream_t st);
+cudaError_t launch_residual_split(const void *awork, int64_t n, const double *X, int64_t ldx,
+                                  const double *B, int64_t ldb, double *R, int64_t ldr,
+                                  int64_t nrhs, double *norms, void *xwork, int sm_count, int *err,
+                                  long long wait_ns, cudaStream_t st);
 cudaError_t launch_axpy_cols(double *X, int64_t ldx, const double *D, int64_t ldd, int64_t n,
                              int64_t nrhs, cudaStream_t st);
 template <typename Tf>

@@ -47,7 +47,8 @@ int64_t served_step(int64_t n, gb_dtype dt) {
 
 // Device bytes a job holds while it runs: the FP64 copy of A (refinement or
 // host input), the factor, right-hand sides and solution, the refinement
-// residual and the packed tensor-core operands.
+// residual (with the digit planes of its tensor-core method) and the packed
+// tensor-core operands.
 // Leading dimension of a job's factor buffer: a multiple of 64 elements, so
 // that every row starts on a 256-byte boundary and the tensor-core update's
 // epilogue can reduce into it with TMA (its row pitch must be a multiple of
@@ -60,7 +61,11 @@ size_t footprint(const gb_request &r) {
   const size_t s = (size_t)served_step(r.n, r.dtype);
   const size_t planes = r.dtype == GB_MIX_BF16X3 ? 6 : 1;
   const size_t pack = (r.dtype >= GB_MIX_BF16) ? 2 * n * ((s + 63) / 64 * 64) * 2 * planes : 0;
-  return 8 * n * n + fac + 3 * 8 * n * k + pack + (8u << 20);
+  // refinement's residual by digit products (the default from this order)
+  const size_t split = (r.dtype != GB_F64 && r.n >= SPLIT_RESIDUAL_MIN_N)
+                           ? split_a_bytes(r.n) + split_x_bytes(r.n, r.nrhs, 1024)
+                           : 0;
+  return 8 * n * n + fac + 3 * 8 * n * k + pack + split + (8u << 20);
 }
 
 }  // namespace
