@@ -21,7 +21,7 @@
 // holds exactly (and the tensor cores' FP32 accumulation keeps exactly), so
 // each S_pq is exact.  Then
 //   (A x)_ic ~= sigma_i tau_c sum_{p+q<=RT} 2^{-RW (p+q+2)} S_pq[i][c]
-// summed in FP64, smallest pairs first.  Per term j the truncations and the
+// summed in FP64, smallest scales first.  Per term j the truncations and the
 // dropped pairs (p + q > RT) are below 2^-53.7 sigma_i tau_c: within one
 // FP64 rounding of the largest product of the row, where the plain FP64
 // product carries one rounding of u = 2^-53 per product plus the rounding of
@@ -32,7 +32,8 @@
 // the 16 x 64 digit planes of x per stage, 128-byte swizzle), warp 1 issues
 // tcgen05.mma.kind::f16 (M = 128, N = 16 x the x planes a digit of A pairs
 // with) into a 512-column FP32 accumulator in tensor memory, warps 2..5 read
-// it back (tcgen05.ld) and accumulate in FP64.  The 76 pairs need 1216
+// it back (tcgen05.ld), sum the pairs of one scale exactly in int32 and
+// accumulate the scaled sums in FP64.  The 76 pairs need 1216
 // accumulator columns, so the digits of A go in four passes of at most three
 // (512, 384, 240 and 80 columns), the smallest first.  A K range longer than
 // 2^14 (or a small grid) is split over CTAs whose FP64 partial sums are added
@@ -386,8 +387,9 @@ __global__ void __launch_bounds__(RTHREADS, 1)
     const int qd = warp & 3;  // tensor-memory lane quarter this warp may read
     const int64_t row = (int64_t)m0 + qd * 32 + lane;
     double acc[RBN];
+    float chk[RBN];
 #pragma unroll
-    for (int c = 0; c < RBN; ++c) acc[c] = 0.0;
+    for (int c = 0; c < RBN; ++c) acc[c] = 0.0, chk[c] = 0.0f;
     bool ok = true;
 #pragma unroll
     for (int k = 0; k < NPASS; ++k) {
@@ -397,26 +399,41 @@ __global__ void __launch_bounds__(RTHREADS, 1)
       }
       tc_fence_after();
       const int p0 = pass_first(k), np = pass_count(k);
-      // smallest pairs first: digits of A from the last, x digits from the last
+      // Pairs of one scale t = p + q (at most one per digit of the pass)
+      // are summed exactly in int32 (each |S| < 2^24), then scaled into the
+      // FP64 sum: smallest scales first.  `chk` carries a NaN or Inf of a
+      // non-finite input through (the integer sums cannot).
+#pragma unroll 1
+      for (int t = RT; t >= p0; --t) {
+        int32_t si[RBN];
+        bool any = false;
 #pragma unroll
-      for (int j = RMAXP - 1; j >= 0; --j) {
-        if (j >= np) continue;
-        const int p = p0 + j;
-#pragma unroll
-        for (int q = RP - 1; q >= 0; --q) {
-          if (q >= nq_of(p)) continue;
+        for (int j = 0; j < RMAXP; ++j) {
+          const int p = p0 + j, q = t - p;
+          if (j >= np || q < 0 || q >= nq_of(p)) continue;
           float v[RBN];
           tmem_ld_32x16(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(col_of(k, j) + q * RBN), v);
-          const double sc = pow2_neg(RW * (p + q + 2));
 #pragma unroll
-          for (int c = 0; c < RBN; ++c) acc[c] = fma((double)v[c], sc, acc[c]);
+          for (int c = 0; c < RBN; ++c) {
+            const int32_t iv = __float2int_rn(v[c]);
+            si[c] = any ? si[c] + iv : iv;
+            chk[c] += v[c];
+          }
+          any = true;
         }
+        if (!any) continue;
+        const double sc = pow2_neg(RW * (t + 2));
+#pragma unroll
+        for (int c = 0; c < RBN; ++c) acc[c] = fma((double)si[c], sc, acc[c]);
       }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(acc_empty);
     }
     if (ok && !*abort_flag) {
+#pragma unroll
+      for (int c = 0; c < RBN; ++c)
+        if (!(fabsf(chk[c]) <= 3.4e38f)) acc[c] = (double)chk[c];  // NaN or Inf through
       const int cols = (int)min64(RBN, nrhs - c0);
       if (P) {
         if (row < n) {
