@@ -207,7 +207,7 @@ typedef enum gb_option {
                                factored, alongside the update of the next
                                s-block's columns; 0: after that update.  The
                                same sums.  2 (default): 1 for GB_F64 only.   */
-  GB_OPT_RESIDUAL = 16        /* method of the FP64 residual r = B - A X of
+  GB_OPT_RESIDUAL = 16,       /* method of the FP64 residual r = B - A X of
                                refinement and gb_residual.  0: FP64
                                multiply-adds on the CUDA cores.  1: exact
                                digit products on the tensor cores: each row
@@ -223,6 +223,22 @@ typedef enum gb_option {
                                digits of A, made once per solve call); 0 is
                                used when that cannot be had.  2 (default): 1
                                for n >= 2048, else 0.                        */
+  GB_OPT_F64_UPDATE = 17      /* GB_F64 delayed and inner updates (C -= R R^T
+                               of gb_chol_factor, and gb_rank_update with
+                               lower = 1 and y_is_kxn = 0).  0 (default):
+                               FP64 multiply-adds on the CUDA cores.  1: FP64
+                               accuracy from exact digit products on the
+                               tensor cores: each row of R is scaled by a
+                               power of two and cut into 11 digits of 5 bits
+                               (BF16 planes), the 76 digit pairs of the 12
+                               scales that matter are multiplied with exact
+                               FP32 accumulation (K taken in pieces of at
+                               most 1024), the scales are combined exactly in
+                               integers and the result is subtracted from C
+                               in FP64.  Per term the error is below one FP64
+                               rounding of the row scales' product; the
+                               FP64 multiply-add update rounds at every
+                               term.  Workspace 22 n s bytes per stream.     */
 } gb_option;
 
 gb_status gb_set_option(gb_handle *h, gb_option opt, int64_t value);

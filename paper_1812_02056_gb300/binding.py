@@ -45,6 +45,7 @@ GB_OPT_INNER_RECURSIVE = 13
 GB_OPT_INNER_LOOKAHEAD = 14
 GB_OPT_EARLY_REST = 15
 GB_OPT_RESIDUAL = 16
+GB_OPT_F64_UPDATE = 17
 PEAKS = {"dfma": 0, "ffma": 1, "dmma": 2, "tc_bf16": 3, "tc_f16": 4, "tc_tf32": 5,
          "dfma_dmma": 6}
 

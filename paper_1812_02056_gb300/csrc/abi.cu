@@ -279,6 +279,18 @@ gb_status chol_update(gb_handle *h, gb_dtype dt, T *C, const T *X, const T *Y, i
                       int64_t M, int64_t N, int64_t K, int *status, int pack_slot,
                       cudaStream_t st) {
   if (M <= 0 || N <= 0 || K <= 0) return GB_OK;
+  if constexpr (sizeof(T) == 8) {
+    if (dt == GB_F64 && h->f64_update == 1 && tc_supported(h->device)) {
+      // FP64 accuracy from exact digit products on the tensor cores
+      const bool same = X == Y && N <= M;
+      gb_status ws = ws_reserve(h, pack_slot, update_digits_bytes(M, N, K, same), st);
+      if (ws != GB_OK) return ws;
+      GB_CUDA_TRY(launch_update_digits(C, ld, X, ld, Y, ld, M, N, K, status, h->d_err,
+                                       h->spin_limit, h->ws[pack_slot].ptr,
+                                       h->ws[pack_slot].bytes, h->sm_count, st));
+      return GB_OK;
+    }
+  }
   if constexpr (sizeof(T) == 4) {
     if (is_mixed(dt) && h->tc_update) {
       TcUpdateArgs a{};
@@ -361,6 +373,15 @@ gb_status chol_blocked_on(gb_handle *h, int64_t n, int64_t s, T *W, int64_t ld, 
   if (h->inner_lookahead == 1 && h->aux2 && is_mixed(dt) && h->tc_update) {
     const size_t pb = tc_pack_bytes(n, n, std::min(s, n), false, split_of(dt));
     gb_status r = ws_reserve(h, WS_INNER, pb, h->aux2);
+    if (r != GB_OK) return r;
+  }
+  if (dt == GB_F64 && h->f64_update == 1) {
+    // the digit workspaces of every stream at their largest before anything
+    // is in flight (a later growth would free a buffer another stream uses)
+    const size_t db = update_digits_bytes(n, n, std::min(s, n), true);
+    gb_status r = ws_reserve(h, WS_PANEL, db, st);
+    if (r == GB_OK && la) r = ws_reserve(h, WS_PANEL2, db, h->aux);
+    if (r == GB_OK && h->aux2) r = ws_reserve(h, WS_INNER, db, h->aux2);
     if (r != GB_OK) return r;
   }
   bool rest_pending = false;
@@ -618,6 +639,18 @@ gb_status lu_update(gb_handle *h, gb_dtype dt, T *C, const T *X, const T *Y, int
                     int64_t M, int64_t N, int64_t K, int *status, int pack_slot,
                     cudaStream_t st) {
   if (M <= 0 || N <= 0 || K <= 0) return GB_OK;
+  if constexpr (sizeof(T) == 8) {
+    if (dt == GB_F64 && h->f64_update == 1 && tc_supported(h->device)) {
+      // FP64 accuracy from exact digit products on the tensor cores
+      const bool same = X == Y && N <= M;
+      gb_status ws = ws_reserve(h, pack_slot, update_digits_bytes(M, N, K, same), st);
+      if (ws != GB_OK) return ws;
+      GB_CUDA_TRY(launch_update_digits(C, ld, X, ld, Y, ld, M, N, K, status, h->d_err,
+                                       h->spin_limit, h->ws[pack_slot].ptr,
+                                       h->ws[pack_slot].bytes, h->sm_count, st));
+      return GB_OK;
+    }
+  }
   if constexpr (sizeof(T) == 4) {
     if (is_mixed(dt) && h->tc_update) {
       TcUpdateArgs a{};
@@ -1475,6 +1508,10 @@ gb_status gb_set_option(gb_handle *h, gb_option opt, int64_t v) {
       if (v < 0 || v > 2) return -3;
       h->residual = (int)v;
       return GB_OK;
+    case GB_OPT_F64_UPDATE:
+      if (v < 0 || v > 1) return -3;
+      h->f64_update = (int)v;
+      return GB_OK;
     default: return -2;
   }
 }
@@ -1499,6 +1536,7 @@ gb_status gb_get_option(gb_handle *h, gb_option opt, int64_t *v) {
     case GB_OPT_INNER_LOOKAHEAD: *v = h->inner_lookahead; return GB_OK;
     case GB_OPT_EARLY_REST: *v = h->early_rest; return GB_OK;
     case GB_OPT_RESIDUAL: *v = h->residual; return GB_OK;
+    case GB_OPT_F64_UPDATE: *v = h->f64_update; return GB_OK;
     default: return -2;
   }
 }
@@ -2059,6 +2097,14 @@ extern "C" gb_status gb_rank_update(gb_handle *h, gb_dtype dt, int lower, int y_
     gb_status r = general_update<float>(h, (float *)C, ldc, (const float *)X, ldx,
                                         (const float *)Y, ldy, M, N, K, nn, status, WS_STRAS, st);
     if (r != GB_OK) return r;
+  } else if (dt == GB_F64 && h->f64_update == 1 && !nn && tc_supported(h->device)) {
+    const bool same = X == Y && ldx == ldy && N <= M;
+    gb_status r = ws_reserve(h, WS_PANEL, update_digits_bytes(M, N, K, same), st);
+    if (r != GB_OK) return r;
+    GB_CUDA_TRY(launch_update_digits((double *)C, ldc, (const double *)X, ldx, (const double *)Y,
+                                     ldy, M, N, K, status, h->d_err, h->spin_limit,
+                                     h->ws[WS_PANEL].ptr, h->ws[WS_PANEL].bytes, h->sm_count,
+                                     st));
   } else if (dt == GB_F64) {
     GB_CUDA_TRY(launch_update_simt<double>((double *)C, ldc, (const double *)X, ldx,
                                            (const double *)Y, ldy, M, N, K, nn, lower != 0, 0,

@@ -1,0 +1,398 @@
+// The delayed rank-s update of Algorithm 1 in FP64 (arXiv:1812.02056,
+// Sec. 2: "A -= S, S = R R^T") to FP64 accuracy on the tensor cores:
+//   C (FP64) -= X Y^T     (lower: j <= i; X M x K, Y N x K, K-major rows)
+// from exact products of the operands' digits (digits.cuh): row i of X is
+// cut into RP = 11 signed 5-bit digits a_p[i][.] at scale 2^e_i, row j of Y
+// likewise (b_q[j][.], 2^f_j), and
+//   (X Y^T)_ij ~= 2^(e_i + f_j) sum_{t = 0..UT} 2^(-5 (t + 2)) D_t[i][j],
+//   D_t = sum_{p + q = t} a_p b_q^T.
+// Every digit product is an integer below 2^10; a D_t sums at most 11 pairs
+// over K <= UK_MAX = 1024 terms, so every partial sum is an integer below
+// 11 * 1024 * 961 < 2^24 and the tensor cores' FP32 accumulation keeps it
+// exactly.  The twelve D_t of a tile are combined exactly in two 64-bit
+// integers, converted to FP64 and subtracted from C (two roundings).  Per
+// term of K the truncation of both operands (below 2^-55 of their row
+// scales) and the dropped pairs (t > UT) stay below one FP64 rounding of
+// 2^(e_i + f_j); the plain FP64 update rounds at every one of its K
+// multiply-adds.
+//
+// Kernel: persistent CTAs over the valid 128 x 32 output tiles (lower
+// trapezoid, dealt round-robin).  Warp 0 is the TMA producer (2-stage ring;
+// a stage holds up to three 128 x 64 digit planes of X and the 32 x 64
+// digit planes of Y they pair with, 128-byte swizzle), warp 1 issues
+// tcgen05.mma.kind::f16 (M = 128, N = 32, K = 16) into twelve 32-column
+// FP32 accumulators in tensor memory, one per scale t, and warps 2..5 read
+// them back (tcgen05.ld), fold them into two exact 64-bit integers per
+// element and update C.  The digits of X go in four passes of at most three
+// planes over the tile's K range (smallest digits first); all passes
+// accumulate into the same twelve accumulators.  Every mbarrier wait is
+// bounded; a failed column step (`status`) or an expired wait skips the
+// work.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "digits.cuh"
+#include "gb_internal.cuh"
+#include "tc_ptx.cuh"
+
+namespace gb {
+namespace {
+
+using namespace tc;
+using namespace dg;
+
+constexpr int UT = 11;                   // scales kept: p + q <= UT
+constexpr int UG = UT + 1;               // accumulators (scales 0..UT)
+constexpr int UBM = 128, UBN = 32, UBK = 64;
+constexpr int USTAGES = 2;
+constexpr int UMAXP = 3;                 // digit planes of X per pass
+constexpr uint32_t UA_SLOT = UBM * UBK * 2;  // 16 KiB
+constexpr uint32_t UB_SLOT = UBN * UBK * 2;  // 4 KiB
+constexpr uint32_t USTAGE = UMAXP * UA_SLOT + RP * UB_SLOT;  // 92 KiB
+constexpr size_t USMEM = (size_t)USTAGES * USTAGE + 1024 + 256;
+constexpr int UTHREADS = 192;
+constexpr uint32_t UTMEM_COLS = 512;     // twelve 32-column accumulators (384) fit
+constexpr int UNPASS = 4;
+constexpr int64_t UK_MAX = 1024;         // K per launch: D_t partial sums below 2^24
+static_assert(USMEM <= 232448, "shared memory per CTA");
+static_assert(UG * UBN <= (int)UTMEM_COLS, "accumulators fit tensor memory");
+
+__host__ __device__ constexpr int unq_of(int p) { return UT + 1 - p < RP ? UT + 1 - p : RP; }
+__host__ __device__ constexpr int upass_first(int k) { return k == 0 ? 9 : k == 1 ? 6 : k == 2 ? 3 : 0; }
+__host__ __device__ constexpr int upass_count(int k) { return k == 0 ? 2 : 3; }
+
+// Digits of the rows of X (M x K, ldx): planes[p][i][k] (row pitch kp), and
+// the row scale exponents.  One warp per row; lane l converts columns
+// 2l, 2l + 1, 2l + 64, ... (two digits per 4-byte store).
+__global__ void digits_rows_kernel(const double *__restrict__ X, int64_t ldx, int64_t M,
+                                   int64_t K, uint16_t *__restrict__ planes, int64_t kp,
+                                   int64_t pstride, int *__restrict__ rexp, const int *status) {
+  if (status && *reinterpret_cast<const volatile int *>(status) != 0) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  if (i >= M) return;
+  const double *row = X + i * ldx;
+  constexpr unsigned long long ABS = 0x7fffffffffffffffull;
+  unsigned long long mx = 0;
+  for (int64_t k = lane; k < K; k += 32) {
+    const unsigned long long a = (unsigned long long)__double_as_longlong(row[k]) & ABS;
+    mx = a > mx ? a : mx;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long m2 = __shfl_xor_sync(0xffffffffu, mx, o);
+    mx = m2 > mx ? m2 : mx;
+  }
+  const int e = scale_exp(__longlong_as_double((long long)mx));
+  if (lane == 0) rexp[i] = e;
+  uint16_t *dst = planes + i * kp;
+  for (int64_t k = 2 * lane; k < K; k += 64) {
+    uint32_t d[RP];
+    digits2(row[k], k + 1 < K ? row[k + 1] : 0.0, e, d);
+    if (k + 1 < K) {  // kp even, k even: 4-byte aligned
+#pragma unroll
+      for (int p = 0; p < RP; ++p) *reinterpret_cast<uint32_t *>(dst + p * pstride + k) = d[p];
+    } else {
+#pragma unroll
+      for (int p = 0; p < RP; ++p) dst[p * pstride + k] = (uint16_t)(d[p] & 0xffffu);
+    }
+  }
+}
+
+// The valid tiles of the lower trapezoid (M x N, j <= i), row tiles of UBM
+// rows holding min(ntj, 4 bi + 4) column tiles of UBN, counted row by row;
+// index v goes to the CTA v mod gridDim.x.
+struct UTileIter {
+  int64_t v, total, ntj, bi, base;
+  __device__ int64_t count(int64_t b) const {
+    const int64_t c = (b * UBM + UBM - 1) / UBN + 1;
+    return c < ntj ? c : ntj;
+  }
+  __device__ bool next(int64_t &m0, int64_t &n0) {
+    if (v >= total) return false;
+    while (v >= base + count(bi)) {
+      base += count(bi);
+      ++bi;
+    }
+    m0 = bi * UBM;
+    n0 = (v - base) * UBN;
+    v += gridDim.x;
+    return true;
+  }
+};
+
+__global__ void __launch_bounds__(UTHREADS, 1)
+    update_digits_kernel(const __grid_constant__ CUtensorMap map_a,
+                         const __grid_constant__ CUtensorMap map_b, const int *__restrict__ ea,
+                         const int *__restrict__ eb, double *__restrict__ C, int64_t ldc,
+                         int64_t M, int64_t N, int nkb, int64_t total, const int *status, int *err,
+                         long long wait_ns) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + USTAGES * USTAGE);
+  uint64_t *empty = full + USTAGES;
+  uint64_t *acc_full = empty + USTAGES;
+  uint64_t *acc_empty = acc_full + 1;
+  uint64_t *drain = acc_empty + 1;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+  volatile int *skip = abort_flag + 1;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < USTAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(acc_full, 1);
+    mbar_init(acc_empty, 4);  // the four epilogue warps
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    // skip the work after a failed column step or an expired wait
+    *skip = (*reinterpret_cast<const volatile int *>(status) != 0 ||
+             (*reinterpret_cast<const volatile int *>(err) & DEV_ERR_TIMEOUT))
+                ? 1
+                : 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc<1>(tmem_slot, UTMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const unsigned long long deadline = (unsigned long long)wait_ns;
+  const int64_t ntj = (N + UBN - 1) / UBN;
+  UTileIter it{(int64_t)blockIdx.x, total, ntj, 0, 0};
+  int64_t m0 = 0, n0 = 0;
+
+  if (*skip) {
+    // nothing issued: straight to the teardown
+  } else if (warp == 0) {
+    // ------------------------------------------------ TMA producer
+    if (lane == 0) {
+      uint32_t g = 0;
+      bool ok = true;
+      while (ok && it.next(m0, n0)) {
+#pragma unroll
+        for (int k = 0; k < UNPASS; ++k) {
+          const int p0 = upass_first(k), np = upass_count(k), nb = unq_of(p0);
+          const uint32_t bytes = np * UA_SLOT + nb * UB_SLOT;
+          for (int kb = 0; ok && kb < nkb; ++kb, ++g) {
+            const uint32_t s = g % USTAGES, ph = (g / USTAGES) & 1u;
+            if (g >= (uint32_t)USTAGES && !mbar_wait(&empty[s], ph ^ 1u, deadline, err, abort_flag)) {
+              ok = false;
+              break;
+            }
+            uint8_t *st = smem + s * USTAGE;
+            mbar_expect_tx(&full[s], bytes);
+            for (int j = 0; j < np; ++j)
+              tma_load_3d(st + j * UA_SLOT, &map_a, &full[s], kb * UBK, (int)m0, p0 + j);
+            for (int q = 0; q < nb; ++q)
+              tma_load_3d(st + UMAXP * UA_SLOT + q * UB_SLOT, &map_b, &full[s], kb * UBK, (int)n0, q);
+          }
+        }
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      // FP32 accumulator, BF16 A and B, both K-major, N = 32, M = 128
+      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(UBN >> 3) << 17) |
+                             ((uint32_t)(UBM >> 4) << 24);
+      uint32_t g = 0, i = 0;
+      bool ok = true;
+      while (ok && it.next(m0, n0)) {
+        if (i > 0 && !mbar_wait(acc_empty, (i - 1) & 1u, deadline, err, abort_flag)) break;
+        tc_fence_after();
+        uint32_t started = 0;  // accumulators written in this tile
+#pragma unroll
+        for (int k = 0; k < UNPASS; ++k) {
+          const int p0 = upass_first(k), np = upass_count(k);
+          for (int kb = 0; ok && kb < nkb; ++kb, ++g) {
+            const uint32_t s = g % USTAGES, ph = (g / USTAGES) & 1u;
+            if (!mbar_wait(&full[s], ph, deadline, err, abort_flag)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t st = smem_u32(smem + s * USTAGE);
+            const uint32_t b0 = st + UMAXP * UA_SLOT;
+#pragma unroll
+            for (int j = 0; j < UMAXP; ++j) {
+              if (j >= np) break;
+              const int p = p0 + j;
+              const uint32_t a0 = st + j * UA_SLOT;
+              for (int q = 0; q < unq_of(p); ++q) {
+                const int t = p + q;
+                const uint32_t d = tmem + (uint32_t)(t * UBN);
+                const uint32_t bq = b0 + q * UB_SLOT;
+#pragma unroll
+                for (int kk = 0; kk < UBK / 16; ++kk) {
+                  mma_f16<1>(d, sw128_desc(a0 + kk * 32), sw128_desc(bq + kk * 32), idesc,
+                             (started >> t) & 1u);
+                  started |= 1u << t;
+                }
+              }
+            }
+            mma_commit(&empty[s]);
+          }
+        }
+        if (!ok) break;
+        mma_commit(acc_full);
+        ++i;
+      }
+      mma_commit(drain);
+      const unsigned long long until = now_ns() + deadline;
+      while (!mbar_try_wait(drain, 0)) {
+        if (now_ns() > until) {
+          atomicOr(err, DEV_ERR_TIMEOUT);
+          break;
+        }
+      }
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------ epilogue (warps 2..5)
+    const int qd = warp & 3;  // tensor-memory lane quarter this warp may read
+    uint32_t i = 0;
+    while (it.next(m0, n0)) {
+      if (!mbar_wait(acc_full, i & 1u, deadline, err, abort_flag)) break;
+      tc_fence_after();
+      const int64_t row = m0 + qd * 32 + lane;
+      const int e_i = row < M ? ea[row] : 0;
+#pragma unroll 1
+      for (int h = 0; h < UBN / 16; ++h) {
+        // D_0..D_5 and D_6..D_11 folded exactly: hi = sum S_t 2^(5 (5 - t)),
+        // lo = sum S_t 2^(5 (11 - t)), each below 2^50
+        long long hi[16], lo[16];
+        float chk[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) hi[c] = 0, lo[c] = 0, chk[c] = 0.0f;
+#pragma unroll
+        for (int t = 0; t < UG; ++t) {
+          float v[16];
+          tmem_ld_32x16(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(t * UBN + h * 16), v);
+#pragma unroll
+          for (int c = 0; c < 16; ++c) {
+            const long long sv = (long long)__float2int_rn(v[c]);
+            chk[c] += v[c];
+            if (t <= 5) hi[c] = hi[c] * 32 + sv;
+            else lo[c] = lo[c] * 32 + sv;
+          }
+        }
+        if (row < M && !*abort_flag) {
+          double *crow = C + row * ldc;
+#pragma unroll
+          for (int c = 0; c < 16; ++c) {
+            const int64_t j = n0 + h * 16 + c;
+            if (j < N && j <= row) {
+              const int e = e_i + eb[j];
+              // 2^(e - 35) and 2^(e - 65) built from their exponent fields
+              const double sh = __longlong_as_double((long long)(1023 + e - 35) << 52);
+              const double sl = __longlong_as_double((long long)(1023 + e - 65) << 52);
+              double v = fma((double)lo[c], sl, (double)hi[c] * sh);
+              if (!(fabsf(chk[c]) <= 3.4e38f)) v = (double)chk[c];  // NaN or Inf through
+              crow[j] -= v;
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(acc_empty);
+      ++i;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) tmem_dealloc<1>(tmem, UTMEM_COLS);
+}
+
+int64_t digits_kp(int64_t K) { return (K + 7) / 8 * 8; }
+size_t align256u(size_t b) { return (b + 255) / 256 * 256; }
+
+// 3-D map over RP planes of rows x K BF16 digits (row pitch kp), box 64 x
+// box_rows x 1, 128-byte swizzle; reads beyond K or rows give 0.
+bool make_digit_map(CUtensorMap *map, const void *base, int64_t K, int64_t rows, int64_t kp,
+                    int box_rows) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)RP};
+  cuuint64_t strides[2] = {(cuuint64_t)kp * 2, (cuuint64_t)rows * kp * 2};
+  cuuint32_t box[3] = {(cuuint32_t)UBK, (cuuint32_t)box_rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims,
+                   strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+size_t digit_set_bytes(int64_t rows, int64_t K) {
+  const int64_t k = std::min<int64_t>(K, UK_MAX);
+  return align256u((size_t)RP * rows * digits_kp(k) * 2) + align256u((size_t)rows * sizeof(int));
+}
+
+}  // namespace
+
+size_t update_digits_bytes(int64_t M, int64_t N, int64_t K, bool same) {
+  return digit_set_bytes(M, K) + (same ? 0 : digit_set_bytes(N, K));
+}
+
+cudaError_t launch_update_digits(double *C, int64_t ldc, const double *X, int64_t ldx,
+                                 const double *Y, int64_t ldy, int64_t M, int64_t N, int64_t K,
+                                 const int *status, int *err, int64_t spin_limit, void *work,
+                                 size_t work_bytes, int sm_count, cudaStream_t st) {
+  if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
+  // Y's rows are X's first N rows (a Cholesky update): one set of digits
+  const bool same = X == Y && ldx == ldy && N <= M;
+  if (!work || work_bytes < update_digits_bytes(M, N, K, same)) return cudaErrorInvalidValue;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(update_digits_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)USMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  // a launch takes milliseconds; one second bounds every single wait
+  const long long wait_ns = std::min<long long>((long long)spin_limit * 100LL, 1000000000LL);
+  const int64_t nbi = (M + UBM - 1) / UBM, ntj = (N + UBN - 1) / UBN;
+  int64_t total = 0;
+  for (int64_t b = 0; b < nbi; ++b) total += std::min<int64_t>(ntj, (b * UBM + UBM - 1) / UBN + 1);
+  for (int64_t k0 = 0; k0 < K; k0 += UK_MAX) {
+    const int64_t kc = std::min<int64_t>(UK_MAX, K - k0), kp = digits_kp(kc);
+    uint16_t *pa = reinterpret_cast<uint16_t *>(work);
+    int *ea = reinterpret_cast<int *>((char *)work + align256u((size_t)RP * M * kp * 2));
+    uint16_t *pb = pa;
+    int *eb = ea;
+    digits_rows_kernel<<<(unsigned)ceil_div(M, 8), 256, 0, st>>>(X + k0, ldx, M, kc, pa, kp,
+                                                                  M * kp, ea, status);
+    count_launch();
+    int64_t rows_b = M;
+    if (!same) {
+      char *wb = (char *)work + digit_set_bytes(M, K);
+      pb = reinterpret_cast<uint16_t *>(wb);
+      eb = reinterpret_cast<int *>(wb + align256u((size_t)RP * N * kp * 2));
+      digits_rows_kernel<<<(unsigned)ceil_div(N, 8), 256, 0, st>>>(Y + k0, ldy, N, kc, pb, kp,
+                                                                    N * kp, eb, status);
+      count_launch();
+      rows_b = N;
+    }
+    CUtensorMap ma, mb;
+    if (!make_digit_map(&ma, pa, kc, M, kp, UBM) || !make_digit_map(&mb, pb, kc, rows_b, kp, UBN))
+      return cudaErrorInvalidValue;
+    const int grid = (int)std::min<int64_t>(total, sm_count);
+    update_digits_kernel<<<grid, UTHREADS, USMEM, st>>>(ma, mb, ea, eb, C, ldc, M, N,
+                                                        (int)((kc + UBK - 1) / UBK), total, status,
+                                                        err, wait_ns);
+    count_launch();
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace gb

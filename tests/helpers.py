@@ -41,3 +41,27 @@ def row_scaled_err(got, ref, u: float) -> float:
     scale = u * np.sqrt(np.arange(1, n + 1))[None, :] * rms[:, None]
     err = np.tril(np.abs(got - ref)) / np.maximum(scale, 1e-300)
     return float(err.max())
+
+
+def _veltkamp(a):
+    c = 134217729.0 * a  # 2^27 + 1
+    hi = c - (c - a)
+    return hi, a - hi
+
+
+def exact_dot_minus(c, a, b) -> float:
+    """c - sum_k a_k b_k correctly rounded: every product as the sum of four
+    exact FP64 products of 26-bit halves (Veltkamp), all terms summed
+    exactly by math.fsum."""
+    import math
+    ah, al = _veltkamp(np.asarray(a, dtype=np.float64))
+    bh, bl = _veltkamp(np.asarray(b, dtype=np.float64))
+    terms = np.concatenate([ah * bh, ah * bl, al * bh, al * bl])
+    return math.fsum(np.concatenate([[c], -terms]).tolist())
+
+
+def pow2_scale(v) -> float:
+    """The power of two 2^e with max |v| < 2^e (1 for an all-zero v)."""
+    import math
+    m = float(np.abs(np.asarray(v)).max()) if np.size(v) else 0.0
+    return 2.0 ** math.frexp(m)[1] if m > 0 else 1.0

@@ -22,6 +22,7 @@ import pytest
 
 import oracle
 from paper_1812_02056_gb300 import inputs as I
+from tests.helpers import exact_dot_minus, pow2_scale
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -52,26 +53,6 @@ def _residual(h, method, A, X, B):
     finally:
         h.set_option(binding.GB_OPT_RESIDUAL, prev)
     return R.cpu().numpy(), eta
-
-
-def _veltkamp(a):
-    c = 134217729.0 * a  # 2^27 + 1
-    hi = c - (c - a)
-    return hi, a - hi
-
-
-def exact_residual(A, x, b):
-    """b - A x correctly rounded: every product as a sum of four exact FP64
-    products of 26-bit halves, all terms summed exactly by math.fsum."""
-    ah, al = _veltkamp(A)
-    xh, xl = _veltkamp(x)
-    terms = np.concatenate([ah * xh, ah * xl, al * xh, al * xl])
-    return math.fsum(np.concatenate([[b], -terms]).tolist())
-
-
-def _pow2_scale(v):
-    m = np.abs(v).max()
-    return 2.0 ** math.frexp(m)[1] if m > 0 else 1.0
 
 
 @pytest.mark.parametrize("n,nrhs", [(300, 3), (2100, 16), (5000, 23)])
@@ -117,10 +98,10 @@ def test_digit_method_against_correctly_rounded_residual(h, n, nrhs):
     rows = sorted({0, 1, n // 3, n // 2, n - 2, n - 1, *rng.integers(0, n, 10).tolist()})
     worst_s = worst_f = 0.0
     for i in rows:
-        sig = _pow2_scale(A[i])
+        sig = pow2_scale(A[i])
         for c in range(nrhs):
-            ref = exact_residual(A[i], X[:, c], B[i, c])
-            scale = sig * _pow2_scale(X[:, c])
+            ref = exact_dot_minus(B[i, c], A[i], X[:, c])
+            scale = sig * pow2_scale(X[:, c])
             worst_s = max(worst_s, abs(Rs[i, c] - ref) / scale)
             worst_f = max(worst_f, abs(Rf[i, c] - ref) / scale)
     assert worst_s <= 2.0 ** -48, (worst_s, worst_f)
