@@ -285,9 +285,12 @@ gb_status chol_update(gb_handle *h, gb_dtype dt, T *C, const T *X, const T *Y, i
       const bool same = X == Y && N <= M;
       gb_status ws = ws_reserve(h, pack_slot, update_digits_bytes(M, N, K, same), st);
       if (ws != GB_OK) return ws;
+      // the rest of an update under look-ahead leaves SMs to the column
+      // steps, whose CTAs could not share an SM with the update's
+      const int ctas = st == h->aux ? std::max(1, h->sm_count - h->digits_reserve) : h->sm_count;
       GB_CUDA_TRY(launch_update_digits(C, ld, X, ld, Y, ld, M, N, K, status, h->d_err,
                                        h->spin_limit, h->ws[pack_slot].ptr,
-                                       h->ws[pack_slot].bytes, h->sm_count, st));
+                                       h->ws[pack_slot].bytes, ctas, st));
       return GB_OK;
     }
   }
@@ -645,9 +648,12 @@ gb_status lu_update(gb_handle *h, gb_dtype dt, T *C, const T *X, const T *Y, int
       const bool same = X == Y && N <= M;
       gb_status ws = ws_reserve(h, pack_slot, update_digits_bytes(M, N, K, same), st);
       if (ws != GB_OK) return ws;
+      // the rest of an update under look-ahead leaves SMs to the column
+      // steps, whose CTAs could not share an SM with the update's
+      const int ctas = st == h->aux ? std::max(1, h->sm_count - h->digits_reserve) : h->sm_count;
       GB_CUDA_TRY(launch_update_digits(C, ld, X, ld, Y, ld, M, N, K, status, h->d_err,
                                        h->spin_limit, h->ws[pack_slot].ptr,
-                                       h->ws[pack_slot].bytes, h->sm_count, st));
+                                       h->ws[pack_slot].bytes, ctas, st));
       return GB_OK;
     }
   }

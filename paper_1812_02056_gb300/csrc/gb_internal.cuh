@@ -63,6 +63,7 @@ struct gb_handle {
   int early_rest = 2;         // GB_OPT_EARLY_REST
   int residual = 2;           // GB_OPT_RESIDUAL
   int f64_update = 0;         // GB_OPT_F64_UPDATE
+  int digits_reserve = 16;    // SMs the look-ahead stream's digit updates leave free
   cudaStream_t aux2 = nullptr;  // high priority: the inner updates' rest (inner look-ahead)
   cudaEvent_t ev_ip = nullptr, ev_ir = nullptr;  // inner block's columns final / inner rest done
   // device copies of host buffers come from this pool, which keeps its
@@ -276,12 +277,13 @@ cudaError_t launch_inf_norm_rows(const double *A, int64_t lda, int64_t n, double
 // using `xwork` (split_x_bytes) for the digits of x and partial sums.
 // FP64-accurate delayed update C -= X Y^T (lower, j <= i) from exact digit
 // products on the tensor cores (update_digits.cu); `work` of
-// update_digits_bytes (same: Y is X's first N rows).
+// update_digits_bytes (same: Y is X's first N rows).  At most `max_ctas`
+// persistent CTAs (one per SM): fewer leave SMs to concurrent column steps.
 size_t update_digits_bytes(int64_t M, int64_t N, int64_t K, bool same);
 cudaError_t launch_update_digits(double *C, int64_t ldc, const double *X, int64_t ldx,
                                  const double *Y, int64_t ldy, int64_t M, int64_t N, int64_t K,
                                  const int *status, int *err, int64_t spin_limit, void *work,
-                                 size_t work_bytes, int sm_count, cudaStream_t st);
+                                 size_t work_bytes, int max_ctas, cudaStream_t st);
 // GB_OPT_RESIDUAL 2 (default): the digit products from this order up
 constexpr int64_t SPLIT_RESIDUAL_MIN_N = 2048;
 size_t split_a_bytes(int64_t n);

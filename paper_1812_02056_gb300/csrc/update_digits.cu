@@ -23,7 +23,8 @@
 // tcgen05.mma.kind::f16 (M = 128, N = 32, K = 16) into twelve 32-column
 // FP32 accumulators in tensor memory, one per scale t, and warps 2..5 read
 // them back (tcgen05.ld), fold them into two exact 64-bit integers per
-// element and update C.  The digits of X go in four passes of at most three
+// element and update C through a transpose in shared memory (16 lanes per
+// row of C, so that its loads and stores are coalesced).  The digits of X go in four passes of at most three
 // planes over the tile's K range (smallest digits first); all passes
 // accumulate into the same twelve accumulators.  Every mbarrier wait is
 // bounded; a failed column step (`status`) or an expired wait skips the
@@ -53,7 +54,9 @@ constexpr int UMAXP = 3;                 // digit planes of X per pass
 constexpr uint32_t UA_SLOT = UBM * UBK * 2;  // 16 KiB
 constexpr uint32_t UB_SLOT = UBN * UBK * 2;  // 4 KiB
 constexpr uint32_t USTAGE = UMAXP * UA_SLOT + RP * UB_SLOT;  // 92 KiB
-constexpr size_t USMEM = (size_t)USTAGES * USTAGE + 1024 + 256;
+constexpr int UTP = 17;                  // pitch (doubles) of an epilogue warp's 32 x 16 block
+constexpr uint32_t UEPI = 4 * 32 * UTP * 8;  // the four epilogue warps' blocks
+constexpr size_t USMEM = (size_t)USTAGES * USTAGE + UEPI + 1024 + 256;
 constexpr int UTHREADS = 192;
 constexpr uint32_t UTMEM_COLS = 512;     // twelve 32-column accumulators (384) fit
 constexpr int UNPASS = 4;
@@ -133,7 +136,8 @@ __global__ void __launch_bounds__(UTHREADS, 1)
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  uint64_t *full = reinterpret_cast<uint64_t *>(smem + USTAGES * USTAGE);
+  double *sT = reinterpret_cast<double *>(smem + USTAGES * USTAGE);  // epilogue transposes
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + USTAGES * USTAGE + UEPI);
   uint64_t *empty = full + USTAGES;
   uint64_t *acc_full = empty + USTAGES;
   uint64_t *acc_empty = acc_full + 1;
@@ -263,8 +267,11 @@ __global__ void __launch_bounds__(UTHREADS, 1)
     while (it.next(m0, n0)) {
       if (!mbar_wait(acc_full, i & 1u, deadline, err, abort_flag)) break;
       tc_fence_after();
-      const int64_t row = m0 + qd * 32 + lane;
-      const int e_i = row < M ? ea[row] : 0;
+      // row m0 + 32 qd + lane is this thread's in tensor memory; C is then
+      // written through a transpose in shared memory, 16 lanes per row
+      double *blk = sT + (warp - 2) * 32 * UTP;
+      const int64_t r0 = m0 + qd * 32;
+      const int e_r = r0 + lane < M ? ea[r0 + lane] : 0;  // row scales, shared by shuffles
 #pragma unroll 1
       for (int h = 0; h < UBN / 16; ++h) {
         // D_0..D_5 and D_6..D_11 folded exactly: hi = sum S_t 2^(5 (5 - t)),
@@ -285,22 +292,32 @@ __global__ void __launch_bounds__(UTHREADS, 1)
             else lo[c] = lo[c] * 32 + sv;
           }
         }
-        if (row < M && !*abort_flag) {
-          double *crow = C + row * ldc;
+        // hi + lo 2^-30 in FP64 (one rounding); the scale 2^(e_i + e_j - 35)
+        // is applied after the transpose
 #pragma unroll
-          for (int c = 0; c < 16; ++c) {
-            const int64_t j = n0 + h * 16 + c;
-            if (j < N && j <= row) {
-              const int e = e_i + eb[j];
-              // 2^(e - 35) and 2^(e - 65) built from their exponent fields
-              const double sh = __longlong_as_double((long long)(1023 + e - 35) << 52);
-              const double sl = __longlong_as_double((long long)(1023 + e - 65) << 52);
-              double v = fma((double)lo[c], sl, (double)hi[c] * sh);
-              if (!(fabsf(chk[c]) <= 3.4e38f)) v = (double)chk[c];  // NaN or Inf through
-              crow[j] -= v;
+        for (int c = 0; c < 16; ++c) {
+          double v = fma((double)lo[c], 0x1p-30, (double)hi[c]);
+          if (!(fabsf(chk[c]) <= 3.4e38f)) v = (double)chk[c];  // NaN or Inf through
+          blk[lane * UTP + c] = v;
+        }
+        __syncwarp();
+        const int cl = lane & 15;
+        const int64_t j = n0 + h * 16 + cl;
+        const int e_j = j < N ? eb[j] : 0;
+        if (!*abort_flag) {
+#pragma unroll 4
+          for (int it = 0; it < 16; ++it) {
+            const int r = 2 * it + (lane >> 4);
+            const int64_t row = r0 + r;
+            const int e = __shfl_sync(0xffffffffu, e_r, r) + e_j;
+            if (row < M && j < N && j <= row) {
+              const double sc = __longlong_as_double((long long)(1023 + e - 35) << 52);
+              double *cp = C + row * ldc + j;
+              *cp = *cp - blk[r * UTP + cl] * sc;
             }
           }
         }
+        __syncwarp();
       }
       tc_fence_before();
       __syncwarp();
@@ -347,7 +364,7 @@ size_t update_digits_bytes(int64_t M, int64_t N, int64_t K, bool same) {
 cudaError_t launch_update_digits(double *C, int64_t ldc, const double *X, int64_t ldx,
                                  const double *Y, int64_t ldy, int64_t M, int64_t N, int64_t K,
                                  const int *status, int *err, int64_t spin_limit, void *work,
-                                 size_t work_bytes, int sm_count, cudaStream_t st) {
+                                 size_t work_bytes, int max_ctas, cudaStream_t st) {
   if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
   // Y's rows are X's first N rows (a Cholesky update): one set of digits
   const bool same = X == Y && ldx == ldy && N <= M;
@@ -386,7 +403,7 @@ cudaError_t launch_update_digits(double *C, int64_t ldc, const double *X, int64_
     CUtensorMap ma, mb;
     if (!make_digit_map(&ma, pa, kc, M, kp, UBM) || !make_digit_map(&mb, pb, kc, rows_b, kp, UBN))
       return cudaErrorInvalidValue;
-    const int grid = (int)std::min<int64_t>(total, sm_count);
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(total, max_ctas));
     update_digits_kernel<<<grid, UTHREADS, USMEM, st>>>(ma, mb, ea, eb, C, ldc, M, N,
                                                         (int)((kc + UBK - 1) / UBK), total, status,
                                                         err, wait_ns);
