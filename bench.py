@@ -416,6 +416,30 @@ def run_ours(args):
             sweep[f"lu_f64_s{ss}"] = lu_flops(n) / (a0.elapsed_time(a1) * 1e-3) / 1e9
         extra["sweep_gflops"] = sweep
         del Alu, LU
+        # FP64 accuracy with the delayed and inner updates from exact digit
+        # products on the tensor cores (GB_OPT_F64_UPDATE = 1), same input
+        if args.dtype == "f64":
+            Ld = torch.empty_like(A)
+            dig = {}
+            h.set_option(binding.GB_OPT_F64_UPDATE, 1)
+            try:
+                for ss in (256, 512):
+                    h.gb_chol_factor(n, ss, binding.GB_F64, A, n, Ld, n, info, stream)
+                    a0 = torch.cuda.Event(enable_timing=True)
+                    a1 = torch.cuda.Event(enable_timing=True)
+                    a0.record(stream)
+                    for _ in range(3):
+                        h.gb_chol_factor(n, ss, binding.GB_F64, A, n, Ld, n, info, stream)
+                    a1.record(stream)
+                    torch.cuda.synchronize()
+                    ms = a0.elapsed_time(a1) / 3
+                    dig[f"s{ss}"] = {"ms": ms, "gflops": flops / (ms * 1e-3) / 1e9,
+                                     "backward_error": h.backward_error(A, Ld, "f64"),
+                                     "info": int(info.item())}
+            finally:
+                h.set_option(binding.GB_OPT_F64_UPDATE, 0)
+            extra["f64_digit_update"] = dig
+            del Ld
 
     if rank == 0 and world == 1 and not args.quick and not args.no_extras:
         extra["workloads"] = other_workloads(args)
