@@ -46,27 +46,39 @@ namespace {
 using namespace tc;
 using namespace dg;
 
-constexpr int UT = 11;                   // scales kept: p + q <= UT
-constexpr int UG = UT + 1;               // accumulators (scales 0..UT)
-constexpr int UBM = 128, UBN = 32, UBK = 64;
+constexpr int UT = 11;                   // scales kept: t = p + q <= UT
+constexpr int USC = 6;                   // scales per scale pass (0..5, then 6..11)
+constexpr int UBM = 128, UBN = 64, UBK = 64;
 constexpr int USTAGES = 2;
-constexpr int UMAXP = 3;                 // digit planes of X per pass
-constexpr uint32_t UA_SLOT = UBM * UBK * 2;  // 16 KiB
-constexpr uint32_t UB_SLOT = UBN * UBK * 2;  // 4 KiB
-constexpr uint32_t USTAGE = UMAXP * UA_SLOT + RP * UB_SLOT;  // 92 KiB
+constexpr uint32_t UA_SLOT = UBM * UBK * 2;  // 16 KiB: a 128 x 64 digit plane of X
+constexpr uint32_t UB_SLOT = UBN * UBK * 2;  // 8 KiB: a 64 x 64 digit plane of Y
+constexpr int UMAXA = 3, UMAXB = 7;          // planes per stage
+constexpr uint32_t USTAGE = UMAXA * UA_SLOT + UMAXB * UB_SLOT;  // 104 KiB
 constexpr int UTP = 17;                  // pitch (doubles) of an epilogue warp's 32 x 16 block
 constexpr uint32_t UEPI = 4 * 32 * UTP * 8;  // the four epilogue warps' blocks
 constexpr size_t USMEM = (size_t)USTAGES * USTAGE + UEPI + 1024 + 256;
 constexpr int UTHREADS = 192;
-constexpr uint32_t UTMEM_COLS = 512;     // twelve 32-column accumulators (384) fit
-constexpr int UNPASS = 4;
+constexpr uint32_t UTMEM_COLS = 512;     // six 64-column accumulators (384) fit
 constexpr int64_t UK_MAX = 1024;         // K per launch: D_t partial sums below 2^24
 static_assert(USMEM <= 232448, "shared memory per CTA");
-static_assert(UG * UBN <= (int)UTMEM_COLS, "accumulators fit tensor memory");
+static_assert(USC * UBN <= (int)UTMEM_COLS, "accumulators fit tensor memory");
 
-__host__ __device__ constexpr int unq_of(int p) { return UT + 1 - p < RP ? UT + 1 - p : RP; }
-__host__ __device__ constexpr int upass_first(int k) { return k == 0 ? 9 : k == 1 ? 6 : k == 2 ? 3 : 0; }
-__host__ __device__ constexpr int upass_count(int k) { return k == 0 ? 2 : 3; }
+// The streams of a tile: (scale pass, first digit of X, digits of X, first
+// digit of Y, digits of Y).  Each runs over the tile's K range; together
+// they hold every pair (p, q) with p + q <= UT exactly once in the scale
+// pass of p + q, and no stage needs more than UMAXA + UMAXB planes.
+constexpr int USTREAMS = 7;
+__host__ __device__ constexpr int us_pass(int i) { return i < 2 ? 0 : 1; }
+__host__ __device__ constexpr int us_p0(int i) {
+  return i == 0 ? 0 : i == 1 ? 3 : i == 2 ? 0 : i == 3 ? 3 : i == 4 ? 5 : i == 5 ? 7 : 9;
+}
+__host__ __device__ constexpr int us_np(int i) { return i <= 2 ? 3 : 2; }
+__host__ __device__ constexpr int us_q0(int i) {
+  return i == 2 ? 4 : i == 3 ? 2 : 0;
+}
+__host__ __device__ constexpr int us_nq(int i) {
+  return i == 0 ? 6 : i == 1 ? 3 : i <= 4 ? 7 : i == 5 ? 5 : 3;
+}
 
 // Digits of the rows of X (M x K, ldx): planes[p][i][k] (row pitch kp), and
 // the row scale exponents.  One warp per row; lane l converts columns
@@ -182,9 +194,9 @@ __global__ void __launch_bounds__(UTHREADS, 1)
       bool ok = true;
       while (ok && it.next(m0, n0)) {
 #pragma unroll
-        for (int k = 0; k < UNPASS; ++k) {
-          const int p0 = upass_first(k), np = upass_count(k), nb = unq_of(p0);
-          const uint32_t bytes = np * UA_SLOT + nb * UB_SLOT;
+        for (int si = 0; si < USTREAMS; ++si) {
+          const int p0 = us_p0(si), np = us_np(si), q0 = us_q0(si), nq = us_nq(si);
+          const uint32_t bytes = np * UA_SLOT + nq * UB_SLOT;
           for (int kb = 0; ok && kb < nkb; ++kb, ++g) {
             const uint32_t s = g % USTAGES, ph = (g / USTAGES) & 1u;
             if (g >= (uint32_t)USTAGES && !mbar_wait(&empty[s], ph ^ 1u, deadline, err, abort_flag)) {
@@ -195,8 +207,9 @@ __global__ void __launch_bounds__(UTHREADS, 1)
             mbar_expect_tx(&full[s], bytes);
             for (int j = 0; j < np; ++j)
               tma_load_3d(st + j * UA_SLOT, &map_a, &full[s], kb * UBK, (int)m0, p0 + j);
-            for (int q = 0; q < nb; ++q)
-              tma_load_3d(st + UMAXP * UA_SLOT + q * UB_SLOT, &map_b, &full[s], kb * UBK, (int)n0, q);
+            for (int q = 0; q < nq; ++q)
+              tma_load_3d(st + UMAXA * UA_SLOT + q * UB_SLOT, &map_b, &full[s], kb * UBK, (int)n0,
+                          q0 + q);
           }
         }
       }
@@ -205,18 +218,26 @@ __global__ void __launch_bounds__(UTHREADS, 1)
   } else if (warp == 1) {
     // ------------------------------------------------ MMA issuer
     if (lane == 0) {
-      // FP32 accumulator, BF16 A and B, both K-major, N = 32, M = 128
+      // FP32 accumulator, BF16 A and B, both K-major, N = 64, M = 128
       const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(UBN >> 3) << 17) |
                              ((uint32_t)(UBM >> 4) << 24);
-      uint32_t g = 0, i = 0;
+      uint32_t g = 0, i = 0;  // i: scale passes issued
       bool ok = true;
       while (ok && it.next(m0, n0)) {
-        if (i > 0 && !mbar_wait(acc_empty, (i - 1) & 1u, deadline, err, abort_flag)) break;
-        tc_fence_after();
-        uint32_t started = 0;  // accumulators written in this tile
+        uint32_t started = 0;  // accumulators written in this scale pass
 #pragma unroll
-        for (int k = 0; k < UNPASS; ++k) {
-          const int p0 = upass_first(k), np = upass_count(k);
+        for (int si = 0; si < USTREAMS; ++si) {
+          const int pass = us_pass(si);
+          if (si == 0 || pass != us_pass(si - 1)) {  // a new scale pass: its accumulators free
+            if (i > 0 && !mbar_wait(acc_empty, (i - 1) & 1u, deadline, err, abort_flag)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            started = 0;
+          }
+          const int p0 = us_p0(si), np = us_np(si), q0 = us_q0(si), nq = us_nq(si);
+          const int tlo = pass * USC, thi = tlo + USC - 1;
           for (int kb = 0; ok && kb < nkb; ++kb, ++g) {
             const uint32_t s = g % USTAGES, ph = (g / USTAGES) & 1u;
             if (!mbar_wait(&full[s], ph, deadline, err, abort_flag)) {
@@ -225,16 +246,15 @@ __global__ void __launch_bounds__(UTHREADS, 1)
             }
             tc_fence_after();
             const uint32_t st = smem_u32(smem + s * USTAGE);
-            const uint32_t b0 = st + UMAXP * UA_SLOT;
-#pragma unroll
-            for (int j = 0; j < UMAXP; ++j) {
-              if (j >= np) break;
+            const uint32_t b0 = st + UMAXA * UA_SLOT;
+            for (int j = 0; j < np; ++j) {
               const int p = p0 + j;
               const uint32_t a0 = st + j * UA_SLOT;
-              for (int q = 0; q < unq_of(p); ++q) {
-                const int t = p + q;
+              const int qa = max(q0, tlo - p), qb = min(q0 + nq - 1, thi - p);
+              for (int q = qa; q <= qb; ++q) {
+                const int t = p + q - tlo;
                 const uint32_t d = tmem + (uint32_t)(t * UBN);
-                const uint32_t bq = b0 + q * UB_SLOT;
+                const uint32_t bq = b0 + (q - q0) * UB_SLOT;
 #pragma unroll
                 for (int kk = 0; kk < UBK / 16; ++kk) {
                   mma_f16<1>(d, sw128_desc(a0 + kk * 32), sw128_desc(bq + kk * 32), idesc,
@@ -245,10 +265,12 @@ __global__ void __launch_bounds__(UTHREADS, 1)
             }
             mma_commit(&empty[s]);
           }
+          if (!ok) break;
+          if (si == USTREAMS - 1 || us_pass(si + 1) != pass) {  // the scale pass is complete
+            mma_commit(acc_full);
+            ++i;
+          }
         }
-        if (!ok) break;
-        mma_commit(acc_full);
-        ++i;
       }
       mma_commit(drain);
       const unsigned long long until = now_ns() + deadline;
@@ -263,66 +285,68 @@ __global__ void __launch_bounds__(UTHREADS, 1)
   } else {
     // ------------------------------------------------ epilogue (warps 2..5)
     const int qd = warp & 3;  // tensor-memory lane quarter this warp may read
+    double *blk = sT + (warp - 2) * 32 * UTP;
     uint32_t i = 0;
-    while (it.next(m0, n0)) {
-      if (!mbar_wait(acc_full, i & 1u, deadline, err, abort_flag)) break;
-      tc_fence_after();
+    bool ok = true;
+    while (ok && it.next(m0, n0)) {
       // row m0 + 32 qd + lane is this thread's in tensor memory; C is then
       // written through a transpose in shared memory, 16 lanes per row
-      double *blk = sT + (warp - 2) * 32 * UTP;
       const int64_t r0 = m0 + qd * 32;
       const int e_r = r0 + lane < M ? ea[r0 + lane] : 0;  // row scales, shared by shuffles
+      for (int pass = 0; pass < 2; ++pass, ++i) {
+        if (!mbar_wait(acc_full, i & 1u, deadline, err, abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const int thi = pass * USC + USC - 1;
 #pragma unroll 1
-      for (int h = 0; h < UBN / 16; ++h) {
-        // D_0..D_5 and D_6..D_11 folded exactly: hi = sum S_t 2^(5 (5 - t)),
-        // lo = sum S_t 2^(5 (11 - t)), each below 2^50
-        long long hi[16], lo[16];
-        float chk[16];
+        for (int h = 0; h < UBN / 16; ++h) {
+          // the pass's six scales folded exactly: v = sum S_t 2^(5 (thi - t)),
+          // below 2^50; its weight is 2^(-5 (thi + 2))
+          long long v[16];
+          float chk[16];
 #pragma unroll
-        for (int c = 0; c < 16; ++c) hi[c] = 0, lo[c] = 0, chk[c] = 0.0f;
+          for (int c = 0; c < 16; ++c) v[c] = 0, chk[c] = 0.0f;
 #pragma unroll
-        for (int t = 0; t < UG; ++t) {
-          float v[16];
-          tmem_ld_32x16(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(t * UBN + h * 16), v);
+          for (int t = 0; t < USC; ++t) {
+            float w[16];
+            tmem_ld_32x16(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(t * UBN + h * 16), w);
 #pragma unroll
-          for (int c = 0; c < 16; ++c) {
-            const long long sv = (long long)__float2int_rn(v[c]);
-            chk[c] += v[c];
-            if (t <= 5) hi[c] = hi[c] * 32 + sv;
-            else lo[c] = lo[c] * 32 + sv;
-          }
-        }
-        // hi + lo 2^-30 in FP64 (one rounding); the scale 2^(e_i + e_j - 35)
-        // is applied after the transpose
-#pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          double v = fma((double)lo[c], 0x1p-30, (double)hi[c]);
-          if (!(fabsf(chk[c]) <= 3.4e38f)) v = (double)chk[c];  // NaN or Inf through
-          blk[lane * UTP + c] = v;
-        }
-        __syncwarp();
-        const int cl = lane & 15;
-        const int64_t j = n0 + h * 16 + cl;
-        const int e_j = j < N ? eb[j] : 0;
-        if (!*abort_flag) {
-#pragma unroll 4
-          for (int it = 0; it < 16; ++it) {
-            const int r = 2 * it + (lane >> 4);
-            const int64_t row = r0 + r;
-            const int e = __shfl_sync(0xffffffffu, e_r, r) + e_j;
-            if (row < M && j < N && j <= row) {
-              const double sc = __longlong_as_double((long long)(1023 + e - 35) << 52);
-              double *cp = C + row * ldc + j;
-              *cp = *cp - blk[r * UTP + cl] * sc;
+            for (int c = 0; c < 16; ++c) {
+              v[c] = v[c] * 32 + (long long)__float2int_rn(w[c]);
+              chk[c] += w[c];
             }
           }
+#pragma unroll
+          for (int c = 0; c < 16; ++c) {
+            double dv = (double)v[c];
+            if (!(fabsf(chk[c]) <= 3.4e38f)) dv = (double)chk[c];  // NaN or Inf through
+            blk[lane * UTP + c] = dv;
+          }
+          __syncwarp();
+          const int cl = lane & 15;
+          const int64_t j = n0 + h * 16 + cl;
+          const int e_j = j < N ? eb[j] : 0;
+          if (!*abort_flag) {
+#pragma unroll 4
+            for (int it2 = 0; it2 < 16; ++it2) {
+              const int r = 2 * it2 + (lane >> 4);
+              const int64_t row = r0 + r;
+              const int e = __shfl_sync(0xffffffffu, e_r, r) + e_j - RW * (thi + 2);
+              if (row < M && j < N && j <= row) {
+                const double sc = __longlong_as_double((long long)(1023 + e) << 52);
+                double *cp = C + row * ldc + j;
+                *cp = *cp - blk[r * UTP + cl] * sc;
+              }
+            }
+          }
+          __syncwarp();
         }
+        tc_fence_before();
         __syncwarp();
+        if (lane == 0) mbar_arrive(acc_empty);
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(acc_empty);
-      ++i;
     }
   }
   tc_fence_before();
