@@ -302,42 +302,49 @@ __global__ void __launch_bounds__(UTHREADS, 1)
         const int thi = pass * USC + USC - 1;
 #pragma unroll 1
         for (int h = 0; h < UBN / 16; ++h) {
+          // this lane's 16 entries of C for the chunk (row 2 it2 + lane / 16,
+          // column lane % 16), loaded first: they arrive while the
+          // accumulators are read and folded
+          const int cl = lane & 15;
+          const int64_t j = n0 + h * 16 + cl;
+          double cv[16];
+#pragma unroll
+          for (int it2 = 0; it2 < 16; ++it2) {
+            const int64_t row = r0 + 2 * it2 + (lane >> 4);
+            cv[it2] = (row < M && j < N && j <= row) ? C[row * ldc + j] : 0.0;
+          }
           // the pass's six scales folded exactly: v = sum S_t 2^(5 (thi - t)),
           // below 2^50; its weight is 2^(-5 (thi + 2))
           long long v[16];
-          float chk[16];
+          uint32_t bad = 0;  // columns with a non-finite sum (from a non-finite input)
 #pragma unroll
-          for (int c = 0; c < 16; ++c) v[c] = 0, chk[c] = 0.0f;
+          for (int c = 0; c < 16; ++c) v[c] = 0;
 #pragma unroll
           for (int t = 0; t < USC; ++t) {
             float w[16];
             tmem_ld_32x16(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(t * UBN + h * 16), w);
 #pragma unroll
             for (int c = 0; c < 16; ++c) {
+              // every finite sum is an integer below 2^24: NaN or Inf otherwise
+              bad |= (fabsf(w[c]) < 3.0e7f ? 0u : 1u) << c;
               v[c] = v[c] * 32 + (long long)__float2int_rn(w[c]);
-              chk[c] += w[c];
             }
           }
 #pragma unroll
-          for (int c = 0; c < 16; ++c) {
-            double dv = (double)v[c];
-            if (!(fabsf(chk[c]) <= 3.4e38f)) dv = (double)chk[c];  // NaN or Inf through
-            blk[lane * UTP + c] = dv;
-          }
+          for (int c = 0; c < 16; ++c)
+            blk[lane * UTP + c] = ((bad >> c) & 1u) ? __longlong_as_double(0x7ff8000000000000LL)
+                                                     : (double)v[c];
           __syncwarp();
-          const int cl = lane & 15;
-          const int64_t j = n0 + h * 16 + cl;
           const int e_j = j < N ? eb[j] : 0;
           if (!*abort_flag) {
-#pragma unroll 4
+#pragma unroll
             for (int it2 = 0; it2 < 16; ++it2) {
               const int r = 2 * it2 + (lane >> 4);
               const int64_t row = r0 + r;
               const int e = __shfl_sync(0xffffffffu, e_r, r) + e_j - RW * (thi + 2);
               if (row < M && j < N && j <= row) {
                 const double sc = __longlong_as_double((long long)(1023 + e) << 52);
-                double *cp = C + row * ldc + j;
-                *cp = *cp - blk[r * UTP + cl] * sc;
+                C[row * ldc + j] = cv[it2] - blk[r * UTP + cl] * sc;
               }
             }
           }
