@@ -9,26 +9,27 @@
 // Every digit product is an integer below 2^10; a D_t sums at most 11 pairs
 // over K <= UK_MAX = 1024 terms, so every partial sum is an integer below
 // 11 * 1024 * 961 < 2^24 and the tensor cores' FP32 accumulation keeps it
-// exactly.  The twelve D_t of a tile are combined exactly in two 64-bit
-// integers, converted to FP64 and subtracted from C (two roundings).  Per
+// exactly.  The D_t of a tile are combined exactly in 64-bit integers, four
+// at a time, converted to FP64 and subtracted from C.  Per
 // term of K the truncation of both operands (below 2^-55 of their row
 // scales) and the dropped pairs (t > UT) stay below one FP64 rounding of
 // 2^(e_i + f_j); the plain FP64 update rounds at every one of its K
 // multiply-adds.
 //
-// Kernel: persistent CTAs over the valid 128 x 32 output tiles (lower
+// Kernel: persistent CTAs over the valid 128 x 64 output tiles (lower
 // trapezoid, dealt round-robin).  Warp 0 is the TMA producer (2-stage ring;
-// a stage holds up to three 128 x 64 digit planes of X and the 32 x 64
-// digit planes of Y they pair with, 128-byte swizzle), warp 1 issues
-// tcgen05.mma.kind::f16 (M = 128, N = 32, K = 16) into twelve 32-column
-// FP32 accumulators in tensor memory, one per scale t, and warps 2..5 read
-// them back (tcgen05.ld), fold them into two exact 64-bit integers per
-// element and update C through a transpose in shared memory (16 lanes per
-// row of C, so that its loads and stores are coalesced).  The digits of X go in four passes of at most three
-// planes over the tile's K range (smallest digits first); all passes
-// accumulate into the same twelve accumulators.  Every mbarrier wait is
-// bounded; a failed column step (`status`) or an expired wait skips the
-// work.
+// a stage holds up to three 128 x 64 digit planes of X and up to seven
+// 64 x 64 digit planes of Y that they pair with, 128-byte swizzle); warp 1
+// issues tcgen05.mma.kind::f16 (M = 128, N = 64, K = 16); warps 2..5 are the
+// epilogue.  The twelve scales go in three passes of four (0..3, 4..7,
+// 8..11), each pass into a set of four 64-column FP32 accumulators in tensor
+// memory; two sets alternate, so one pass's epilogue overlaps the next
+// pass's MMAs.  The epilogue reads a set back (tcgen05.ld), folds its four
+// scales exactly into one 64-bit integer per element and subtracts it from
+// C (three roundings of C per tile), C loaded ahead and written through a
+// transpose in shared memory (16 lanes per row, coalesced).  Every mbarrier
+// wait is bounded; a failed column step (`status`) or an expired wait skips
+// the work.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -47,7 +48,8 @@ using namespace tc;
 using namespace dg;
 
 constexpr int UT = 11;                   // scales kept: t = p + q <= UT
-constexpr int USC = 6;                   // scales per scale pass (0..5, then 6..11)
+constexpr int USC = 4;                   // scales per pass: 0..3, 4..7, 8..11
+constexpr int UNP = 3;                   // scale passes per tile
 constexpr int UBM = 128, UBN = 64, UBK = 64;
 constexpr int USTAGES = 2;
 constexpr uint32_t UA_SLOT = UBM * UBK * 2;  // 16 KiB: a 128 x 64 digit plane of X
@@ -58,26 +60,31 @@ constexpr int UTP = 17;                  // pitch (doubles) of an epilogue warp'
 constexpr uint32_t UEPI = 4 * 32 * UTP * 8;  // the four epilogue warps' blocks
 constexpr size_t USMEM = (size_t)USTAGES * USTAGE + UEPI + 1024 + 256;
 constexpr int UTHREADS = 192;
-constexpr uint32_t UTMEM_COLS = 512;     // six 64-column accumulators (384) fit
+constexpr uint32_t UTMEM_COLS = 512;     // two sets of four 64-column accumulators
+constexpr uint32_t UACC = USC * UBN;     // columns of one set (256)
 constexpr int64_t UK_MAX = 1024;         // K per launch: D_t partial sums below 2^24
 static_assert(USMEM <= 232448, "shared memory per CTA");
-static_assert(USC * UBN <= (int)UTMEM_COLS, "accumulators fit tensor memory");
+static_assert(2 * UACC <= UTMEM_COLS, "two accumulator sets fit tensor memory");
 
 // The streams of a tile: (scale pass, first digit of X, digits of X, first
 // digit of Y, digits of Y).  Each runs over the tile's K range; together
-// they hold every pair (p, q) with p + q <= UT exactly once in the scale
+// they hold every pair (p, q) with p + q <= UT exactly once, in the scale
 // pass of p + q, and no stage needs more than UMAXA + UMAXB planes.
-constexpr int USTREAMS = 7;
-__host__ __device__ constexpr int us_pass(int i) { return i < 2 ? 0 : 1; }
+constexpr int USTREAMS = 9;
+__host__ __device__ constexpr int us_pass(int i) { return i < 2 ? 0 : i < 5 ? 1 : 2; }
 __host__ __device__ constexpr int us_p0(int i) {
-  return i == 0 ? 0 : i == 1 ? 3 : i == 2 ? 0 : i == 3 ? 3 : i == 4 ? 5 : i == 5 ? 7 : 9;
+  return i == 0 ? 0 : i == 1 ? 3 : i == 2 ? 0 : i == 3 ? 3 : i == 4 ? 6
+       : i == 5 ? 0 : i == 6 ? 3 : i == 7 ? 6 : 9;
 }
-__host__ __device__ constexpr int us_np(int i) { return i <= 2 ? 3 : 2; }
+__host__ __device__ constexpr int us_np(int i) {
+  return i == 1 ? 1 : (i == 4 || i == 8) ? 2 : 3;
+}
 __host__ __device__ constexpr int us_q0(int i) {
-  return i == 2 ? 4 : i == 3 ? 2 : 0;
+  return i == 2 ? 2 : i == 5 ? 6 : i == 6 ? 3 : 0;
 }
 __host__ __device__ constexpr int us_nq(int i) {
-  return i == 0 ? 6 : i == 1 ? 3 : i <= 4 ? 7 : i == 5 ? 5 : 3;
+  return i == 0 ? 4 : i == 1 ? 1 : i == 2 ? 6 : i == 3 ? 5 : i == 4 ? 2
+       : i == 5 ? 5 : i == 6 ? 6 : i == 7 ? 6 : 3;
 }
 
 // Digits of the rows of X (M x K, ldx): planes[p][i][k] (row pitch kp), and
@@ -151,9 +158,9 @@ __global__ void __launch_bounds__(UTHREADS, 1)
   double *sT = reinterpret_cast<double *>(smem + USTAGES * USTAGE);  // epilogue transposes
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + USTAGES * USTAGE + UEPI);
   uint64_t *empty = full + USTAGES;
-  uint64_t *acc_full = empty + USTAGES;
-  uint64_t *acc_empty = acc_full + 1;
-  uint64_t *drain = acc_empty + 1;
+  uint64_t *acc_full = empty + USTAGES;    // per accumulator set
+  uint64_t *acc_empty = acc_full + 2;
+  uint64_t *drain = acc_empty + 2;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
   volatile int *skip = abort_flag + 1;
@@ -164,8 +171,10 @@ __global__ void __launch_bounds__(UTHREADS, 1)
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(acc_full, 1);
-    mbar_init(acc_empty, 4);  // the four epilogue warps
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 4);  // the four epilogue warps
+    }
     mbar_init(drain, 1);
     *abort_flag = 0;
     // skip the work after a failed column step or an expired wait
@@ -221,20 +230,24 @@ __global__ void __launch_bounds__(UTHREADS, 1)
       // FP32 accumulator, BF16 A and B, both K-major, N = 64, M = 128
       const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(UBN >> 3) << 17) |
                              ((uint32_t)(UBM >> 4) << 24);
-      uint32_t g = 0, i = 0;  // i: scale passes issued
+      uint32_t g = 0, i = 0;  // i: scale passes issued; pass i uses set i & 1
       bool ok = true;
       while (ok && it.next(m0, n0)) {
         uint32_t started = 0;  // accumulators written in this scale pass
+        uint32_t dset = 0;
 #pragma unroll
         for (int si = 0; si < USTREAMS; ++si) {
           const int pass = us_pass(si);
-          if (si == 0 || pass != us_pass(si - 1)) {  // a new scale pass: its accumulators free
-            if (i > 0 && !mbar_wait(acc_empty, (i - 1) & 1u, deadline, err, abort_flag)) {
+          if (si == 0 || pass != us_pass(si - 1)) {
+            // a new scale pass: the epilogue of pass i - 2 has freed its set
+            if (i >= 2 && !mbar_wait(&acc_empty[i & 1u], ((i >> 1) - 1) & 1u, deadline, err,
+                                     abort_flag)) {
               ok = false;
               break;
             }
             tc_fence_after();
             started = 0;
+            dset = (i & 1u) * UACC;
           }
           const int p0 = us_p0(si), np = us_np(si), q0 = us_q0(si), nq = us_nq(si);
           const int tlo = pass * USC, thi = tlo + USC - 1;
@@ -253,7 +266,7 @@ __global__ void __launch_bounds__(UTHREADS, 1)
               const int qa = max(q0, tlo - p), qb = min(q0 + nq - 1, thi - p);
               for (int q = qa; q <= qb; ++q) {
                 const int t = p + q - tlo;
-                const uint32_t d = tmem + (uint32_t)(t * UBN);
+                const uint32_t d = tmem + dset + (uint32_t)(t * UBN);
                 const uint32_t bq = b0 + (q - q0) * UB_SLOT;
 #pragma unroll
                 for (int kk = 0; kk < UBK / 16; ++kk) {
@@ -267,7 +280,7 @@ __global__ void __launch_bounds__(UTHREADS, 1)
           }
           if (!ok) break;
           if (si == USTREAMS - 1 || us_pass(si + 1) != pass) {  // the scale pass is complete
-            mma_commit(acc_full);
+            mma_commit(&acc_full[i & 1u]);
             ++i;
           }
         }
@@ -293,13 +306,14 @@ __global__ void __launch_bounds__(UTHREADS, 1)
       // written through a transpose in shared memory, 16 lanes per row
       const int64_t r0 = m0 + qd * 32;
       const int e_r = r0 + lane < M ? ea[r0 + lane] : 0;  // row scales, shared by shuffles
-      for (int pass = 0; pass < 2; ++pass, ++i) {
-        if (!mbar_wait(acc_full, i & 1u, deadline, err, abort_flag)) {
+      for (int pass = 0; pass < UNP; ++pass, ++i) {
+        if (!mbar_wait(&acc_full[i & 1u], (i >> 1) & 1u, deadline, err, abort_flag)) {
           ok = false;
           break;
         }
         tc_fence_after();
         const int thi = pass * USC + USC - 1;
+        const uint32_t dset = (i & 1u) * UACC;
 #pragma unroll 1
         for (int h = 0; h < UBN / 16; ++h) {
           // this lane's 16 entries of C for the chunk (row 2 it2 + lane / 16,
@@ -322,7 +336,8 @@ __global__ void __launch_bounds__(UTHREADS, 1)
 #pragma unroll
           for (int t = 0; t < USC; ++t) {
             float w[16];
-            tmem_ld_32x16(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(t * UBN + h * 16), w);
+            tmem_ld_32x16(tmem + ((uint32_t)(qd * 32) << 16) + dset + (uint32_t)(t * UBN + h * 16),
+                          w);
 #pragma unroll
             for (int c = 0; c < 16; ++c) {
               // every finite sum is an integer below 2^24: NaN or Inf otherwise
@@ -352,7 +367,7 @@ __global__ void __launch_bounds__(UTHREADS, 1)
         }
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(acc_empty);
+        if (lane == 0) mbar_arrive(&acc_empty[i & 1u]);
       }
     }
   }
