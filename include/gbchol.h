@@ -224,13 +224,14 @@ typedef enum gb_option {
                                used when that cannot be had.  2 (default): 1
                                for n >= 2048, else 0.                        */
   GB_OPT_F64_UPDATE = 17      /* GB_F64 delayed and inner updates (C -= R R^T
-                               of gb_chol_factor, and gb_rank_update with
-                               lower = 1 and y_is_kxn = 0).  0 (default):
+                               of gb_chol_factor, C -= R_L R_U of
+                               gb_lu_factor, and gb_rank_update).  0 (default):
                                FP64 multiply-adds on the CUDA cores.  1: FP64
                                accuracy from exact digit products on the
-                               tensor cores: each row of R is scaled by a
-                               power of two and cut into 11 digits of 5 bits
-                               (BF16 planes), the 76 digit pairs of the 12
+                               tensor cores: each row of R (column of R_U)
+                               is scaled by a power of two and cut into 11
+                               digits of 5 bits (BF16 planes), the 76 digit
+                               pairs of the 12
                                scales that matter are multiplied with exact
                                FP32 accumulation (K taken in pieces of at
                                most 1024), the scales are combined exactly in

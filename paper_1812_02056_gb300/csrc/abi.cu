@@ -288,8 +288,8 @@ gb_status chol_update(gb_handle *h, gb_dtype dt, T *C, const T *X, const T *Y, i
       // the rest of an update under look-ahead leaves SMs to the column
       // steps, whose CTAs could not share an SM with the update's
       const int ctas = st == h->aux ? std::max(1, h->sm_count - h->digits_reserve) : h->sm_count;
-      GB_CUDA_TRY(launch_update_digits(C, ld, X, ld, Y, ld, M, N, K, status, h->d_err,
-                                       h->spin_limit, h->ws[pack_slot].ptr,
+      GB_CUDA_TRY(launch_update_digits(C, ld, X, ld, Y, ld, M, N, K, true, false, status,
+                                       h->d_err, h->spin_limit, h->ws[pack_slot].ptr,
                                        h->ws[pack_slot].bytes, ctas, st));
       return GB_OK;
     }
@@ -644,15 +644,15 @@ gb_status lu_update(gb_handle *h, gb_dtype dt, T *C, const T *X, const T *Y, int
   if (M <= 0 || N <= 0 || K <= 0) return GB_OK;
   if constexpr (sizeof(T) == 8) {
     if (dt == GB_F64 && h->f64_update == 1 && tc_supported(h->device)) {
-      // FP64 accuracy from exact digit products on the tensor cores
-      const bool same = X == Y && N <= M;
-      gb_status ws = ws_reserve(h, pack_slot, update_digits_bytes(M, N, K, same), st);
+      // FP64 accuracy from exact digit products on the tensor cores: the
+      // whole M x N block, R_U (K x N) cut into digits by columns
+      gb_status ws = ws_reserve(h, pack_slot, update_digits_bytes(M, N, K, false), st);
       if (ws != GB_OK) return ws;
       // the rest of an update under look-ahead leaves SMs to the column
       // steps, whose CTAs could not share an SM with the update's
       const int ctas = st == h->aux ? std::max(1, h->sm_count - h->digits_reserve) : h->sm_count;
-      GB_CUDA_TRY(launch_update_digits(C, ld, X, ld, Y, ld, M, N, K, status, h->d_err,
-                                       h->spin_limit, h->ws[pack_slot].ptr,
+      GB_CUDA_TRY(launch_update_digits(C, ld, X, ld, Y, ld, M, N, K, false, true, status,
+                                       h->d_err, h->spin_limit, h->ws[pack_slot].ptr,
                                        h->ws[pack_slot].bytes, ctas, st));
       return GB_OK;
     }
@@ -690,6 +690,28 @@ gb_status lu_update(gb_handle *h, gb_dtype dt, T *C, const T *X, const T *Y, int
                            pack_slot == WS_PANEL2 ? WS_STRAS2 : WS_STRAS, st);
 }
 
+// The products inside an s-block of Algorithm 2 (C -= R_L R_U, R_U K x N):
+// FP64 multiply-adds on the CUDA cores, or the digit products of
+// GB_OPT_F64_UPDATE on `st`'s workspace (WS_PANEL, reserved at its largest
+// by lu_blocked_on).
+template <typename T>
+gb_status lu_inner_update(gb_handle *h, gb_dtype dt, T *C, const T *X, const T *Y, int64_t ld,
+                          int64_t M, int64_t N, int64_t K, int *status, cudaStream_t st) {
+  if (M <= 0 || N <= 0 || K <= 0) return GB_OK;
+  if constexpr (sizeof(T) == 8) {
+    if (dt == GB_F64 && h->f64_update == 1 && tc_supported(h->device)) {
+      gb_status ws = ws_reserve(h, WS_PANEL, update_digits_bytes(M, N, K, false), st);
+      if (ws != GB_OK) return ws;
+      GB_CUDA_TRY(launch_update_digits(C, ld, X, ld, Y, ld, M, N, K, false, true, status,
+                                       h->d_err, h->spin_limit, h->ws[WS_PANEL].ptr,
+                                       h->ws[WS_PANEL].bytes, h->sm_count, st));
+      return GB_OK;
+    }
+  }
+  GB_CUDA_TRY(launch_update_simt<T>(C, ld, X, ld, Y, ld, M, N, K, true, false, 0, status, st));
+  return GB_OK;
+}
+
 template <typename T, typename Tc>
 gb_status lu_blocked_on(gb_handle *h, int64_t n, int64_t s, T *W, int64_t ld, int *status,
                         gb_dtype dt, cudaStream_t st, bool la);
@@ -719,6 +741,14 @@ gb_status lu_blocked_on(gb_handle *h, int64_t n, int64_t s, T *W, int64_t ld, in
     if (r == GB_OK) r = ws_reserve(h, WS_PANEL2, pb, h->aux);
     if (r != GB_OK) return r;
   }
+  if (dt == GB_F64 && h->f64_update == 1) {
+    // the digit workspaces of both streams at their largest before anything
+    // is in flight (a later growth would free a buffer another stream uses)
+    const size_t db = update_digits_bytes(n, n, std::min(s, n), false);
+    gb_status r = ws_reserve(h, WS_PANEL, db, st);
+    if (r == GB_OK && la) r = ws_reserve(h, WS_PANEL2, db, h->aux);
+    if (r != GB_OK) return r;
+  }
   bool rest_pending = false;
   for (int64_t z = 0; z < n; z += s) {
     const int64_t sb = std::min(s, n - z);
@@ -745,17 +775,17 @@ gb_status lu_blocked_on(gb_handle *h, int64_t n, int64_t s, T *W, int64_t ld, in
           // the s-block's remaining columns (all rows below) ...
           PhaseTimer t(h, st, GB_PHASE_INNER, update_flops(n - r0, pe - r0, bw, false),
                        update_bytes(n - r0, pe - r0, bw, false, e));
-          GB_CUDA_TRY(launch_update_simt<T>(W + r0 * ld + r0, ld, W + r0 * ld + j0, ld,
-                                            W + j0 * ld + r0, ld, n - r0, pe - r0, bw, true,
-                                            false, 0, status, st));
+          gb_status r = lu_inner_update<T>(h, dt, W + r0 * ld + r0, W + r0 * ld + j0,
+                                           W + j0 * ld + r0, ld, n - r0, pe - r0, bw, status, st);
+          if (r != GB_OK) return r;
         }
         // ... and the s-block's remaining rows right of the block
         if (pe < n) {
           PhaseTimer t(h, st, GB_PHASE_INNER, update_flops(pe - r0, n - pe, bw, false),
                        update_bytes(pe - r0, n - pe, bw, false, e));
-          GB_CUDA_TRY(launch_update_simt<T>(W + r0 * ld + pe, ld, W + r0 * ld + j0, ld,
-                                            W + j0 * ld + pe, ld, pe - r0, n - pe, bw, true,
-                                            false, 0, status, st));
+          gb_status r = lu_inner_update<T>(h, dt, W + r0 * ld + pe, W + r0 * ld + j0,
+                                           W + j0 * ld + pe, ld, pe - r0, n - pe, bw, status, st);
+          if (r != GB_OK) return r;
         }
       }
     }
@@ -2095,7 +2125,15 @@ extern "C" gb_status gb_rank_update(gb_handle *h, gb_dtype dt, int lower, int y_
   const bool nn = y_is_kxn != 0;
   int *status = h->d_status;
   GB_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), st));
-  if (dt == GB_F64 && !lower) {
+  if (dt == GB_F64 && h->f64_update == 1 && tc_supported(h->device)) {
+    const bool same = !nn && X == Y && ldx == ldy && N <= M;
+    gb_status r = ws_reserve(h, WS_PANEL, update_digits_bytes(M, N, K, same), st);
+    if (r != GB_OK) return r;
+    GB_CUDA_TRY(launch_update_digits((double *)C, ldc, (const double *)X, ldx, (const double *)Y,
+                                     ldy, M, N, K, lower != 0, nn, status, h->d_err,
+                                     h->spin_limit, h->ws[WS_PANEL].ptr, h->ws[WS_PANEL].bytes,
+                                     h->sm_count, st));
+  } else if (dt == GB_F64 && !lower) {
     gb_status r = general_update<double>(h, (double *)C, ldc, (const double *)X, ldx,
                                          (const double *)Y, ldy, M, N, K, nn, status, WS_STRAS, st);
     if (r != GB_OK) return r;
@@ -2103,14 +2141,6 @@ extern "C" gb_status gb_rank_update(gb_handle *h, gb_dtype dt, int lower, int y_
     gb_status r = general_update<float>(h, (float *)C, ldc, (const float *)X, ldx,
                                         (const float *)Y, ldy, M, N, K, nn, status, WS_STRAS, st);
     if (r != GB_OK) return r;
-  } else if (dt == GB_F64 && h->f64_update == 1 && !nn && tc_supported(h->device)) {
-    const bool same = X == Y && ldx == ldy && N <= M;
-    gb_status r = ws_reserve(h, WS_PANEL, update_digits_bytes(M, N, K, same), st);
-    if (r != GB_OK) return r;
-    GB_CUDA_TRY(launch_update_digits((double *)C, ldc, (const double *)X, ldx, (const double *)Y,
-                                     ldy, M, N, K, status, h->d_err, h->spin_limit,
-                                     h->ws[WS_PANEL].ptr, h->ws[WS_PANEL].bytes, h->sm_count,
-                                     st));
   } else if (dt == GB_F64) {
     GB_CUDA_TRY(launch_update_simt<double>((double *)C, ldc, (const double *)X, ldx,
                                            (const double *)Y, ldy, M, N, K, nn, lower != 0, 0,

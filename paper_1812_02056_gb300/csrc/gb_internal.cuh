@@ -280,10 +280,13 @@ cudaError_t launch_inf_norm_rows(const double *A, int64_t lda, int64_t n, double
 // update_digits_bytes (same: Y is X's first N rows).  At most `max_ctas`
 // persistent CTAs (one per SM): fewer leave SMs to concurrent column steps.
 size_t update_digits_bytes(int64_t M, int64_t N, int64_t K, bool same);
+// lower: only j <= i (Cholesky); else every element.  y_kxn: Y is K x N
+// (LU's R_U), else N x K.
 cudaError_t launch_update_digits(double *C, int64_t ldc, const double *X, int64_t ldx,
                                  const double *Y, int64_t ldy, int64_t M, int64_t N, int64_t K,
-                                 const int *status, int *err, int64_t spin_limit, void *work,
-                                 size_t work_bytes, int max_ctas, cudaStream_t st);
+                                 bool lower, bool y_kxn, const int *status, int *err,
+                                 int64_t spin_limit, void *work, size_t work_bytes, int max_ctas,
+                                 cudaStream_t st);
 // GB_OPT_RESIDUAL 2 (default): the digit products from this order up
 constexpr int64_t SPLIT_RESIDUAL_MIN_N = 2048;
 size_t split_a_bytes(int64_t n);

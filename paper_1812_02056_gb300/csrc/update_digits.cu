@@ -1,6 +1,7 @@
 // The delayed rank-s update of Algorithm 1 in FP64 (arXiv:1812.02056,
 // Sec. 2: "A -= S, S = R R^T") to FP64 accuracy on the tensor cores:
-//   C (FP64) -= X Y^T     (lower: j <= i; X M x K, Y N x K, K-major rows)
+//   C (FP64) -= X Y^T     (Cholesky: lower, j <= i; X M x K, Y N x K rows)
+//   C (FP64) -= X Y       (LU: every element; Y K x N, cut by columns)
 // from exact products of the operands' digits (digits.cuh): row i of X is
 // cut into RP = 11 signed 5-bit digits a_p[i][.] at scale 2^e_i, row j of Y
 // likewise (b_q[j][.], 2^f_j), and
@@ -124,12 +125,70 @@ __global__ void digits_rows_kernel(const double *__restrict__ X, int64_t ldx, in
   }
 }
 
-// The valid tiles of the lower trapezoid (M x N, j <= i), row tiles of UBM
-// rows holding min(ntj, 4 bi + 4) column tiles of UBN, counted row by row;
-// index v goes to the CTA v mod gridDim.x.
+// Digits of the columns of Y (K x N, ldy, row-major: column j of Y is row
+// j of the B operand): planes[q][j][k] (row pitch kp), and the column scale
+// exponents.  One CTA of 256 threads per 32 columns: the scales from
+// coalesced row reads, then 64 x 32 tiles transposed in shared memory so
+// that each warp writes consecutive k of one column (two digits per
+// 4-byte store).
+__global__ void __launch_bounds__(256)
+    digits_cols_kernel(const double *__restrict__ Y, int64_t ldy, int64_t N, int64_t K,
+                       uint16_t *__restrict__ planes, int64_t kp, int64_t pstride,
+                       int *__restrict__ cexp, const int *status) {
+  if (status && *reinterpret_cast<const volatile int *>(status) != 0) return;
+  __shared__ double tile[64][33];
+  __shared__ unsigned long long smax[8][32];
+  __shared__ int se[32];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int64_t j0 = (int64_t)blockIdx.x * 32, j = j0 + tx;
+  constexpr unsigned long long ABS = 0x7fffffffffffffffull;
+  unsigned long long mx = 0;
+  if (j < N)
+    for (int64_t k = ty; k < K; k += 8) {
+      const unsigned long long a = (unsigned long long)__double_as_longlong(Y[k * ldy + j]) & ABS;
+      mx = a > mx ? a : mx;
+    }
+  smax[ty][tx] = mx;
+  __syncthreads();
+  if (ty == 0) {
+    for (int t = 1; t < 8; ++t) mx = smax[t][tx] > mx ? smax[t][tx] : mx;
+    const int e = scale_exp(__longlong_as_double((long long)mx));
+    se[tx] = e;
+    if (j < N) cexp[j] = e;
+  }
+  __syncthreads();
+  for (int64_t k0 = 0; k0 < K; k0 += 64) {
+    for (int r = ty; r < 64; r += 8)
+      tile[r][tx] = (k0 + r < K && j < N) ? Y[(k0 + r) * ldy + j] : 0.0;
+    __syncthreads();
+    const int64_t k = k0 + 2 * tx;
+    for (int c = ty; c < 32; c += 8) {
+      const int64_t jc = j0 + c;
+      if (jc < N && k < K) {
+        uint32_t d[RP];
+        digits2(tile[2 * tx][c], tile[2 * tx + 1][c], se[c], d);
+        uint16_t *dst = planes + jc * kp + k;
+        if (k + 1 < K) {  // kp even, k even: 4-byte aligned
+#pragma unroll
+          for (int p = 0; p < RP; ++p) *reinterpret_cast<uint32_t *>(dst + p * pstride) = d[p];
+        } else {
+#pragma unroll
+          for (int p = 0; p < RP; ++p) dst[p * pstride] = (uint16_t)(d[p] & 0xffffu);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// The valid tiles of the lower trapezoid (M x N, j <= i; row tile bi of UBM
+// rows holds min(ntj, 2 bi + 2) column tiles of UBN), or of the whole
+// rectangle, counted row by row; index v goes to the CTA v mod gridDim.x.
 struct UTileIter {
   int64_t v, total, ntj, bi, base;
+  int lower;  // 0: every tile of the M x N rectangle
   __device__ int64_t count(int64_t b) const {
+    if (!lower) return ntj;
     const int64_t c = (b * UBM + UBM - 1) / UBN + 1;
     return c < ntj ? c : ntj;
   }
@@ -150,8 +209,8 @@ __global__ void __launch_bounds__(UTHREADS, 1)
     update_digits_kernel(const __grid_constant__ CUtensorMap map_a,
                          const __grid_constant__ CUtensorMap map_b, const int *__restrict__ ea,
                          const int *__restrict__ eb, double *__restrict__ C, int64_t ldc,
-                         int64_t M, int64_t N, int nkb, int64_t total, const int *status, int *err,
-                         long long wait_ns) {
+                         int64_t M, int64_t N, int nkb, int64_t total, int lower,
+                         const int *status, int *err, long long wait_ns) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -191,7 +250,7 @@ __global__ void __launch_bounds__(UTHREADS, 1)
   const uint32_t tmem = *tmem_slot;
   const unsigned long long deadline = (unsigned long long)wait_ns;
   const int64_t ntj = (N + UBN - 1) / UBN;
-  UTileIter it{(int64_t)blockIdx.x, total, ntj, 0, 0};
+  UTileIter it{(int64_t)blockIdx.x, total, ntj, 0, 0, lower};
   int64_t m0 = 0, n0 = 0;
 
   if (*skip) {
@@ -325,7 +384,7 @@ __global__ void __launch_bounds__(UTHREADS, 1)
 #pragma unroll
           for (int it2 = 0; it2 < 16; ++it2) {
             const int64_t row = r0 + 2 * it2 + (lane >> 4);
-            cv[it2] = (row < M && j < N && j <= row) ? C[row * ldc + j] : 0.0;
+            cv[it2] = (row < M && j < N && (!lower || j <= row)) ? C[row * ldc + j] : 0.0;
           }
           // the pass's six scales folded exactly: v = sum S_t 2^(5 (thi - t)),
           // below 2^50; its weight is 2^(-5 (thi + 2))
@@ -357,7 +416,7 @@ __global__ void __launch_bounds__(UTHREADS, 1)
               const int r = 2 * it2 + (lane >> 4);
               const int64_t row = r0 + r;
               const int e = __shfl_sync(0xffffffffu, e_r, r) + e_j - RW * (thi + 2);
-              if (row < M && j < N && j <= row) {
+              if (row < M && j < N && (!lower || j <= row)) {
                 const double sc = __longlong_as_double((long long)(1023 + e) << 52);
                 C[row * ldc + j] = cv[it2] - blk[r * UTP + cl] * sc;
               }
@@ -409,11 +468,12 @@ size_t update_digits_bytes(int64_t M, int64_t N, int64_t K, bool same) {
 
 cudaError_t launch_update_digits(double *C, int64_t ldc, const double *X, int64_t ldx,
                                  const double *Y, int64_t ldy, int64_t M, int64_t N, int64_t K,
-                                 const int *status, int *err, int64_t spin_limit, void *work,
-                                 size_t work_bytes, int max_ctas, cudaStream_t st) {
+                                 bool lower, bool y_kxn, const int *status, int *err,
+                                 int64_t spin_limit, void *work, size_t work_bytes, int max_ctas,
+                                 cudaStream_t st) {
   if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
   // Y's rows are X's first N rows (a Cholesky update): one set of digits
-  const bool same = X == Y && ldx == ldy && N <= M;
+  const bool same = !y_kxn && X == Y && ldx == ldy && N <= M;
   if (!work || work_bytes < update_digits_bytes(M, N, K, same)) return cudaErrorInvalidValue;
   static bool attr = false;
   if (!attr) {
@@ -426,7 +486,8 @@ cudaError_t launch_update_digits(double *C, int64_t ldc, const double *X, int64_
   const long long wait_ns = std::min<long long>((long long)spin_limit * 100LL, 1000000000LL);
   const int64_t nbi = (M + UBM - 1) / UBM, ntj = (N + UBN - 1) / UBN;
   int64_t total = 0;
-  for (int64_t b = 0; b < nbi; ++b) total += std::min<int64_t>(ntj, (b * UBM + UBM - 1) / UBN + 1);
+  for (int64_t b = 0; b < nbi; ++b)
+    total += lower ? std::min<int64_t>(ntj, (b * UBM + UBM - 1) / UBN + 1) : ntj;
   for (int64_t k0 = 0; k0 < K; k0 += UK_MAX) {
     const int64_t kc = std::min<int64_t>(UK_MAX, K - k0), kp = digits_kp(kc);
     uint16_t *pa = reinterpret_cast<uint16_t *>(work);
@@ -441,8 +502,12 @@ cudaError_t launch_update_digits(double *C, int64_t ldc, const double *X, int64_
       char *wb = (char *)work + digit_set_bytes(M, K);
       pb = reinterpret_cast<uint16_t *>(wb);
       eb = reinterpret_cast<int *>(wb + align256u((size_t)RP * N * kp * 2));
-      digits_rows_kernel<<<(unsigned)ceil_div(N, 8), 256, 0, st>>>(Y + k0, ldy, N, kc, pb, kp,
-                                                                    N * kp, eb, status);
+      if (y_kxn)
+        digits_cols_kernel<<<(unsigned)ceil_div(N, 32), 256, 0, st>>>(Y + k0 * ldy, ldy, N, kc, pb,
+                                                                       kp, N * kp, eb, status);
+      else
+        digits_rows_kernel<<<(unsigned)ceil_div(N, 8), 256, 0, st>>>(Y + k0, ldy, N, kc, pb, kp,
+                                                                      N * kp, eb, status);
       count_launch();
       rows_b = N;
     }
@@ -451,8 +516,8 @@ cudaError_t launch_update_digits(double *C, int64_t ldc, const double *X, int64_
       return cudaErrorInvalidValue;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(total, max_ctas));
     update_digits_kernel<<<grid, UTHREADS, USMEM, st>>>(ma, mb, ea, eb, C, ldc, M, N,
-                                                        (int)((kc + UBK - 1) / UBK), total, status,
-                                                        err, wait_ns);
+                                                        (int)((kc + UBK - 1) / UBK), total,
+                                                        lower ? 1 : 0, status, err, wait_ns);
     count_launch();
   }
   return cudaGetLastError();

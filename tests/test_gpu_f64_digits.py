@@ -13,6 +13,9 @@ oracle references.
   (elementwise, guarded), backward error <= 1e-13, the same bits with and
   without look-ahead, breakdown reported as usual; at the benchmark's
   n = 8192, s = 256 against the oracle's whole factor.
+* Algorithm 2's general update (every element, R_U stored K x N) exact on
+  integers, and gb_lu_factor with the option against the oracle's L and U
+  (1e-10, backward error <= 1e-13) and exact on integer factors.
 """
 import numpy as np
 import pytest
@@ -162,3 +165,59 @@ def test_chol_f64_digits_n8192_full_oracle(h):
     Lo, info_o = oracle.chol(A.cpu().numpy(), 256)
     assert info_o == 0
     assert guarded_rel_err(L.cpu().numpy(), Lo) <= 1e-10
+
+
+def _general_update(h, C, X, Y, y_kxn):
+    """C -= X op(Y) over every element (gb_rank_update with lower = 0)."""
+    from paper_1812_02056_gb300 import binding
+    M, K = X.shape
+    N = Y.shape[1] if y_kxn else Y.shape[0]
+    Cd, Xd, Yd = _t(C), _t(X), _t(Y)
+    st = h.gb_rank_update(binding.GB_F64, 0, int(y_kxn), M, N, K, Cd, N, Xd, K, Yd,
+                          N if y_kxn else K)
+    assert st == 0, binding.status_string(st)
+    torch.cuda.synchronize()
+    return Cd.cpu().numpy()
+
+
+@pytest.mark.parametrize("M,N,K,y_kxn", [(700, 1300, 300, True), (2100, 500, 1100, True),
+                                         (640, 640, 64, False), (300, 1000, 17, True)])
+def test_general_integer_update_is_exact(h, M, N, K, y_kxn):
+    """Algorithm 2's update (every element; R_U stored K x N and cut into
+    digits by columns), and the N x K form, exact on integers."""
+    rng = np.random.default_rng(M * 7 + N + K)
+    X = rng.integers(-1000, 1001, (M, K))
+    Y = rng.integers(-1000, 1001, (K, N) if y_kxn else (N, K))
+    C = rng.integers(-10 ** 9, 10 ** 9, (M, N))
+    ref = C - X @ (Y if y_kxn else Y.T)
+    with _digits(h):
+        got = _general_update(h, C.astype(np.float64), X.astype(np.float64),
+                              Y.astype(np.float64), y_kxn)
+    assert np.array_equal(got, ref.astype(np.float64))
+
+
+@pytest.mark.parametrize("n,s", [(300, 32), (1000, 256), (2600, 512), (3001, 300)])
+def test_lu_f64_digits_matches_oracle(h, n, s):
+    from tests.helpers import lu_split
+    A = I.lu_diag_dominant(n, 500 + n)
+    with _digits(h):
+        LU, info = h.lu_factor(_t(A), s, "f64")
+    assert int(info.item()) == 0
+    L, U = lu_split(LU.cpu().numpy())
+    Lo, Uo, info_o = oracle.lu(A, s)
+    assert info_o == 0
+    assert guarded_rel_err(L, Lo) <= 1e-10
+    assert guarded_rel_err(U, Uo) <= 1e-10
+    assert oracle.lu_backward_error(A, L, U) <= 1e-13
+
+
+@pytest.mark.parametrize("s", [7, 64])
+def test_lu_f64_digits_integer_factors_exact(h, s):
+    from tests.helpers import lu_split
+    n = 120
+    L0 = I.unit_lower_integer(n, 5)
+    U0 = I.unit_lower_integer(n, 6).T
+    with _digits(h):
+        LU, info = h.lu_factor(_t(L0 @ U0), s, "f64")
+    L, U = lu_split(LU.cpu().numpy())
+    assert int(info.item()) == 0 and np.array_equal(L, L0) and np.array_equal(U, U0)
